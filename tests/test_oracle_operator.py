@@ -1,0 +1,209 @@
+"""Pins of the oracle's operator against facts fixed by the paper and the mathematics.
+
+* Symmetry and definiteness: the paper's operator is symmetric positive
+  definite (Section 3, Eq. (ModelEquation); the column blocks are "symmetric
+  tridiagonal", Eq. (TridiagonalMatrix)).
+* Row sums: every difference term vanishes on a constant vector, so
+  A 1 = lambda^2 x (cell volume), and A 1 = 0 when lambda^2 = 0.
+* Discrete Fourier eigenvalues of the periodic horizontal operator (a closed
+  form independent of the assembly code).
+* Total area of the latitude band and total shell volume (closed forms).
+* Second-order convergence to a manufactured solution of the continuous PDE
+  (the finite-volume scheme of Section 3.1), which fails for a dropped term,
+  a wrong sign, a wrong metric factor or a misplaced face coefficient.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import FluxOperator, apply_rows, assemble_csr, cell_volumes, operator_terms
+
+
+def _problems():
+    return [
+        W.box_problem(5, 4, 6, 0.01, name="box"),
+        W.box_problem(4, 6, 5, 0.02, alpha="sin", name="box-sin"),
+        W.box_problem(3, 3, 4, 0.01, lambda2=0.5, name="box-3"),
+        W.latlon_problem(8, 5, 4, thickness=0.01, name="latlon"),
+        W.box_problem(1, 2, 3, 0.01, name="box-1x2"),
+    ]
+
+
+@pytest.mark.parametrize("p", _problems(), ids=lambda p: p.name)
+def test_symmetric_bitwise(p):
+    a = assemble_csr(p)
+    diff = a - a.T
+    diff.eliminate_zeros()
+    assert diff.nnz == 0
+
+
+@pytest.mark.parametrize("p", _problems(), ids=lambda p: p.name)
+def test_positive_definite(p):
+    a = assemble_csr(p).toarray()
+    np.linalg.cholesky(a)            # raises if not SPD
+    assert np.linalg.eigvalsh(a).min() > 0
+
+
+@pytest.mark.parametrize("p", _problems(), ids=lambda p: p.name)
+def test_row_sums_are_mass_terms(p):
+    # flux form: every flux vanishes on a constant vector, so A 1 is the mass
+    # term exactly; the assembled matrix agrees to the rounding of its diagonal.
+    vol = cell_volumes(p).ravel()
+    op = FluxOperator(p)
+    rs = op @ np.ones(p.n_cells)
+    np.testing.assert_allclose(rs, p.lambda2 * vol, rtol=1e-13, atol=0)
+    assert (rs == op.mass).all()
+    a = assemble_csr(p)
+    ra = a @ np.ones(p.n_cells)
+    assert np.abs(ra - rs).max() <= 8 * np.finfo(float).eps * np.abs(a.diagonal()).max()
+
+
+def test_row_sums_vanish_without_mass():
+    for p in (W.box_problem(6, 5, 7, 0.01, lambda2=0.0, alpha="sin"),
+              W.latlon_problem(8, 6, 5, thickness=0.01, lambda2=0.0)):
+        assert not (FluxOperator(p) @ np.ones(p.n_cells)).any()
+        a = assemble_csr(p)
+        rs = a @ np.ones(p.n_cells)
+        assert np.abs(rs).max() <= 1e-14 * np.abs(a.diagonal()).max()
+
+
+@pytest.mark.parametrize("p", _problems(), ids=lambda p: p.name)
+def test_flux_form_is_the_assembled_operator(p):
+    a = assemble_csr(p)
+    op = FluxOperator(p)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        x = rng.standard_normal(p.n_cells)
+        ya, yf = a @ x, op @ x
+        bound = 16 * np.finfo(float).eps * (abs(a) @ abs(x))      # componentwise SpMV error bound
+        assert (np.abs(yf - ya) <= bound).all()
+    if min(p.n_x, p.n_y) > 1:      # on a one-cell periodic axis a cell couples to itself
+        np.testing.assert_allclose(op.diagonal(), a.diagonal(), rtol=8 * np.finfo(float).eps)
+    diff = op.C - op.C.T
+    diff.eliminate_zeros()
+    assert diff.nnz == 0 and (op.C.data > 0).all()
+
+
+def test_stencil_has_seven_points_and_neumann_ends():
+    p = W.box_problem(6, 5, 4, 0.01)
+    a = assemble_csr(p)
+    nnz_per_row = np.diff(a.indptr).reshape(p.shape)
+    assert (nnz_per_row[1:-1] == 7).all()          # interior levels: 7-point stencil
+    assert (nnz_per_row[0] == 6).all() and (nnz_per_row[-1] == 6).all()
+    p = W.latlon_problem(8, 5, 4, thickness=0.01)
+    nnz = np.diff(assemble_csr(p).indptr).reshape(p.shape)
+    assert (nnz[1:-1, 1:-1] == 7).all()
+    assert (nnz[1:-1, 0] == 6).all() and (nnz[1:-1, -1] == 6).all()   # latitude edges: Neumann
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_horizontal_fourier_eigenvalues(mode):
+    # u_ijk = cos(2 pi m (i + 1/2)/n_x) for every j, k: vertical and y terms vanish,
+    # and the periodic second difference has eigenvalue 2 - 2 cos(2 pi m / n_x).
+    n_x, n_y, n_z = 12, 5, 4
+    p = W.box_problem(n_x, n_y, n_z, 0.01, lambda2=0.3)
+    a = assemble_csr(p)
+    hx, hy = 1.0 / n_x, 1.0 / n_y
+    dz = np.diff(p.z_iface)
+    i = np.arange(n_x)
+    u = np.broadcast_to(np.cos(2 * np.pi * mode * (i + 0.5) / n_x), p.shape)
+    lam = p.lambda2 * hx * hy + (hy / hx) * (2 - 2 * np.cos(2 * np.pi * mode / n_x))
+    expect = lam * dz[:, None, None] * u
+    np.testing.assert_allclose((a @ u.ravel()).reshape(p.shape), expect, rtol=1e-11, atol=1e-17)
+    # the same in y
+    j = np.arange(n_y)
+    u = np.broadcast_to(np.cos(2 * np.pi * mode * (j[:, None] + 0.5) / n_y), p.shape)
+    lam = p.lambda2 * hx * hy + (hx / hy) * (2 - 2 * np.cos(2 * np.pi * mode / n_y))
+    np.testing.assert_allclose((a @ u.ravel()).reshape(p.shape), lam * dz[:, None, None] * u,
+                               rtol=1e-11, atol=1e-17)
+
+
+def test_latlon_band_area_and_volume():
+    p = W.latlon_problem(36, 20, 6, thickness=0.05, lat_deg=70.0)
+    t = operator_terms(p)
+    band = 2 * np.pi * (math.sin(p.lat1) - math.sin(p.lat0))
+    assert abs(t.area.sum() * p.n_x - band) < 1e-13 * band
+    r0, r1 = p.z_iface[0], p.z_iface[-1]
+    shell = band * (r1 ** 3 - r0 ** 3) / 3
+    assert abs(cell_volumes(p).sum() - shell) < 1e-12 * shell
+
+
+@pytest.mark.parametrize("p", _problems(), ids=lambda p: p.name)
+def test_apply_rows_matches_matrix(p):
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(p.shape)
+    a = assemble_csr(p)
+    y = (a @ x.ravel()).reshape(p.shape)
+    cells = np.stack(np.meshgrid(np.arange(p.n_z), np.arange(p.n_y), np.arange(p.n_x), indexing="ij")).reshape(3, -1)
+    yr = apply_rows(p, x, cells)
+    np.testing.assert_allclose(yr, y.ravel(), rtol=1e-13, atol=1e-13 * np.abs(y).max())
+
+
+# ---------------------------------------------------------------------------
+# Manufactured solutions: second-order convergence of the discrete solution to
+# the continuous one under uniform refinement of every spacing.
+# ---------------------------------------------------------------------------
+
+def _mms_box(n, depth=1.0, bscale=0.5, lam2=1.0):
+    sym = pytest.importorskip("sympy")
+    x, y, z = sym.symbols("x y z", real=True)
+    u = sym.cos(2 * sym.pi * x) * sym.cos(2 * sym.pi * y) * sym.cos(sym.pi * z / depth)
+    alpha = 1 + sym.Rational(1, 2) * sym.sin(2 * sym.pi * x) * sym.sin(2 * sym.pi * y)
+    beta = sym.exp(-z / bscale)
+    f = (-sym.diff(alpha * sym.diff(u, x), x) - sym.diff(alpha * sym.diff(u, y), y)
+         - sym.diff(beta * sym.diff(u, z), z) + lam2 * u)
+    fn = sym.lambdify((x, y, z), f, "numpy")
+    un = sym.lambdify((x, y, z), u, "numpy")
+    zi = W.smooth_graded_interfaces(n, depth)
+    ae, an = W.sinusoidal_alpha(n, n)
+    p = W.Problem(kind=W.GEOM_BOX, n_x=n, n_y=n, n_z=n, z_iface=zi,
+                  beta_iface=W.exp_profile(zi, bscale), lambda2=lam2, alpha_e=ae, alpha_n=an)
+    xc = (np.arange(n) + 0.5) / n
+    zc = 0.5 * (zi[1:] + zi[:-1])
+    Z, Y, X = np.meshgrid(zc, xc, xc, indexing="ij")
+    b = fn(X, Y, Z) * cell_volumes(p)
+    ue = un(X, Y, Z)
+    uh = spla.spsolve(assemble_csr(p).tocsc(), b.ravel()).reshape(p.shape)
+    return np.sqrt(np.mean((uh - ue) ** 2))
+
+
+def _mms_latlon(n, H=0.5, bscale=0.5, lam2=1.0, lat_deg=60.0):
+    sym = pytest.importorskip("sympy")
+    lon, lat, r = sym.symbols("lon lat r", real=True)
+    L0 = -sym.pi * lat_deg / 180
+    L1 = sym.pi * lat_deg / 180
+    u = sym.cos(lon) * sym.cos(sym.pi * (lat - L0) / (L1 - L0)) * sym.cos(sym.pi * (r - 1) / H)
+    beta = sym.exp(-(r - 1) / bscale)
+    lap_sphere = (sym.diff(sym.cos(lat) * sym.diff(u, lat), lat) / sym.cos(lat)
+                  + sym.diff(u, lon, 2) / sym.cos(lat) ** 2)
+    f = -lap_sphere / r ** 2 - sym.diff(r ** 2 * beta * sym.diff(u, r), r) / r ** 2 + lam2 * u
+    fn = sym.lambdify((lon, lat, r), f, "numpy")
+    un = sym.lambdify((lon, lat, r), u, "numpy")
+    ri = 1.0 + W.smooth_graded_interfaces(n, H)
+    p = W.Problem(kind=W.GEOM_LATLON, n_x=2 * n, n_y=n, n_z=n, z_iface=ri,
+                  beta_iface=W.exp_profile(ri, bscale, origin=1.0), lambda2=lam2,
+                  lat0=-math.radians(lat_deg), lat1=math.radians(lat_deg))
+    lonc = (np.arange(2 * n) + 0.5) * 2 * np.pi / (2 * n)
+    dlat = (p.lat1 - p.lat0) / n
+    latc = p.lat0 + (np.arange(n) + 0.5) * dlat
+    rc = 0.5 * (ri[1:] + ri[:-1])
+    R, LAT, LON = np.meshgrid(rc, latc, lonc, indexing="ij")
+    b = fn(LON, LAT, R) * cell_volumes(p)
+    ue = un(LON, LAT, R)
+    uh = spla.spsolve(assemble_csr(p).tocsc(), b.ravel()).reshape(p.shape)
+    return np.sqrt(np.mean((uh - ue) ** 2))
+
+
+def test_manufactured_solution_box_second_order():
+    e = [_mms_box(n) for n in (8, 16, 32)]
+    ratios = [e[0] / e[1], e[1] / e[2]]
+    assert all(3.3 < q < 4.8 for q in ratios), (e, ratios)
+
+
+def test_manufactured_solution_latlon_second_order():
+    e = [_mms_latlon(n) for n in (8, 16, 32)]
+    ratios = [e[0] / e[1], e[1] / e[2]]
+    assert all(3.3 < q < 4.8 for q in ratios), (e, ratios)
