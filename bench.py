@@ -1,0 +1,350 @@
+"""Benchmark: PCG solves/s of the line-preconditioned matrix-free CG solver.
+
+Workload (one "step" = one full solve, every stage of the iteration):
+256 x 256 x 128 periodic box, depth 0.004, levels graded by 1.05,
+alpha = 1, beta = exp(-z/0.005), lambda^2 = 1e-2, right-hand side
+uniform[-1, 1] (seed 0) plus sin(2 pi x) cos(2 pi y) zeta, FP64 PCG with the
+vertical-line preconditioner to relative residual 1e-8 (Algorithm 1).
+
+Reported on one JSON line: solves/s (device time, inputs resident), the same
+through the host-buffer entry point (e2e), the roofline of the dominant
+fused sweep, sampled clocks, the CPU oracle as a reported baseline, and the
+mixed-precision (FP32 inner + FP64 refinement) form of the same solve.
+
+Multi-GPU: the solver does not shard (one problem per GPU); with N ranks each
+rank runs its own replica of the workload and `value` counts the solves of
+all ranks over the slowest rank's time ("replicas only", weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+TOL = 1e-8
+WORKLOAD = "box256x256x128_fp64_tol1e-8"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 pipe: 2 FP64 FMA per clock per SM on this part (measured with a
+# dependent-free DFMA loop: 0.595e12 per s at ~1.96 GHz on 152 SMs).
+FP64_OPS_PER_CLK_SM = 2.0
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_iterations():
+    """Iterations of one solve of this workload, as counted by the CPU oracle
+    (tests/golden/make_oracle_counts.py writes the file)."""
+    with open(os.path.join(ROOT, "tests", "golden", "medium_box_oracle.json")) as f:
+        return int(json.load(f)["iterations"])
+
+
+def _oracle_setup():
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    import workloads as W
+    from oracle import FluxOperator, LinePreconditioner, assemble_csr
+    p = W.medium_box()
+    b = W.medium_box_rhs(p)
+    t0 = time.perf_counter()
+    op = FluxOperator(p)
+    m = LinePreconditioner(assemble_csr(p), p)
+    return p, b, op, m, time.perf_counter() - t0
+
+
+def cpu_baseline(seconds: float = 15.0):
+    """The CPU oracle (plain FP64 PCG with an explicit CSR operator and
+    LAPACK line solves), timed on a bounded sample of the same workload:
+    a fixed number of Algorithm-1 passes, scaled to solves/s by the
+    oracle's own iteration count for one solve."""
+    from oracle import pcg_interleaved
+    p, b, op, m, setup = _oracle_setup()
+    t0 = time.perf_counter()
+    pcg_interleaved(op, m, b, eps=0.0, maxiter=1)
+    dt = time.perf_counter() - t0
+    k = max(2, int(2 * seconds / max(dt, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    pcg_interleaved(op, m, b, eps=0.0, maxiter=k)
+    dt = time.perf_counter() - t0
+    return {"s_per_iteration": dt / (k + 1), "iterations_timed": k, "setup_s": setup, "cores": 1}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle on the host cores, on this arm's
+    metric and workload; each step is a bounded sample (a fixed number of
+    Algorithm-1 passes of the full problem), scaled by the oracle's
+    iteration count per solve."""
+    if rank != 0:
+        return
+    from oracle import pcg_interleaved
+    iters = oracle_iterations()
+    p, b, op, m, setup = _oracle_setup()
+    passes = 6
+    for _ in range(args.warmup):
+        pcg_interleaved(op, m, b, eps=0.0, maxiter=passes - 1)
+    t_steps = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pcg_interleaved(op, m, b, eps=0.0, maxiter=passes - 1)
+        t_steps.append(time.perf_counter() - t0)
+    t_pass = sum(t_steps) / (args.steps * passes)
+    sps = 1.0 / (t_pass * iters)
+    sample = (f"{passes} Algorithm-1 passes of the full 256x256x128 problem per step "
+              f"({t_pass * 1e3:.0f} ms each), scaled by the oracle's {iters} iterations per solve; "
+              f"setup (CSR assembly, LAPACK factorisation) {setup:.1f} s not included")
+    line = {
+        "impl": "reference", "metric": "PCG solves/s", "value": sps, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / sps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [256, 256, 128], "tol": TOL, "precision": "fp64",
+                   "l2": "not applicable (CPU)"},
+        "cpu_baseline": {"value": sps, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": sps, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+    import paper_1302_7193_gb300 as pkg
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p = W.medium_box()
+    b_np = W.medium_box_rhs(p).ravel()
+    n = p.n_cells
+    b = torch.from_numpy(b_np).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+    solver = pkg.Solver(p, stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up
+    for _ in range(args.warmup):
+        x.zero_()
+        solver.solve(b, x, tol=TOL, maxit=100000)
+    barrier()
+    times, iters, stats = [], [], None
+    launches = 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                      # evict L2 between timed steps
+            x.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats = solver.solve(b, x, tol=TOL, maxit=100000)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            iters.append(stats.iterations)
+            launches += solver.kernel_launches
+    barrier()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    clocks = clk.summary()
+    value = world * args.steps / (total_ms / 1000.0)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the fused sweeps (CUDA events around each launch, same stream)
+    ms_prec, ms_spmv = solver.pcg_time_sweeps(b, "fp64", passes=20)
+    hbm_peak, peak_kind = _peaks()
+    sm_mhz = clocks.get("sm_mhz") or 1965.0
+    fp64_peak_ops = FP64_OPS_PER_CLK_SM * 152 * sm_mhz * 1e6
+    # algorithmic traffic: prec sweep reads r, q, writes r, z; SpMV sweep reads u, p, q, z, writes u, p, q
+    bytes_prec, bytes_spmv = 4 * 8 * n, 7 * 8 * n
+    # FP64 operations per unknown as written (flux-form stencil and excess-form Thomas)
+    ops_prec, ops_spmv = 9 * n, 18 * n
+    dom = "spmv" if ms_spmv >= ms_prec else "prec"
+    t_dom = ms_spmv if dom == "spmv" else ms_prec
+    by, op_ = (bytes_spmv, ops_spmv) if dom == "spmv" else (bytes_prec, ops_prec)
+    gbs = by / (t_dom * 1e-3) / 1e9
+    alu = op_ / (t_dom * 1e-3)
+    frac_hbm, frac_alu = gbs / hbm_peak, alu / fp64_peak_ops
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": alu / 1e12, "peak": fp64_peak_ops / 1e12, "unit": "TFP64op/s",
+                "frac": frac_alu, "traffic": None}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm, "traffic": None}
+    roof.update({"kernel": f"k_sweep_{dom}<double>", "ms_per_launch": t_dom,
+                 "hbm_gbs_algorithmic": gbs, "hbm_frac": frac_hbm, "peak_source": peak_kind,
+                 "iteration_gbs_algorithmic": (bytes_prec + bytes_spmv) / ((ms_prec + ms_spmv) * 1e-3) / 1e9,
+                 "ms_per_iteration": ms_prec + ms_spmv})
+
+    # end to end: the host-buffer entry point, pinned buffers, copies inside the timed region
+    bh = torch.from_numpy(b_np.copy()).pin_memory().numpy()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    solver.solve_host(bh, xh, tol=TOL, maxit=100000)
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        xh[:] = 0.0
+        t0 = time.perf_counter()
+        solver.solve_host(bh, xh, tol=TOL, maxit=100000)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": world / statistics.mean(e2e_t), "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * n,
+           "d2h_bytes_per_step": 8 * n}
+
+    # mixed precision form of the same solve
+    mixed = None
+    if not args.no_mixed:
+        with pkg.Solver(p, precision="mixed", stream=stream.cuda_stream) as sm:
+            for _ in range(2):
+                x.zero_()
+                sm.solve(b, x, tol=TOL, maxit=100000)
+            mt = []
+            for _ in range(max(1, min(args.steps, 3))):
+                flush.fill_(1.0)
+                x.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mst = sm.solve(b, x, tol=TOL, maxit=100000)
+                e1.record(stream)
+                e1.synchronize()
+                mt.append(e0.elapsed_time(e1))
+            mp, ms = sm.pcg_time_sweeps(b, "mixed", passes=20)
+            it_gbs = (4 + 7) * 4 * n / ((mp + ms) * 1e-3) / 1e9
+            mixed = {"value": 1000.0 / statistics.mean(mt), "unit": "solves/s", "inner_iterations": mst.iterations,
+                     "outer_sweeps": mst.outer_sweeps, "relres_true": mst.relres_true,
+                     "speedup_vs_fp64": (1000.0 / statistics.mean(mt)) / (1000.0 / ms_per_step),
+                     "fp32_ms_per_iteration": mp + ms, "fp32_iteration_gbs_algorithmic": it_gbs,
+                     "fp32_iteration_hbm_frac": it_gbs / hbm_peak}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cb = cpu_baseline()
+            oi = oracle_iterations()
+            cps = 1.0 / (cb["s_per_iteration"] * oi)
+            cpu = {"value": cps, "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
+                   "sample": f"{cb['iterations_timed']} Algorithm-1 passes of the full problem "
+                             f"({cb['s_per_iteration'] * 1e3:.1f} ms each), scaled by the oracle's "
+                             f"{oi} iterations per solve"}
+        except Exception as e:           # the baseline is reported, never required
+            cpu = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {
+            "metric": "PCG solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [256, 256, 128], "unknowns": n, "tol": TOL,
+                       "iterations_per_solve": statistics.mean(iters), "precision": "fp64",
+                       "relres_true": stats.relres_true, "parallelism": f"replicas{world}",
+                       "l2": "256 MB buffer written between timed steps; working set 5 x 67 MB"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+            "cpu_baseline": cpu, "mixed": mixed,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * pcg.h -- C-ABI of the GB300 matrix-free line-preconditioned CG solver.
+ *
+ * The library solves A u = b for the finite-volume discretisation of the
+ * anisotropic elliptic model equation of Mueller, Guo, Scheichl, Shi,
+ * "Matrix-free GPU implementation of a preconditioned conjugate gradient
+ * solver for anisotropic elliptic PDEs" (Section 3, Eq. (ModelEquation)), in
+ * the generalised form
+ *
+ *     -div_h(alpha grad_h u) - (1/S) d_z(S beta d_z u) + lambda^2 u = f
+ *
+ * on a tensor-product column grid: a periodic rectangle (S = 1) or a
+ * latitude-longitude band of a spherical shell (S = r^2, Neumann at the
+ * latitude edges), with Neumann conditions at the bottom and top of every
+ * column.  The operator is never stored: each application recomputes the
+ * stencil from per-level profiles and per-column metric terms (Section 4.2).
+ * The preconditioner is the vertical-line (block-Jacobi) preconditioner
+ * M = block-diag(A), one tridiagonal solve per column (Section 4.1).  The
+ * solver is the interleaved PCG loop of Algorithm 1 (Section 4.3) with its
+ * two fused grid sweeps (Algorithms 2 and 3 of the appendix).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Vectors are contiguous arrays in the layout [nrhs][n_z][n_y][n_x]
+ *    (x fastest; each vertical level is one contiguous horizontal plane).
+ *  - "Device pointer" arguments are CUDA device (or managed) memory owned by
+ *    the caller; the library never frees them.  "Host" arguments are read
+ *    during the call and copied; the library keeps no reference to them.
+ *  - Work is enqueued on the stream given in pcg_opts_t at creation.  Calls
+ *    return after enqueueing unless stated otherwise; stats are final once
+ *    the call that fills them has returned.
+ *  - Every function returns a pcg_status value; on failure the reason is
+ *    available from pcg_last_error().  No function aborts, throws or traps.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef PCG_GB300_H
+#define PCG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+enum pcg_status {
+    PCG_OK = 0,
+    PCG_ERR_INVALID_ARG = 1,   /* bad pointer, size, geometry or option          */
+    PCG_ERR_OOM = 2,           /* device or pinned host allocation failed        */
+    PCG_ERR_CUDA = 3,          /* a CUDA runtime call failed (text in last_error) */
+    PCG_NOT_CONVERGED = 4,     /* maxit reached before the stopping test passed  */
+    PCG_BREAKDOWN = 5,         /* <p,Ap> <= 0, <r,z> < 0 or a non-finite scalar    */
+    PCG_TIMEOUT = 6            /* a bounded device wait gave up (serving only)    */
+};
+
+/* ---- geometry / precision selectors ------------------------------------- */
+enum pcg_geometry {
+    PCG_GEOM_BOX = 0,          /* periodic lx x ly rectangle, heights z_iface    */
+    PCG_GEOM_LATLON = 1        /* lon periodic over 2 pi, lat in [lat0, lat1]    */
+};
+enum pcg_precision {
+    PCG_FP64 = 0,              /* FP64 storage and arithmetic throughout          */
+    PCG_MIXED = 1              /* FP32 inner PCG inside FP64 iterative refinement */
+};
+
+typedef struct pcg_ctx* pcg_t;
+
+/* Grid (Section 3.1: tensor product of a horizontal grid and a graded
+ * vertical grid).  z_iface: host array of n_z+1 strictly increasing
+ * interface heights (box) or radii (latlon). */
+typedef struct {
+    int geometry;              /* pcg_geometry                                    */
+    int n_x, n_y, n_z;         /* cells per direction, each >= 1                  */
+    int nrhs;                  /* right-hand sides solved together, >= 1          */
+    const double* z_iface;     /* host, n_z + 1 values                            */
+    double lx, ly;             /* box: periodic extents (> 0)                     */
+    double lat0, lat1;         /* latlon: band edges in radians, -pi/2 < lat0 < lat1 < pi/2 */
+} pcg_grid_t;
+
+/* Coefficients of the model equation, sampled where the finite-volume scheme
+ * needs them: alpha at horizontal face midpoints, beta at level interfaces. */
+typedef struct {
+    const double* alpha_e;     /* host [n_y][n_x]: alpha on the east face of (i,j), or NULL for alpha = 1 */
+    const double* alpha_n;     /* host [n_y][n_x]: alpha on the north face of (i,j), or NULL for alpha = 1;
+                                  ignored on the northern edge of a latlon band   */
+    const double* beta_iface;  /* host, n_z + 1 values (only interior ones enter) */
+    double lambda2;            /* zero-order coefficient, >= 0 (> 0 for an SPD system with periodic x, y) */
+} pcg_coeffs_t;
+
+typedef struct {
+    int precision;             /* pcg_precision                                   */
+    double inner_tol;          /* PCG_MIXED: relative tolerance of each FP32 inner solve; 0 selects 1e-5 */
+    int inner_maxit;           /* PCG_MIXED: iteration cap of each inner solve; 0 selects 20000 */
+    int max_outer;             /* PCG_MIXED: refinement sweeps cap; 0 selects 16   */
+    int passes_per_launch;     /* PCG passes per CUDA-graph launch between convergence polls; 0 selects 16 */
+    void* stream;              /* cudaStream_t for all work; NULL = default stream */
+} pcg_opts_t;
+
+/* Per-solve statistics.  For nrhs > 1 the scalar fields report the worst
+ * right-hand side; per-rhs values are available from pcg_rhs_stats(). */
+typedef struct {
+    int status;                /* pcg_status of the solve                         */
+    int iterations;            /* FP64: CG iterations (updates of u); MIXED: inner iterations summed over sweeps */
+    int outer_sweeps;          /* MIXED: refinement sweeps taken; FP64: 0         */
+    int stagnated;             /* MIXED: 1 if refinement stopped because the FP64 residual stopped falling */
+    double relres_recursive;   /* FP64: ||r_k||/||b|| of the updated residual at exit */
+    double relres_true;        /* ||b - A x||/||b|| recomputed in FP64 after exit  */
+    double elapsed_ms;         /* wall time of the call on the host               */
+} pcg_stats_t;
+
+/* Create a solver for one grid and coefficient set (Section 4.2: the level
+ * profiles and column metric terms are computed once here and kept on the
+ * device; per-column tridiagonal factors of M are precomputed in FP64).
+ * All inputs are copied.  On failure *out is set to NULL.
+ * Errors: PCG_ERR_INVALID_ARG, PCG_ERR_OOM, PCG_ERR_CUDA. */
+int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opts_t* opts, pcg_t* out);
+
+/* Solve A x = b for all nrhs right-hand sides (Algorithm 1).
+ * b, x: device pointers, FP64, nrhs * n_z * n_y * n_x values; x is the
+ * initial guess on entry and the solution on return.  The stopping test
+ * is ||r_k|| < tol ||b|| on the recursively updated residual (Algorithm 1);
+ * tol = 0 runs exactly maxit iterations.  PCG_MIXED refines in FP64 until
+ * ||b - A x|| < tol ||b|| or the FP64 residual stops falling.  Blocks the
+ * host until the solve has finished; stats may be NULL.
+ * Returns PCG_OK, PCG_NOT_CONVERGED, PCG_BREAKDOWN or an error code. */
+int pcg_solve(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_stats_t* stats);
+
+/* As pcg_solve, with b and x in host memory (pinned or pageable): copies b
+ * and x to the handle's device buffers, solves, copies x back. */
+int pcg_solve_host(pcg_t h, const double* b_host, double* x_host, double tol, int maxit, pcg_stats_t* stats);
+
+/* Statistics of right-hand side `rhs` from the last solve. */
+int pcg_rhs_stats(pcg_t h, int rhs, pcg_stats_t* stats);
+
+/* y = A x (Section 4.2 stencil, flux form), FP64 device pointers, nrhs
+ * vectors.  x and y must not overlap.  Asynchronous on the handle's stream. */
+int pcg_apply_A(pcg_t h, const double* x, double* y);
+
+/* z = M^{-1} r, M = block-diag(A) (Section 4.1; one Thomas solve per
+ * column), FP64 device pointers, nrhs vectors; r and z must not overlap.
+ * Asynchronous on the handle's stream. */
+int pcg_precond(pcg_t h, const double* r, double* z);
+
+/* FP32 versions of the two operators (the kernels of the FP32 inner solve
+ * of PCG_MIXED), FP32 device pointers.  Asynchronous. */
+int pcg_apply_A_f32(pcg_t h, const float* x, float* y);
+int pcg_precond_f32(pcg_t h, const float* r, float* z);
+
+/* Benchmark helper: starting from x0 = 0 on right-hand side b (FP64 device
+ * pointer), run `passes` passes of Algorithm 1 in the FP64 sweeps
+ * (precision = PCG_FP64) or the FP32 inner sweeps (PCG_MIXED), launching each
+ * sweep on its own between CUDA events on the handle's stream, and return
+ * the mean device time per launch of the preconditioner sweep (Algorithm 3)
+ * and of the SpMV sweep (Algorithm 2) in milliseconds.  Uses the handle's
+ * workspace; blocks until done.  Errors: PCG_ERR_INVALID_ARG, PCG_ERR_CUDA. */
+int pcg_time_sweeps(pcg_t h, const double* b, int precision, int passes, double* ms_prec, double* ms_spmv);
+
+/* Block the host until all work enqueued on the handle's stream is done. */
+int pcg_sync(pcg_t h);
+
+/* Device bytes held by the handle (workspace and tables). */
+size_t pcg_device_bytes(pcg_t h);
+
+/* Number of kernels the last solve launched (graph nodes included). */
+long long pcg_kernel_launches(pcg_t h);
+
+/* Text of the last error on this handle (or of the last failed pcg_create
+ * on this thread when h is NULL).  Never NULL. */
+const char* pcg_last_error(pcg_t h);
+
+/* Free everything the handle allocated; caller buffers are untouched. */
+void pcg_destroy(pcg_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCG_GB300_H */

@@ -33,8 +33,9 @@ box     periodic lx x ly rectangle, hx = lx/n_x, hy = ly/n_y:
         mu_E = alpha_e hy/hx, mu_N = alpha_n hx/hy.
 latlon  longitude periodic over 2 pi (dlon = 2 pi/n_x), latitude
         [lat0, lat1] (dlat = (lat1-lat0)/n_y), radius interfaces r_k:
-        |T_j| = dlon (sin lat_{j+1/2} - sin lat_{j-1/2}),
-        d_k = r_{k+1} - r_k, a_k = lambda^2 (r_{k+1}^3 - r_k^3)/3,
+        |T_j| = dlon (sin lat_{j+1/2} - sin lat_{j-1/2}) = 2 dlon cos lat_j sin(dlat/2),
+        d_k = r_{k+1} - r_k, a_k = lambda^2 (r_{k+1}^3 - r_k^3)/3
+            = lambda^2 (r_{k+1} - r_k)(r_{k+1}^2 + r_{k+1} r_k + r_k^2)/3,
         w_{k+1/2} = beta(r_{k+1}) r_{k+1}^2 / (rc_{k+1} - rc_k),
         mu_E(j) = alpha_e dlat / (cos lat_j dlon),
         mu_N(j) = alpha_n cos lat_{j+1/2} dlon / dlat (0 on the northern edge).
@@ -89,9 +90,12 @@ def operator_terms(p: Problem) -> OperatorTerms:
         dlat = (p.lat1 - p.lat0) / p.n_y
         lat_f = p.lat0 + dlat * np.arange(p.n_y + 1)          # faces lat_{j-1/2}, j = 0..n_y
         lat_c = p.lat0 + dlat * (np.arange(p.n_y) + 0.5)       # centres
-        area = dlon * (np.sin(lat_f[1:]) - np.sin(lat_f[:-1]))
+        # sin(a) - sin(b) = 2 cos((a+b)/2) sin((a-b)/2) and
+        # r1^3 - r0^3 = (r1 - r0)(r1^2 + r1 r0 + r0^2): the same quantities
+        # without the cancellation of two nearly equal numbers
+        area = dlon * 2.0 * np.cos(lat_c) * np.sin(0.5 * dlat)
         d = dz.copy()
-        mass = p.lambda2 * (z[1:] ** 3 - z[:-1] ** 3) / 3.0
+        mass = p.lambda2 * dz * (z[1:] * z[1:] + z[1:] * z[:-1] + z[:-1] * z[:-1]) / 3.0
         w_up[:-1] = beta[1:-1] * z[1:-1] ** 2 / gap
         mu_e = ae * (dlat / (np.cos(lat_c) * dlon))[:, None]
         mu_n = an * (np.cos(lat_f[1:]) * dlon / dlat)[:, None]
@@ -111,7 +115,7 @@ def cell_volumes(p: Problem) -> np.ndarray:
     if p.kind == GEOM_BOX:
         vz = z[1:] - z[:-1]
     else:
-        vz = (z[1:] ** 3 - z[:-1] ** 3) / 3.0
+        vz = (z[1:] - z[:-1]) * (z[1:] * z[1:] + z[1:] * z[:-1] + z[:-1] * z[:-1]) / 3.0
     return np.broadcast_to(vz[:, None, None] * t.area[None, :, None], p.shape).copy()
 
 

@@ -10,6 +10,15 @@ order (blocks separated by zero couplings), factors it once with LAPACK's
 partial-pivoting tridiagonal LU (dgttrf) and applies it with dgttrs: the
 GTTRF/GTTRS routines the paper's CPU code used (Section 6.2).  It is a
 different algorithm from the pivot-free Thomas recurrence of the GPU path.
+
+At strong anisotropy a row's diagonal is the sum of two large vertical
+couplings and a much smaller remainder s (the zero-order term plus the
+horizontal couplings); stored in FP64 the diagonal keeps s only to a
+relative accuracy of about eps * W / s, and the LU inherits that error.  The
+solve therefore takes one step of classical iterative refinement with the
+residual r - M z evaluated in flux form,
+    (M z)_k = s_k z_k + W_k (z_k - z_{k+1}) + W_{k-1} (z_k - z_{k-1}),
+which is exact to rounding, so the returned z is M^{-1} r to FP64 accuracy.
 """
 from __future__ import annotations
 
@@ -17,14 +26,26 @@ import numpy as np
 import scipy.linalg.lapack as lapack
 
 from workloads import Problem
-from .discretisation import column_blocks
+from .discretisation import _row_entries, column_blocks, operator_terms
 
 
 class LinePreconditioner:
-    def __init__(self, a, p: Problem):
+    def __init__(self, a, p: Problem, refine_steps: int = 1):
         self.p = p
+        self.refine_steps = refine_steps
         lower, main, upper = column_blocks(a, p)
         self.lower, self.main, self.upper = lower, main, upper
+        # flux form of the column blocks: remainder s and vertical couplings W
+        t = operator_terms(p)
+        kk, jj, ii = np.meshgrid(np.arange(p.n_z), np.arange(p.n_y), np.arange(p.n_x), indexing="ij")
+        cols, vals = _row_entries(p, t, kk.ravel(), jj.ravel(), ii.ravel())
+        own_col = cols[0] % (p.n_x * p.n_y)
+        rem = t.area[jj.ravel()] * t.mass[kk.ravel()]
+        for f in range(1, 5):                       # horizontal neighbours in other columns
+            other = (cols[f] % (p.n_x * p.n_y)) != own_col
+            rem = rem + np.where(other, -vals[f], 0.0)
+        self.s_col = self._to_columns(rem).reshape(-1, p.n_z)
+        self.w_col = self._to_columns(-vals[5]).reshape(-1, p.n_z)     # coupling k -> k+1 (0 at the top)
         # column-contiguous flattening: position c * n_z + k
         dl = lower[:, 1:]          # couplings k -> k-1 for k >= 1
         du = upper[:, :-1]         # couplings k -> k+1 for k <= n_z-2
@@ -54,14 +75,30 @@ class LinePreconditioner:
         nz = self.p.n_z
         return np.ascontiguousarray(v.reshape(-1, nz).T).reshape(self.p.shape)
 
-    def solve(self, r: np.ndarray) -> np.ndarray:
-        """z = M^{-1} r for a canonical-layout vector (any shape with n entries)."""
-        shape = np.shape(r)
-        rc = self._to_columns(r)
+    def _lu_solve(self, rc):
         dl, d, du, du2, ipiv = self._lu
         x, info = lapack.dgttrs(dl, d, du, du2, ipiv, rc)
         if info != 0:
             raise np.linalg.LinAlgError(f"dgttrs failed, info={info}")
+        return x
+
+    def apply_flux(self, zc: np.ndarray) -> np.ndarray:
+        """M z in flux form for a column-contiguous vector."""
+        z = zc.reshape(-1, self.p.n_z)
+        w = self.w_col
+        f = w[:, :-1] * (z[:, :-1] - z[:, 1:])          # flux from level k to k+1
+        y = self.s_col * z
+        y[:, :-1] += f
+        y[:, 1:] -= f
+        return y.ravel()
+
+    def solve(self, r: np.ndarray) -> np.ndarray:
+        """z = M^{-1} r for a canonical-layout vector (any shape with n entries)."""
+        shape = np.shape(r)
+        rc = self._to_columns(r)
+        x = self._lu_solve(rc)
+        for _ in range(self.refine_steps):
+            x = x + self._lu_solve(rc - self.apply_flux(x))
         return self._from_columns(x).reshape(shape)
 
     def __call__(self, r):

@@ -1,0 +1,584 @@
+// Device kernels of the matrix-free line-preconditioned CG solver (sm_103a).
+//
+// Data layout: every vector is [nrhs][n_z][n_y][n_x] with x fastest, so a
+// vertical level is one contiguous horizontal plane and a warp of threads
+// that own neighbouring columns reads 32 consecutive values per level
+// (the coalescing argument of Section 6.1, Eq. (MemoryMappingCUDAC)).
+//
+// Parallelisation: one thread per vertical column for the kernels that carry
+// the vertical recurrence of the Thomas algorithm (Section 6.1: the line
+// solve is sequential in the vertical); threads are grouped in 32 x 4 tiles
+// of columns.  The k-loop keeps the column's current, next and previous
+// values and the running vertical flux in registers.
+//
+// Operator (Section 3.1, Eq. (TridiagonalMatrix), Section 4.2 stencil) in
+// flux form:
+//   (A z)_{ijk} = |T_j| ( m_k z_k + F_k - F_{k-1} ) + d_k sum_f mu_f (z_k - z_f),
+//   F_k = w_k (z_k - z_{k+1})   (w_{n_z-1} = 0: Neumann top; F_{-1} = 0: Neumann bottom).
+// Each flux is computed once and enters rows k and k+1 with opposite signs,
+// and every neighbour enters through an exact difference, so A 1 = |T| m
+// exactly and near-constant vectors lose no precision to cancellation.
+//
+// Preconditioner (Section 4.1, Eq. (MatrixFreeTridiagonalSystem)): per
+// column M = L D L^T with pivots D_k = W_k + E_k (W_k = |T| w_k the coupling
+// to level k+1, E_k >= 0 the pivot's excess over it).  With precomputed
+// g_k = 1/D_k and E_k the two Thomas sweeps read
+//   forward:  y_k = (r_k - e_{k-1} y_{k-1}) + y_{k-1},   e = E g  (= 1 - W/D),
+//   backward: z_k = z_{k+1} + g_k (y_k - E_k z_{k+1}),
+// which is the textbook recurrence y_k = r_k + (W/D) y_{k-1},
+// z_k = (y_k + W_k z_{k+1})/D_k written so that the small excesses are never
+// added to or subtracted from the large couplings: at strong anisotropy W/D
+// rounds to 1 in FP32 and the column's near-constant mode would be lost.
+// <r, M^{-1} r> = sum_k g_k y_k^2 is accumulated in the forward sweep.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pcg {
+
+constexpr int BX = 32;
+constexpr int BY = 4;
+constexpr int NT = BX * BY;
+
+// Per right-hand-side scalar state of one PCG solve (Algorithm 1).
+struct SolveState {
+    double alpha;       // step length of the last SpMV sweep (0 before the first)
+    double beta;        // kappa / kappa_old of the last preconditioner sweep
+    double kappa_old;   // <r, z> of the previous pass (1 before the first)
+    double sigma;       // <p, q> of the last SpMV sweep
+    double rr;          // <r, r> of the last preconditioner sweep
+    double kappa;       // <r, z> of the last preconditioner sweep
+    double bnorm2;      // <b, b>
+    double thresh2;     // stop when rr < thresh2 (= tol^2 <b, b>)
+    double tol2;        // tol^2 as requested
+    double rr_true;     // <b - A x, b - A x> after the solve
+    double rsum;        // sum_i (b - A x)_i (refinement: constant-mode projection)
+    double coarse;      // constant added to x by the refinement's coarse correction
+    double rr_emit;     // <r', r'> of the inner right-hand side r' = b - A x - coarse A 1
+    int done;           // 1 once the solve of this rhs has stopped
+    int status;         // pcg_status of this rhs
+    int pass;           // preconditioner sweeps completed
+    int maxit;          // iteration cap
+    int zero_rhs;       // b == 0: the solution is 0
+    int pad_;
+};
+
+// Read-only view of the operator tables in precision T.
+template <typename T>
+struct OpView {
+    int nx, ny, nz;
+    long long plane;            // nx * ny
+    long long vol;              // plane * nz (one right-hand side)
+    const T* mass;              // [nz] zero-order term per unit area
+    const T* wv;                // [nz] vertical coupling per unit area between k and k+1 (0 at the top)
+    const T* dk;                // [nz] weight of the horizontal couplings per level
+    const T* area;              // [ny] |T_j|
+    const T* mue;               // [ny][nx] east-face weight
+    const T* mun;               // [ny][nx] north-face weight (0 on a Neumann edge)
+    int periodic_y;
+    const T* fg;                // [nz][ncls] 1 / D_k
+    const T* fe;                // [nz][ncls] E_k = D_k - W_k
+    int cls_mode;               // 0: one factor set; 1: per row j; 2: per column
+    int ncls;
+};
+
+// Per-thread accumulators: plain FP64, or compensated FP32 (exact product
+// error by FMA, TwoSum accumulation) converted to FP64 at the end.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        float p = a * b;
+        float pe = fmaf(a, b, -p);
+        float t = s + p;
+        float bp = t - s;
+        float e = (s - (t - bp)) + (p - bp);
+        s = t;
+        c += e + pe;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <typename T>
+__device__ __forceinline__ T ldro(const T* p) { return __ldg(p); }
+
+// Geometry of one column: neighbour offsets within a plane and face weights.
+template <typename T>
+struct Col {
+    long long c, ce, cw, cn, cs;
+    T area, me, mw, mn, ms;
+    int cls;
+    bool valid;
+};
+
+template <typename T>
+__device__ __forceinline__ Col<T> make_col(const OpView<T>& op, int i, int j) {
+    Col<T> col;
+    col.valid = (i < op.nx) && (j < op.ny);
+    const int ii = col.valid ? i : 0;
+    const int jj = col.valid ? j : 0;
+    const int ie = (ii + 1 == op.nx) ? 0 : ii + 1;
+    const int iw = (ii == 0) ? op.nx - 1 : ii - 1;
+    int jn, js;
+    if (op.periodic_y) {
+        jn = (jj + 1 == op.ny) ? 0 : jj + 1;
+        js = (jj == 0) ? op.ny - 1 : jj - 1;
+    } else {
+        jn = (jj + 1 == op.ny) ? jj : jj + 1;   // weight is 0 there
+        js = (jj == 0) ? jj : jj - 1;
+    }
+    const long long nx = op.nx;
+    col.c = (long long)jj * nx + ii;
+    col.ce = (long long)jj * nx + ie;
+    col.cw = (long long)jj * nx + iw;
+    col.cn = (long long)jn * nx + ii;
+    col.cs = (long long)js * nx + ii;
+    col.area = ldro(op.area + jj);
+    col.me = ldro(op.mue + col.c);
+    col.mw = ldro(op.mue + col.cw);
+    col.mn = ldro(op.mun + col.c);
+    col.ms = (op.periodic_y || jj > 0) ? ldro(op.mun + col.cs) : T(0);
+    col.cls = op.cls_mode == 0 ? 0 : (op.cls_mode == 1 ? jj : (int)col.c);
+    return col;
+}
+
+// Horizontal part sum_f mu_f (z_c - z_f) at one level; zl points at the plane.
+template <typename T>
+__device__ __forceinline__ T horiz(const Col<T>& col, const T* __restrict__ zl, T zc) {
+    T a = col.me * (zc - ldro(zl + col.ce));
+    a = fma(col.mw, zc - ldro(zl + col.cw), a);
+    a = fma(col.mn, zc - ldro(zl + col.cn), a);
+    a = fma(col.ms, zc - ldro(zl + col.cs), a);
+    return a;
+}
+
+// ---------------------------------------------------------------------------
+// Block / grid reductions with a deterministic order.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[NT / 32]) {
+    const int tid = threadIdx.y * BX + threadIdx.x;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        double a = v[n];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if ((tid & 31) == 0) sh[n][tid >> 5] = a;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            double a = 0.0;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) a += sh[n][w];
+            v[n] = a;
+        }
+    }
+}
+
+// Each block stores its N partial sums; the last block to arrive sums all
+// partials of its right-hand side in block order and returns true on thread 0
+// (with the totals in v).  Other threads of the last block return false.
+template <int N>
+__device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsigned* counter, int nblocks) {
+    __shared__ double sh[N][NT / 32];
+    __shared__ bool am_last;
+    __shared__ double tot[N][NT / 32];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum<N>(v, sh);
+    if (tid == 0) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) partials[(long long)bid * N + n] = v[n];
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        am_last = (prev == (unsigned)nblocks - 1u);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    double acc[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) acc[n] = 0.0;
+    for (int b = tid; b < nblocks; b += NT) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) acc[n] += __ldcg(partials + (long long)b * N + n);
+    }
+    __syncthreads();
+    block_sum<N>(acc, tot);
+    if (tid == 0) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) v[n] = acc[n];
+        *counter = 0u;
+    }
+    return tid == 0;
+}
+
+// ---------------------------------------------------------------------------
+// y = A x
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ __launch_bounds__(NT) void k_apply(OpView<T> op, const T* __restrict__ x, T* __restrict__ y) {
+    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+    if (!col.valid) return;
+    const long long base = (long long)blockIdx.z * op.vol;
+    const T* __restrict__ xb = x + base;
+    T* __restrict__ yb = y + base;
+    T zc = xb[col.c];
+    T fprev = T(0);
+#pragma unroll 4
+    for (int k = 0; k < op.nz; ++k) {
+        const T* xl = xb + (long long)k * op.plane;
+        const T zu = (k + 1 < op.nz) ? ldro(xl + op.plane + col.c) : zc;
+        const T f = ldro(op.wv + k) * (zc - zu);
+        const T hz = horiz(col, xl, zc);
+        yb[(long long)k * op.plane + col.c] =
+            fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+        fprev = f;
+        zc = zu;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z = M^{-1} r (one Thomas solve per column)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ __launch_bounds__(NT) void k_precond(OpView<T> op, const T* __restrict__ r, T* __restrict__ z) {
+    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+    if (!col.valid) return;
+    const long long base = (long long)blockIdx.z * op.vol;
+    const T* rb = r + base;
+    T* zb = z + base;
+    const T* fg = op.fg + col.cls;
+    const T* fe = op.fe + col.cls;
+    const long long fs = op.ncls;
+    T y = T(0), eprev = T(0);
+#pragma unroll 4
+    for (int k = 0; k < op.nz; ++k) {
+        y = fma(-eprev, y, rb[(long long)k * op.plane + col.c]) + y;
+        zb[(long long)k * op.plane + col.c] = y;
+        eprev = ldro(fe + k * fs) * ldro(fg + k * fs);
+    }
+    T zn = T(0);
+#pragma unroll 4
+    for (int k = op.nz - 1; k >= 0; --k) {
+        const long long o = (long long)k * op.plane + col.c;
+        zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, zb[o]), zn);
+        zb[o] = zn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioner sweep of Algorithm 1 (Algorithm 3): r <- r - alpha q,
+// <r, r>, z = M^{-1} r, kappa = <r, z>; the last block applies the stopping
+// test and forms beta = kappa / kappa_old.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__ r, const T* __restrict__ q,
+                                                   T* __restrict__ z, SolveState* __restrict__ states,
+                                                   double* __restrict__ partials, unsigned* __restrict__ counters,
+                                                   int nblocks) {
+    const int rhs = blockIdx.z;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const T alpha = (T)st->alpha;
+    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+    Acc<T> rr, kap;
+    if (col.valid) {
+        const long long base = (long long)rhs * op.vol + col.c;
+        T* rb = r + base;
+        const T* qb = q + base;
+        T* zb = z + base;
+        const T* fg = op.fg + col.cls;
+        const T* fe = op.fe + col.cls;
+        const long long fs = op.ncls;
+        T y = T(0), eprev = T(0);
+#pragma unroll 4
+        for (int k = 0; k < op.nz; ++k) {
+            const long long o = (long long)k * op.plane;
+            const T rn = fma(-alpha, qb[o], rb[o]);
+            rb[o] = rn;
+            rr.add_prod(rn, rn);
+            y = fma(-eprev, y, rn) + y;
+            zb[o] = y;
+            const T g = ldro(fg + k * fs);
+            kap.add_prod(g * y, y);
+            eprev = ldro(fe + k * fs) * g;
+        }
+        T zn = T(0);
+#pragma unroll 4
+        for (int k = op.nz - 1; k >= 0; --k) {
+            const long long o = (long long)k * op.plane;
+            zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, zb[o]), zn);
+            zb[o] = zn;
+        }
+    }
+    double v[2] = {rr.value(), kap.value()};
+    if (grid_sum<2>(v, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks)) {
+        const double rrv = v[0], kv = v[1];
+        st->rr = rrv;
+        st->kappa = kv;
+        st->pass += 1;
+        if (!(isfinite(rrv) && isfinite(kv)) || kv < 0.0) {
+            st->done = 1;
+            st->status = 5;   // PCG_BREAKDOWN
+        } else if (rrv == 0.0 || rrv < st->thresh2) {
+            st->done = 1;
+            st->status = 0;   // PCG_OK
+        } else if (st->pass > st->maxit) {
+            st->done = 1;
+            st->status = 4;   // PCG_NOT_CONVERGED
+        } else {
+            st->beta = kv / st->kappa_old;
+            st->kappa_old = kv;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SpMV sweep of Algorithm 1 (Algorithm 2): u <- u + alpha p, p <- z + beta p,
+// q <- A z + beta q, sigma = <p, q>; the last block forms alpha = kappa_old/sigma.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__ u, T* __restrict__ p,
+                                                   T* __restrict__ q, const T* __restrict__ z,
+                                                   SolveState* __restrict__ states, double* __restrict__ partials,
+                                                   unsigned* __restrict__ counters, int nblocks) {
+    const int rhs = blockIdx.z;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const T alpha = (T)st->alpha;
+    const T beta = (T)st->beta;
+    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+    Acc<T> sig;
+    if (col.valid) {
+        const long long base = (long long)rhs * op.vol;
+        const T* __restrict__ zb = z + base;
+        T* ub = u + base + col.c;
+        T* pb = p + base + col.c;
+        T* qb = q + base + col.c;
+        T zc = zb[col.c];
+        T fprev = T(0);
+#pragma unroll 4
+        for (int k = 0; k < op.nz; ++k) {
+            const long long o = (long long)k * op.plane;
+            const T* zl = zb + o;
+            const T zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
+            const T pk = pb[o];
+            const T qk = qb[o];
+            ub[o] = fma(alpha, pk, ub[o]);
+            const T pn = fma(beta, pk, zc);
+            pb[o] = pn;
+            const T f = ldro(op.wv + k) * (zc - zu);
+            const T hz = horiz(col, zl, zc);
+            const T az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+            const T qn = fma(beta, qk, az);
+            qb[o] = qn;
+            sig.add_prod(pn, qn);
+            fprev = f;
+            zc = zu;
+        }
+    }
+    double v[1] = {sig.value()};
+    if (grid_sum<1>(v, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks)) {
+        const double s = v[0];
+        st->sigma = s;
+        if (!(s > 0.0) || !isfinite(s)) {
+            st->done = 1;
+            st->status = 5;   // PCG_BREAKDOWN
+            st->alpha = 0.0;
+        } else {
+            st->alpha = st->kappa_old / s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual r = b - A x in FP64, with reductions of <b,b>, <r,r> and sum(r).
+// mode 0: start of an FP64 solve: also u = x, writes r; sets the stopping threshold.
+// mode 1: true residual after a solve: writes nothing, stores rr_true.
+// mode 2: refinement, measure: writes nothing, stores bnorm2, rr and rsum.
+// mode 3: refinement, emit: writes r' = b - A x - coarse * m (the inner
+//         right-hand side, in TO) and stores <r', r'> in rr_emit.
+// ---------------------------------------------------------------------------
+template <typename TO>
+__global__ __launch_bounds__(NT) void k_residual(OpView<double> op, const double* __restrict__ b,
+                                                 const double* __restrict__ x, double* __restrict__ u,
+                                                 TO* __restrict__ rout, SolveState* __restrict__ states,
+                                                 double* __restrict__ partials, unsigned* __restrict__ counters,
+                                                 int nblocks, int mode) {
+    const int rhs = blockIdx.z;
+    SolveState* st = states + rhs;
+    const Col<double> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+    const double coarse = (mode == 3) ? st->coarse : 0.0;
+    double bb = 0.0, rr = 0.0, rs = 0.0;
+    if (col.valid) {
+        const long long base = (long long)rhs * op.vol;
+        const double* __restrict__ xb = x + base;
+        const double* __restrict__ bbp = b + base + col.c;
+        double zc = xb[col.c];
+        double fprev = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < op.nz; ++k) {
+            const long long o = (long long)k * op.plane;
+            const double* xl = xb + o;
+            const double zu = (k + 1 < op.nz) ? ldro(xl + op.plane + col.c) : zc;
+            const double f = ldro(op.wv + k) * (zc - zu);
+            const double hz = horiz(col, xl, zc);
+            const double cm = col.area * ldro(op.mass + k);
+            const double az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+            const double bv = bbp[o];
+            const double rv = fma(-coarse, cm, bv - az);
+            bb = fma(bv, bv, bb);
+            rr = fma(rv, rv, rr);
+            rs += rv;
+            if (mode == 0) u[base + o + col.c] = zc;
+            if (mode == 0 || mode == 3) rout[base + o + col.c] = (TO)rv;
+            fprev = f;
+            zc = zu;
+        }
+    }
+    double v[3] = {bb, rr, rs};
+    if (grid_sum<3>(v, partials + (long long)rhs * nblocks * 3, counters + rhs, nblocks)) {
+        if (mode == 0) {
+            st->bnorm2 = v[0];
+            st->rr = v[1];
+            st->thresh2 = st->tol2 * v[0];
+            if (v[0] == 0.0) {
+                st->zero_rhs = 1;
+                st->done = 1;
+                st->status = 0;
+            }
+        } else if (mode == 1) {
+            st->rr_true = v[1];
+        } else if (mode == 2) {
+            st->bnorm2 = v[0];
+            st->rr = v[1];
+            st->rsum = v[2];
+        } else {
+            st->rr_emit = v[1];
+        }
+    }
+}
+
+// Initialise the scalar state of nrhs solves.
+__global__ void k_init_state(SolveState* states, int nrhs, double tol2, int maxit, const int* active) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    SolveState s;
+    s.alpha = 0.0;
+    s.beta = 0.0;
+    s.kappa_old = 1.0;
+    s.sigma = 0.0;
+    s.rr = 0.0;
+    s.kappa = 0.0;
+    s.bnorm2 = 0.0;
+    s.thresh2 = 0.0;
+    s.tol2 = tol2;
+    s.rr_true = 0.0;
+    s.done = active ? (active[r] ? 0 : 1) : 0;
+    s.status = 0;
+    s.pass = 0;
+    s.maxit = maxit;
+    s.zero_rhs = 0;
+    s.rsum = 0.0;
+    s.coarse = 0.0;
+    s.rr_emit = 0.0;
+    s.pad_ = 0;
+    states[r] = s;
+}
+
+// Inner-solve thresholds from the refinement residual: thresh2 = tol_in^2 <r', r'>.
+__global__ void k_inner_thresholds(SolveState* inner, const SolveState* outer, int nrhs, double tol_in2) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    inner[r].thresh2 = tol_in2 * outer[r].rr_emit;
+    inner[r].bnorm2 = outer[r].rr_emit;
+}
+
+// Coarse correction of one refinement sweep: the Galerkin projection of the
+// residual onto the constant vector, c = sum(r) / sum(A 1) (A 1 is the mass
+// vector exactly), so that the inner solve sees a residual orthogonal to 1.
+__global__ void k_coarse(SolveState* states, int nrhs, double total_mass) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    states[r].coarse = total_mass > 0.0 ? states[r].rsum / total_mass : 0.0;
+}
+
+// Final update of an FP64 solve: x = u + alpha p (x = 0 for a zero right-hand side).
+__global__ __launch_bounds__(NT) void k_finish(int nx, int ny, int nz, long long plane, long long vol,
+                                               double* __restrict__ x, const double* __restrict__ u,
+                                               const double* __restrict__ p, const SolveState* __restrict__ states) {
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const SolveState* st = states + blockIdx.z;
+    const double alpha = st->alpha;
+    const bool zero = st->zero_rhs != 0;
+    const long long base = (long long)blockIdx.z * vol + (long long)j * nx + i;
+    for (int k = 0; k < nz; ++k) {
+        const long long o = base + (long long)k * plane;
+        x[o] = zero ? 0.0 : fma(alpha, p[o], u[o]);
+    }
+}
+
+// Refinement update x += coarse + u + alpha p (the coarse correction, the
+// inner FP32 iterate and the deferred last step of Algorithm 1), for
+// right-hand sides whose inner solve ran.
+__global__ __launch_bounds__(NT) void k_refine_update(int nx, int ny, int nz, long long plane, long long vol,
+                                                      double* __restrict__ x, const float* __restrict__ u,
+                                                      const float* __restrict__ p, const SolveState* __restrict__ inner,
+                                                      const SolveState* __restrict__ outer, const int* __restrict__ active) {
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    if (!active[blockIdx.z]) return;
+    const double alpha = inner[blockIdx.z].alpha;
+    const double coarse = outer[blockIdx.z].coarse;
+    const long long base = (long long)blockIdx.z * vol + (long long)j * nx + i;
+    for (int k = 0; k < nz; ++k) {
+        const long long o = base + (long long)k * plane;
+        x[o] = fma(alpha, (double)p[o], (x[o] + coarse) + (double)u[o]);
+    }
+}
+
+// Thomas factors of M for every factor class, in FP64, carrying the pivot as
+// W_k + E_k with the excess E_k = s_k + W_{k-1} E_{k-1} / D_{k-1} >= 0
+// (s_k: zero-order plus horizontal-diagonal part of row k).  No term is
+// subtracted, so the pivots keep full relative accuracy however small s_k is
+// next to the vertical couplings.
+__global__ void k_factors(OpView<double> op, double* __restrict__ fg, double* __restrict__ fe) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= op.ncls) return;
+    int i = 0, j = 0;
+    if (op.cls_mode == 1) j = c;
+    if (op.cls_mode == 2) { i = c % op.nx; j = c / op.nx; }
+    const Col<double> col = make_col(op, i, j);
+    // a face whose neighbour is the column itself (one cell across a periodic
+    // axis) couples the column to itself and is not part of its block
+    const double musum = ((col.ce != col.c ? col.me : 0.0) + (col.cw != col.c ? col.mw : 0.0)) +
+                         ((col.cn != col.c ? col.mn : 0.0) + (col.cs != col.c ? col.ms : 0.0));
+    double e = 0.0, wprev = 0.0, dprev = 1.0;
+    for (int k = 0; k < op.nz; ++k) {
+        const double s = col.area * op.mass[k] + op.dk[k] * musum;
+        const double w = col.area * op.wv[k];
+        e = (k == 0) ? s : s + wprev * (e / dprev);
+        const double d = w + e;
+        fg[(long long)k * op.ncls + c] = 1.0 / d;
+        fe[(long long)k * op.ncls + c] = e;
+        wprev = w;
+        dprev = d;
+    }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) b[i] = (float)a[i];
+}
+
+}  // namespace pcg

@@ -1,0 +1,716 @@
+// C-ABI implementation of the GB300 line-preconditioned CG solver.
+//
+// Host side: builds the operator tables of the finite-volume scheme
+// (Section 3.1: per-level profiles shared by every column, per-column metric
+// terms), owns the device workspace, and drives Algorithm 1 (Section 4.3) as
+// CUDA graphs of `passes_per_launch` pairs of fused sweeps.  All scalars of
+// the iteration live on the device; the host only polls the per-rhs `done`
+// flags between graph launches (two launches are kept in flight so the GPU
+// never waits for the poll).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pcg.h"
+#include "kernels.cuh"
+
+using pcg::BX;
+using pcg::BY;
+using pcg::OpView;
+using pcg::SolveState;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct DevTables {
+    void* base = nullptr;       // one allocation for all tables of one precision
+    void* mass = nullptr;
+    void* wv = nullptr;
+    void* dk = nullptr;
+    void* area = nullptr;
+    void* mue = nullptr;
+    void* mun = nullptr;
+    void* fg = nullptr;
+    void* fe = nullptr;
+};
+
+}  // namespace
+
+struct pcg_ctx {
+    int geometry = 0, nx = 0, ny = 0, nz = 0, nrhs = 1;
+    long long plane = 0, vol = 0, ntot = 0;
+    int periodic_y = 1;
+    int cls_mode = 0, ncls = 1;
+    int precision = PCG_FP64;
+    double inner_tol = 1e-5;
+    int inner_maxit = 20000, max_outer = 16, ppl = 16;
+    int trace = 0;                        // PCG_TRACE=1: print the refinement history to stderr
+    double total_mass = 0.0;              // sum over cells of |T| a_k = sum(A 1) per right-hand side
+    cudaStream_t stream = nullptr;        // user stream (may be the default stream)
+    cudaStream_t cap_stream = nullptr;    // private stream used only for graph capture
+
+    DevTables t64, t32;
+
+    // workspace
+    double *u64 = nullptr, *r64 = nullptr, *z64 = nullptr, *p64 = nullptr, *q64 = nullptr;
+    float *u32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    double *hb = nullptr, *hx = nullptr;  // device staging for pcg_solve_host
+    SolveState* st = nullptr;              // [nrhs] outer / FP64 state
+    SolveState* st_in = nullptr;           // [nrhs] inner FP32 state
+    SolveState* h_st = nullptr;            // pinned [2][nrhs] poll slots
+    int* d_active = nullptr;               // [nrhs]
+    double* partials = nullptr;            // [nrhs][nblocks][3]
+    unsigned* counters = nullptr;          // [nrhs]
+    int nblocks = 0;
+    dim3 grid, block;
+
+    cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+
+    size_t bytes = 0;
+    long long launches = 0;
+    std::vector<pcg_stats_t> rhs_stats;
+    std::string err = "no error";
+
+    OpView<double> view64() const { return view<double>(t64); }
+    OpView<float> view32() const { return view<float>(t32); }
+
+    template <typename T>
+    OpView<T> view(const DevTables& t) const {
+        OpView<T> v;
+        v.nx = nx;
+        v.ny = ny;
+        v.nz = nz;
+        v.plane = plane;
+        v.vol = vol;
+        v.mass = (const T*)t.mass;
+        v.wv = (const T*)t.wv;
+        v.dk = (const T*)t.dk;
+        v.area = (const T*)t.area;
+        v.mue = (const T*)t.mue;
+        v.mun = (const T*)t.mun;
+        v.periodic_y = periodic_y;
+        v.fg = (const T*)t.fg;
+        v.fe = (const T*)t.fe;
+        v.cls_mode = cls_mode;
+        v.ncls = ncls;
+        return v;
+    }
+};
+
+namespace {
+
+int fail(pcg_t h, int code, const std::string& msg) {
+    if (h) h->err = msg; else g_create_error = msg;
+    return code;
+}
+
+#define PCG_CK(h, call)                                                                       \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            int code_ = (e_ == cudaErrorMemoryAllocation) ? PCG_ERR_OOM : PCG_ERR_CUDA;       \
+            return fail(h, code_, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+        }                                                                                     \
+    } while (0)
+
+template <typename T>
+int dmalloc(pcg_t h, T** p, size_t count) {
+    size_t b = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, b);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(h, e == cudaErrorMemoryAllocation ? PCG_ERR_OOM : PCG_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->bytes += b;
+    return PCG_OK;
+}
+
+// Host computation of the operator tables (Section 3.1; Section 4.2 stores
+// per-level vectors once and per-column metric terms once per column).
+struct HostTables {
+    std::vector<double> mass, wv, dk, area, mue, mun;
+};
+
+int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t) {
+    const int nx = g->n_x, ny = g->n_y, nz = g->n_z;
+    const double* z = g->z_iface;
+    const double* beta = c->beta_iface;
+    t.mass.assign(nz, 0.0);
+    t.wv.assign(nz, 0.0);
+    t.dk.assign(nz, 0.0);
+    t.area.assign(ny, 0.0);
+    t.mue.assign((size_t)nx * ny, 0.0);
+    t.mun.assign((size_t)nx * ny, 0.0);
+    for (int k = 0; k <= nz; ++k) {
+        if (!std::isfinite(z[k]) || !std::isfinite(beta[k])) return fail(h, PCG_ERR_INVALID_ARG, "non-finite z_iface or beta_iface");
+        if (k > 0 && !(z[k] > z[k - 1])) return fail(h, PCG_ERR_INVALID_ARG, "z_iface must be strictly increasing");
+    }
+    auto centre = [&](int k) { return 0.5 * (z[k] + z[k + 1]); };
+    if (g->geometry == PCG_GEOM_BOX) {
+        if (!(g->lx > 0.0) || !(g->ly > 0.0)) return fail(h, PCG_ERR_INVALID_ARG, "box extents must be positive");
+        const double hx = g->lx / nx, hy = g->ly / ny;
+        for (int k = 0; k < nz; ++k) {
+            const double dz = z[k + 1] - z[k];
+            t.mass[k] = c->lambda2 * dz;
+            t.dk[k] = dz;
+            t.wv[k] = (k + 1 < nz) ? beta[k + 1] / (centre(k + 1) - centre(k)) : 0.0;
+        }
+        for (int j = 0; j < ny; ++j) t.area[j] = hx * hy;
+        for (size_t idx = 0; idx < (size_t)nx * ny; ++idx) {
+            const double ae = c->alpha_e ? c->alpha_e[idx] : 1.0;
+            const double an = c->alpha_n ? c->alpha_n[idx] : 1.0;
+            t.mue[idx] = ae * (hy / hx);
+            t.mun[idx] = an * (hx / hy);
+        }
+    } else if (g->geometry == PCG_GEOM_LATLON) {
+        const double pi = 3.14159265358979323846;
+        if (!(g->lat0 > -0.5 * pi && g->lat1 < 0.5 * pi && g->lat0 < g->lat1))
+            return fail(h, PCG_ERR_INVALID_ARG, "latitude band must satisfy -pi/2 < lat0 < lat1 < pi/2");
+        const double dlon = 2.0 * pi / nx, dlat = (g->lat1 - g->lat0) / ny;
+        for (int k = 0; k < nz; ++k) {
+            // shell volume per unit solid angle, (r1^3 - r0^3)/3 without cancellation
+            const double r0 = z[k], r1 = z[k + 1];
+            t.mass[k] = c->lambda2 * ((r1 - r0) * (r1 * r1 + r1 * r0 + r0 * r0)) / 3.0;
+            t.dk[k] = r1 - r0;
+            t.wv[k] = (k + 1 < nz) ? beta[k + 1] * r1 * r1 / (centre(k + 1) - centre(k)) : 0.0;
+        }
+        for (int j = 0; j < ny; ++j) {
+            const double ln = g->lat0 + (j + 1) * dlat, lc = g->lat0 + (j + 0.5) * dlat;
+            // dlon (sin ln - sin ls) written as 2 dlon cos(lc) sin(dlat/2): no cancellation
+            t.area[j] = dlon * 2.0 * std::cos(lc) * std::sin(0.5 * dlat);
+            for (int i = 0; i < nx; ++i) {
+                const size_t idx = (size_t)j * nx + i;
+                const double ae = c->alpha_e ? c->alpha_e[idx] : 1.0;
+                const double an = c->alpha_n ? c->alpha_n[idx] : 1.0;
+                t.mue[idx] = ae * dlat / (std::cos(lc) * dlon);
+                t.mun[idx] = (j + 1 < ny) ? an * std::cos(ln) * dlon / dlat : 0.0;
+            }
+        }
+    } else {
+        return fail(h, PCG_ERR_INVALID_ARG, "unknown geometry");
+    }
+    // sum over all cells of |T_j| a_k = sum_i (A 1)_i, the Galerkin coarse operator on the constant vector
+    double sa = 0.0, sm = 0.0;
+    for (int j = 0; j < ny; ++j) sa += t.area[j];
+    for (int k = 0; k < nz; ++k) sm += t.mass[k];
+    h->total_mass = (double)nx * sa * sm;
+    return PCG_OK;
+}
+
+int upload_tables(pcg_t h, const HostTables& t) {
+    const size_t nz = h->nz, ny = h->ny, nxy = (size_t)h->nx * h->ny, nf = (size_t)nz * h->ncls;
+    const size_t n64 = 3 * nz + ny + 2 * nxy + 2 * nf;
+    double* b64 = nullptr;
+    float* b32 = nullptr;
+    int rc = dmalloc(h, &b64, n64);
+    if (rc) return rc;
+    rc = dmalloc(h, &b32, n64);
+    if (rc) return rc;
+    h->t64.base = b64;
+    h->t32.base = b32;
+    size_t off = 0;
+    auto carve = [&](size_t n, void*& p64, void*& p32) {
+        p64 = b64 + off;
+        p32 = b32 + off;
+        off += n;
+    };
+    carve(nz, h->t64.mass, h->t32.mass);
+    carve(nz, h->t64.wv, h->t32.wv);
+    carve(nz, h->t64.dk, h->t32.dk);
+    carve(ny, h->t64.area, h->t32.area);
+    carve(nxy, h->t64.mue, h->t32.mue);
+    carve(nxy, h->t64.mun, h->t32.mun);
+    carve(nf, h->t64.fg, h->t32.fg);
+    carve(nf, h->t64.fe, h->t32.fe);
+    cudaStream_t s = h->stream;
+    PCG_CK(h, cudaMemcpyAsync(h->t64.mass, t.mass.data(), nz * 8, cudaMemcpyHostToDevice, s));
+    PCG_CK(h, cudaMemcpyAsync(h->t64.wv, t.wv.data(), nz * 8, cudaMemcpyHostToDevice, s));
+    PCG_CK(h, cudaMemcpyAsync(h->t64.dk, t.dk.data(), nz * 8, cudaMemcpyHostToDevice, s));
+    PCG_CK(h, cudaMemcpyAsync(h->t64.area, t.area.data(), ny * 8, cudaMemcpyHostToDevice, s));
+    PCG_CK(h, cudaMemcpyAsync(h->t64.mue, t.mue.data(), nxy * 8, cudaMemcpyHostToDevice, s));
+    PCG_CK(h, cudaMemcpyAsync(h->t64.mun, t.mun.data(), nxy * 8, cudaMemcpyHostToDevice, s));
+    // Thomas factors of every class, in FP64 on the device
+    const OpView<double> v = h->view64();
+    pcg::k_factors<<<(h->ncls + 127) / 128, 128, 0, s>>>(v, (double*)h->t64.fg, (double*)h->t64.fe);
+    PCG_CK(h, cudaGetLastError());
+    const long long nconv = (long long)n64;
+    pcg::k_to_float<<<1024, 256, 0, s>>>(b64, b32, nconv);
+    PCG_CK(h, cudaGetLastError());
+    PCG_CK(h, cudaStreamSynchronize(s));
+    return PCG_OK;
+}
+
+int ensure_ws64(pcg_t h) {
+    if (h->u64) return PCG_OK;
+    int rc;
+    for (double** p : {&h->u64, &h->r64, &h->z64, &h->p64, &h->q64})
+        if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
+    return PCG_OK;
+}
+
+int ensure_ws32(pcg_t h) {
+    if (h->u32) return PCG_OK;
+    int rc;
+    for (float** p : {&h->u32, &h->r32, &h->z32, &h->p32, &h->q32})
+        if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
+    return PCG_OK;
+}
+
+// Capture `ppl` passes of Algorithm 1 (preconditioner sweep + SpMV sweep).
+template <typename T>
+int capture_passes(pcg_t h, OpView<T> v, T* u, T* r, T* z, T* p, T* q, SolveState* st, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    PCG_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < h->ppl; ++i) {
+        pcg::k_sweep_prec<T><<<h->grid, h->block, 0, h->cap_stream>>>(v, r, q, z, st, h->partials, h->counters, h->nblocks);
+        pcg::k_sweep_spmv<T><<<h->grid, h->block, 0, h->cap_stream>>>(v, u, p, q, z, st, h->partials, h->counters, h->nblocks);
+    }
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess) return fail(h, PCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, PCG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return PCG_OK;
+}
+
+// Run passes until every rhs is done (or `max_launch` graph launches).
+// Two graph launches are kept in flight; after each, the per-rhs states are
+// copied to a pinned slot and polled when the launch's event completes.
+int run_graph(pcg_t h, cudaGraphExec_t graph, SolveState* st, long long max_launch) {
+    const size_t sb = sizeof(SolveState) * h->nrhs;
+    long long issued = 0, polled = 0;
+    bool all_done = false;
+    auto issue = [&](long long n) -> int {
+        PCG_CK(h, cudaGraphLaunch(graph, h->stream));
+        PCG_CK(h, cudaMemcpyAsync(h->h_st + (n & 1) * h->nrhs, st, sb, cudaMemcpyDeviceToHost, h->stream));
+        PCG_CK(h, cudaEventRecord(h->ev[n & 1], h->stream));
+        h->launches += 2LL * h->ppl;
+        return PCG_OK;
+    };
+    int rc;
+    if ((rc = issue(issued++))) return rc;
+    while (!all_done && polled < max_launch) {
+        if (issued < max_launch && issued == polled + 1)
+            if ((rc = issue(issued++))) return rc;
+        PCG_CK(h, cudaEventSynchronize(h->ev[polled & 1]));
+        const SolveState* s = h->h_st + (polled & 1) * h->nrhs;
+        all_done = true;
+        for (int r = 0; r < h->nrhs; ++r) all_done = all_done && s[r].done;
+        ++polled;
+    }
+    PCG_CK(h, cudaStreamSynchronize(h->stream));
+    return PCG_OK;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int solve_fp64(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_stats_t* stats) {
+    int rc;
+    if ((rc = ensure_ws64(h))) return rc;
+    if (!h->graph64) {
+        if ((rc = capture_passes<double>(h, h->view64(), h->u64, h->r64, h->z64, h->p64, h->q64, h->st, &h->graph64)))
+            return rc;
+    }
+    const OpView<double> v = h->view64();
+    cudaStream_t s = h->stream;
+    h->launches = 0;
+    pcg::k_init_state<<<(h->nrhs + 63) / 64, 64, 0, s>>>(h->st, h->nrhs, tol * tol, maxit, nullptr);
+    pcg::k_residual<double><<<h->grid, h->block, 0, s>>>(v, b, x, h->u64, h->r64, h->st, h->partials, h->counters,
+                                                        h->nblocks, 0);
+    PCG_CK(h, cudaMemsetAsync(h->p64, 0, sizeof(double) * h->ntot, s));
+    PCG_CK(h, cudaMemsetAsync(h->q64, 0, sizeof(double) * h->ntot, s));
+    PCG_CK(h, cudaGetLastError());
+    h->launches += 2;
+    const long long max_launch = ((long long)maxit + 1 + h->ppl - 1) / h->ppl + 1;
+    if ((rc = run_graph(h, h->graph64, h->st, max_launch))) return rc;
+    pcg::k_finish<<<h->grid, h->block, 0, s>>>(h->nx, h->ny, h->nz, h->plane, h->vol, x, h->u64, h->p64, h->st);
+    pcg::k_residual<double><<<h->grid, h->block, 0, s>>>(v, b, x, nullptr, (double*)nullptr, h->st, h->partials,
+                                                        h->counters, h->nblocks, 1);
+    PCG_CK(h, cudaGetLastError());
+    h->launches += 2;
+    PCG_CK(h, cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState) * h->nrhs, cudaMemcpyDeviceToHost, s));
+    PCG_CK(h, cudaStreamSynchronize(s));
+    int worst = PCG_OK;
+    for (int r = 0; r < h->nrhs; ++r) {
+        const SolveState& q = h->h_st[r];
+        pcg_stats_t& o = h->rhs_stats[r];
+        o = pcg_stats_t{};
+        o.status = q.done ? q.status : PCG_NOT_CONVERGED;
+        o.iterations = std::max(0, q.pass - 1);
+        o.outer_sweeps = 0;
+        o.relres_recursive = q.bnorm2 > 0 ? std::sqrt(q.rr / q.bnorm2) : 0.0;
+        o.relres_true = q.bnorm2 > 0 ? std::sqrt(q.rr_true / q.bnorm2) : 0.0;
+        if (o.status != PCG_OK && worst == PCG_OK) worst = o.status;
+        if (o.status == PCG_BREAKDOWN) worst = PCG_BREAKDOWN;
+    }
+    (void)stats;
+    return worst;
+}
+
+int solve_mixed(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_stats_t* stats) {
+    int rc;
+    if ((rc = ensure_ws32(h))) return rc;
+    if (!h->graph32) {
+        if ((rc = capture_passes<float>(h, h->view32(), h->u32, h->r32, h->z32, h->p32, h->q32, h->st_in, &h->graph32)))
+            return rc;
+    }
+    const int inner_cap = (maxit > 0 && maxit < h->inner_maxit) ? maxit : h->inner_maxit;
+    const OpView<double> v = h->view64();
+    cudaStream_t s = h->stream;
+    const int nr = h->nrhs;
+    h->launches = 0;
+    std::vector<int> active(nr, 1), done(nr, 0), status(nr, PCG_NOT_CONVERGED), stag(nr, 0), sweeps(nr, 0), inner_it(nr, 0);
+    std::vector<std::vector<double>> hist(nr);
+    std::vector<double> bb(nr, 0.0), last_rr(nr, 0.0);
+    pcg::k_init_state<<<(nr + 63) / 64, 64, 0, s>>>(h->st, nr, tol * tol, 0, nullptr);
+    h->launches += 1;
+    for (int m = 0; m <= h->max_outer; ++m) {
+        // true residual of x in FP64 (its norm decides; its sum gives the coarse correction)
+        pcg::k_residual<float><<<h->grid, h->block, 0, s>>>(v, b, x, nullptr, (float*)nullptr, h->st, h->partials,
+                                                           h->counters, h->nblocks, 2);
+        PCG_CK(h, cudaGetLastError());
+        h->launches += 1;
+        PCG_CK(h, cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState) * nr, cudaMemcpyDeviceToHost, s));
+        PCG_CK(h, cudaStreamSynchronize(s));
+        bool any = false;
+        for (int r = 0; r < nr; ++r) {
+            active[r] = 0;
+            if (done[r]) continue;
+            const double rrv = h->h_st[r].rr;
+            bb[r] = h->h_st[r].bnorm2;
+            last_rr[r] = rrv;
+            if (bb[r] == 0.0) {     // the solution is zero
+                PCG_CK(h, cudaMemsetAsync(x + (size_t)r * h->vol, 0, sizeof(double) * h->vol, s));
+                done[r] = 1;
+                status[r] = PCG_OK;
+                last_rr[r] = 0.0;
+                continue;
+            }
+            const double rel = std::sqrt(rrv / bb[r]);
+            hist[r].push_back(rel);
+            if (h->trace) std::fprintf(stderr, "[pcg] rhs %d sweep %d relres_true %.3e inner_its_so_far %d\n", r, m, rel, inner_it[r]);
+            if (!std::isfinite(rel)) { done[r] = 1; status[r] = PCG_BREAKDOWN; continue; }
+            if (rel < tol) { done[r] = 1; status[r] = PCG_OK; continue; }
+            const size_t n = hist[r].size();
+            if (n >= 3) {
+                // stop when the best residual so far has not fallen tenfold over two sweeps:
+                // the FP64 representation of x has been reached
+                const double best_now = *std::min_element(hist[r].begin(), hist[r].end());
+                const double best_before = *std::min_element(hist[r].begin(), hist[r].end() - 2);
+                if (best_now > 0.1 * best_before) { done[r] = 1; status[r] = PCG_OK; stag[r] = 1; continue; }
+            }
+            if (m == h->max_outer) { done[r] = 1; status[r] = PCG_NOT_CONVERGED; continue; }
+            active[r] = 1;
+            any = true;
+        }
+        if (!any) break;
+        // coarse correction with the constant vector, then the inner right-hand side
+        // r' = b - A x - c A 1 in FP32
+        pcg::k_coarse<<<(nr + 63) / 64, 64, 0, s>>>(h->st, nr, h->total_mass);
+        pcg::k_residual<float><<<h->grid, h->block, 0, s>>>(v, b, x, nullptr, h->r32, h->st, h->partials,
+                                                           h->counters, h->nblocks, 3);
+        PCG_CK(h, cudaGetLastError());
+        h->launches += 2;
+        PCG_CK(h, cudaMemcpyAsync(h->d_active, active.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, s));
+        pcg::k_init_state<<<(nr + 63) / 64, 64, 0, s>>>(h->st_in, nr, 0.0, inner_cap, h->d_active);
+        pcg::k_inner_thresholds<<<(nr + 63) / 64, 64, 0, s>>>(h->st_in, h->st, nr, h->inner_tol * h->inner_tol);
+        PCG_CK(h, cudaMemsetAsync(h->u32, 0, sizeof(float) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->p32, 0, sizeof(float) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->q32, 0, sizeof(float) * h->ntot, s));
+        PCG_CK(h, cudaGetLastError());
+        h->launches += 2;
+        const long long max_launch = ((long long)inner_cap + 1 + h->ppl - 1) / h->ppl + 1;
+        if ((rc = run_graph(h, h->graph32, h->st_in, max_launch))) return rc;
+        pcg::k_refine_update<<<h->grid, h->block, 0, s>>>(h->nx, h->ny, h->nz, h->plane, h->vol, x, h->u32, h->p32,
+                                                         h->st_in, h->st, h->d_active);
+        PCG_CK(h, cudaGetLastError());
+        h->launches += 1;
+        PCG_CK(h, cudaMemcpyAsync(h->h_st + nr, h->st_in, sizeof(SolveState) * nr, cudaMemcpyDeviceToHost, s));
+        PCG_CK(h, cudaStreamSynchronize(s));
+        for (int r = 0; r < nr; ++r) {
+            if (!active[r]) continue;
+            sweeps[r] += 1;
+            inner_it[r] += std::max(0, h->h_st[nr + r].pass - 1);
+            if (h->h_st[nr + r].status == PCG_BREAKDOWN) { done[r] = 1; status[r] = PCG_BREAKDOWN; }
+        }
+    }
+    int worst = PCG_OK;
+    for (int r = 0; r < nr; ++r) {
+        pcg_stats_t& o = h->rhs_stats[r];
+        o = pcg_stats_t{};
+        o.status = done[r] ? status[r] : PCG_NOT_CONVERGED;
+        o.iterations = inner_it[r];
+        o.outer_sweeps = sweeps[r];
+        o.stagnated = stag[r];
+        o.relres_true = bb[r] > 0 ? std::sqrt(last_rr[r] / bb[r]) : 0.0;
+        o.relres_recursive = o.relres_true;
+        if (o.status != PCG_OK && worst == PCG_OK) worst = o.status;
+        if (o.status == PCG_BREAKDOWN) worst = PCG_BREAKDOWN;
+    }
+    (void)stats;
+    return worst;
+}
+
+void summarise(pcg_t h, pcg_stats_t* stats, int rc, double t0) {
+    if (!stats) return;
+    pcg_stats_t s{};
+    s.status = rc;
+    for (int r = 0; r < h->nrhs; ++r) {
+        const pcg_stats_t& o = h->rhs_stats[r];
+        s.iterations = std::max(s.iterations, o.iterations);
+        s.outer_sweeps = std::max(s.outer_sweeps, o.outer_sweeps);
+        s.stagnated = std::max(s.stagnated, o.stagnated);
+        s.relres_recursive = std::max(s.relres_recursive, o.relres_recursive);
+        s.relres_true = std::max(s.relres_true, o.relres_true);
+    }
+    s.elapsed_ms = now_ms() - t0;
+    *stats = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opts_t* opts, pcg_t* out) {
+    if (!out) return fail(nullptr, PCG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !coeffs) return fail(nullptr, PCG_ERR_INVALID_ARG, "grid and coeffs are required");
+    if (grid->n_x < 1 || grid->n_y < 1 || grid->n_z < 1 || grid->nrhs < 1)
+        return fail(nullptr, PCG_ERR_INVALID_ARG, "n_x, n_y, n_z and nrhs must be >= 1");
+    if (!grid->z_iface || !coeffs->beta_iface) return fail(nullptr, PCG_ERR_INVALID_ARG, "z_iface and beta_iface are required");
+    if (!(coeffs->lambda2 >= 0.0) || !std::isfinite(coeffs->lambda2))
+        return fail(nullptr, PCG_ERR_INVALID_ARG, "lambda2 must be finite and >= 0");
+    const long long plane = (long long)grid->n_x * grid->n_y;
+    if (plane > (1LL << 31) - 1) return fail(nullptr, PCG_ERR_INVALID_ARG, "n_x * n_y too large");
+    pcg_ctx* h = new (std::nothrow) pcg_ctx();
+    if (!h) return fail(nullptr, PCG_ERR_OOM, "host allocation failed");
+    h->geometry = grid->geometry;
+    h->nx = grid->n_x;
+    h->ny = grid->n_y;
+    h->nz = grid->n_z;
+    h->nrhs = grid->nrhs;
+    h->plane = plane;
+    h->vol = plane * grid->n_z;
+    h->ntot = h->vol * grid->nrhs;
+    h->periodic_y = grid->geometry == PCG_GEOM_BOX ? 1 : 0;
+    const bool field = coeffs->alpha_e || coeffs->alpha_n;
+    h->cls_mode = field ? 2 : (grid->geometry == PCG_GEOM_LATLON ? 1 : 0);
+    h->ncls = h->cls_mode == 0 ? 1 : (h->cls_mode == 1 ? h->ny : (int)plane);
+    if (opts) {
+        h->precision = opts->precision;
+        if (opts->inner_tol > 0) h->inner_tol = opts->inner_tol;
+        if (opts->inner_maxit > 0) h->inner_maxit = opts->inner_maxit;
+        if (opts->max_outer > 0) h->max_outer = opts->max_outer;
+        if (opts->passes_per_launch > 0) h->ppl = opts->passes_per_launch;
+        h->stream = (cudaStream_t)opts->stream;
+    }
+    if (h->precision != PCG_FP64 && h->precision != PCG_MIXED) {
+        delete h;
+        return fail(nullptr, PCG_ERR_INVALID_ARG, "unknown precision");
+    }
+    h->rhs_stats.assign(h->nrhs, pcg_stats_t{});
+    if (const char* tr = std::getenv("PCG_TRACE")) h->trace = std::atoi(tr);
+    h->block = dim3(BX, BY, 1);
+    h->grid = dim3((h->nx + BX - 1) / BX, (h->ny + BY - 1) / BY, h->nrhs);
+    h->nblocks = (int)(h->grid.x * h->grid.y);
+
+    auto bail = [&](int rc) {
+        g_create_error = h->err;
+        pcg_destroy(h);
+        return rc;
+    };
+    HostTables t;
+    int rc = build_tables(h, grid, coeffs, t);
+    if (rc) return bail(rc);
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { h->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
+    for (auto& ev : h->ev) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) { h->err = std::string("cudaEventCreate: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
+    }
+    if ((rc = dmalloc(h, &h->st, h->nrhs))) return bail(rc);
+    if ((rc = dmalloc(h, &h->st_in, h->nrhs))) return bail(rc);
+    if ((rc = dmalloc(h, &h->d_active, h->nrhs))) return bail(rc);
+    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * h->nblocks * 3))) return bail(rc);
+    if ((rc = dmalloc(h, &h->counters, h->nrhs))) return bail(rc);
+    e = cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * h->nrhs, h->stream);
+    if (e != cudaSuccess) { h->err = std::string("cudaMemset: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
+    e = cudaMallocHost((void**)&h->h_st, sizeof(SolveState) * 2 * h->nrhs);
+    if (e != cudaSuccess) { h->h_st = nullptr; h->err = "cudaMallocHost failed"; return bail(PCG_ERR_OOM); }
+    if ((rc = upload_tables(h, t))) return bail(rc);
+    *out = h;
+    return PCG_OK;
+}
+
+int pcg_solve(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_stats_t* stats) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    if (!b || !x) return fail(h, PCG_ERR_INVALID_ARG, "b and x are required");
+    if (!(tol >= 0.0) || maxit < 0) return fail(h, PCG_ERR_INVALID_ARG, "tol must be >= 0 and maxit >= 0");
+    const double t0 = now_ms();
+    int rc = h->precision == PCG_MIXED ? solve_mixed(h, b, x, tol, maxit, stats) : solve_fp64(h, b, x, tol, maxit, stats);
+    if (rc == PCG_ERR_CUDA || rc == PCG_ERR_OOM || rc == PCG_ERR_INVALID_ARG) return rc;
+    summarise(h, stats, rc, t0);
+    return rc;
+}
+
+int pcg_solve_host(pcg_t h, const double* b_host, double* x_host, double tol, int maxit, pcg_stats_t* stats) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    if (!b_host || !x_host) return fail(h, PCG_ERR_INVALID_ARG, "b and x are required");
+    const double t0 = now_ms();
+    int rc;
+    if (!h->hb) {
+        if ((rc = dmalloc(h, &h->hb, (size_t)h->ntot))) return rc;
+        if ((rc = dmalloc(h, &h->hx, (size_t)h->ntot))) return rc;
+    }
+    const size_t nb = sizeof(double) * h->ntot;
+    PCG_CK(h, cudaMemcpyAsync(h->hb, b_host, nb, cudaMemcpyHostToDevice, h->stream));
+    PCG_CK(h, cudaMemcpyAsync(h->hx, x_host, nb, cudaMemcpyHostToDevice, h->stream));
+    rc = h->precision == PCG_MIXED ? solve_mixed(h, h->hb, h->hx, tol, maxit, stats)
+                                   : solve_fp64(h, h->hb, h->hx, tol, maxit, stats);
+    if (rc == PCG_ERR_CUDA || rc == PCG_ERR_OOM || rc == PCG_ERR_INVALID_ARG) return rc;
+    PCG_CK(h, cudaMemcpyAsync(x_host, h->hx, nb, cudaMemcpyDeviceToHost, h->stream));
+    PCG_CK(h, cudaStreamSynchronize(h->stream));
+    summarise(h, stats, rc, t0);
+    return rc;
+}
+
+int pcg_rhs_stats(pcg_t h, int rhs, pcg_stats_t* stats) {
+    if (!h || !stats) return fail(h, PCG_ERR_INVALID_ARG, "handle and stats are required");
+    if (rhs < 0 || rhs >= h->nrhs) return fail(h, PCG_ERR_INVALID_ARG, "rhs out of range");
+    *stats = h->rhs_stats[rhs];
+    return PCG_OK;
+}
+
+int pcg_apply_A(pcg_t h, const double* x, double* y) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    if (!x || !y) return fail(h, PCG_ERR_INVALID_ARG, "x and y are required");
+    pcg::k_apply<double><<<h->grid, h->block, 0, h->stream>>>(h->view64(), x, y);
+    PCG_CK(h, cudaGetLastError());
+    return PCG_OK;
+}
+
+int pcg_precond(pcg_t h, const double* r, double* z) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    if (!r || !z) return fail(h, PCG_ERR_INVALID_ARG, "r and z are required");
+    pcg::k_precond<double><<<h->grid, h->block, 0, h->stream>>>(h->view64(), r, z);
+    PCG_CK(h, cudaGetLastError());
+    return PCG_OK;
+}
+
+int pcg_apply_A_f32(pcg_t h, const float* x, float* y) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    if (!x || !y) return fail(h, PCG_ERR_INVALID_ARG, "x and y are required");
+    pcg::k_apply<float><<<h->grid, h->block, 0, h->stream>>>(h->view32(), x, y);
+    PCG_CK(h, cudaGetLastError());
+    return PCG_OK;
+}
+
+int pcg_precond_f32(pcg_t h, const float* r, float* z) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    if (!r || !z) return fail(h, PCG_ERR_INVALID_ARG, "r and z are required");
+    pcg::k_precond<float><<<h->grid, h->block, 0, h->stream>>>(h->view32(), r, z);
+    PCG_CK(h, cudaGetLastError());
+    return PCG_OK;
+}
+
+int pcg_time_sweeps(pcg_t h, const double* b, int precision, int passes, double* ms_prec, double* ms_spmv) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    if (!b || !ms_prec || !ms_spmv || passes < 1) return fail(h, PCG_ERR_INVALID_ARG, "b, outputs and passes >= 1 required");
+    if (precision != PCG_FP64 && precision != PCG_MIXED) return fail(h, PCG_ERR_INVALID_ARG, "unknown precision");
+    int rc;
+    if ((rc = ensure_ws64(h))) return rc;
+    if (precision == PCG_MIXED && (rc = ensure_ws32(h))) return rc;
+    cudaStream_t s = h->stream;
+    const OpView<double> v = h->view64();
+    std::vector<cudaEvent_t> ev(3);
+    for (auto& e : ev) PCG_CK(h, cudaEventCreate(&e));
+    double tp = 0.0, ts = 0.0;
+    PCG_CK(h, cudaMemsetAsync(h->z64, 0, sizeof(double) * h->ntot, s));   // x0 = 0
+    pcg::k_init_state<<<(h->nrhs + 63) / 64, 64, 0, s>>>(h->st, h->nrhs, 0.0, passes, nullptr);
+    if (precision == PCG_FP64) {
+        pcg::k_residual<double><<<h->grid, h->block, 0, s>>>(v, b, h->z64, h->u64, h->r64, h->st, h->partials,
+                                                            h->counters, h->nblocks, 0);
+        PCG_CK(h, cudaMemsetAsync(h->p64, 0, sizeof(double) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->q64, 0, sizeof(double) * h->ntot, s));
+    } else {
+        pcg::k_residual<float><<<h->grid, h->block, 0, s>>>(v, b, h->z64, nullptr, h->r32, h->st, h->partials,
+                                                           h->counters, h->nblocks, 3);
+        pcg::k_init_state<<<(h->nrhs + 63) / 64, 64, 0, s>>>(h->st_in, h->nrhs, 0.0, passes, nullptr);
+        PCG_CK(h, cudaMemsetAsync(h->u32, 0, sizeof(float) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->p32, 0, sizeof(float) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->q32, 0, sizeof(float) * h->ntot, s));
+    }
+    PCG_CK(h, cudaGetLastError());
+    const OpView<float> v32 = h->view32();
+    for (int i = 0; i < passes; ++i) {
+        PCG_CK(h, cudaEventRecord(ev[0], s));
+        if (precision == PCG_FP64)
+            pcg::k_sweep_prec<double><<<h->grid, h->block, 0, s>>>(v, h->r64, h->q64, h->z64, h->st, h->partials,
+                                                                  h->counters, h->nblocks);
+        else
+            pcg::k_sweep_prec<float><<<h->grid, h->block, 0, s>>>(v32, h->r32, h->q32, h->z32, h->st_in,
+                                                                 h->partials, h->counters, h->nblocks);
+        PCG_CK(h, cudaEventRecord(ev[1], s));
+        if (precision == PCG_FP64)
+            pcg::k_sweep_spmv<double><<<h->grid, h->block, 0, s>>>(v, h->u64, h->p64, h->q64, h->z64, h->st,
+                                                                  h->partials, h->counters, h->nblocks);
+        else
+            pcg::k_sweep_spmv<float><<<h->grid, h->block, 0, s>>>(v32, h->u32, h->p32, h->q32, h->z32, h->st_in,
+                                                                 h->partials, h->counters, h->nblocks);
+        PCG_CK(h, cudaEventRecord(ev[2], s));
+        PCG_CK(h, cudaGetLastError());
+        PCG_CK(h, cudaEventSynchronize(ev[2]));
+        float a = 0.f, c = 0.f;
+        PCG_CK(h, cudaEventElapsedTime(&a, ev[0], ev[1]));
+        PCG_CK(h, cudaEventElapsedTime(&c, ev[1], ev[2]));
+        tp += a;
+        ts += c;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    *ms_prec = tp / passes;
+    *ms_spmv = ts / passes;
+    return PCG_OK;
+}
+
+int pcg_sync(pcg_t h) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    PCG_CK(h, cudaStreamSynchronize(h->stream));
+    return PCG_OK;
+}
+
+size_t pcg_device_bytes(pcg_t h) { return h ? h->bytes : 0; }
+
+long long pcg_kernel_launches(pcg_t h) { return h ? h->launches : 0; }
+
+const char* pcg_last_error(pcg_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void pcg_destroy(pcg_t h) {
+    if (!h) return;
+    if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
+    if (h->graph64) cudaGraphExecDestroy(h->graph64);
+    if (h->graph32) cudaGraphExecDestroy(h->graph32);
+    for (void* p : {(void*)h->u64, (void*)h->r64, (void*)h->z64, (void*)h->p64, (void*)h->q64, (void*)h->u32,
+                    (void*)h->r32, (void*)h->z32, (void*)h->p32, (void*)h->q32, (void*)h->hb, (void*)h->hx,
+                    (void*)h->st, (void*)h->st_in, (void*)h->d_active, (void*)h->partials, (void*)h->counters,
+                    h->t64.base, h->t32.base})
+        if (p) cudaFree(p);
+    if (h->h_st) cudaFreeHost(h->h_st);
+    for (auto ev : h->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+}  // extern "C"

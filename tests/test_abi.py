@@ -1,0 +1,102 @@
+"""The C-ABI library loads and exports every entry point of include/pcg.h, and
+its host-side argument checks reject bad input before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1302_7193_gb300 as pkg
+import workloads as W
+from paper_1302_7193_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return pkg.load_library()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "pcg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcg_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("pcg_create", "pcg_solve", "pcg_apply_A", "pcg_precond", "pcg_destroy", "pcg_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(pkg.EXPORTED) == set(names)
+
+
+def _create(p, **over):
+    z, zp = pkg._dbl(p.z_iface)
+    be, bp = pkg._dbl(p.beta_iface)
+    g = pkg.pcg_grid_t(p.kind, p.n_x, p.n_y, p.n_z, 1, zp, 1.0, 1.0, p.lat0, p.lat1)
+    c = pkg.pcg_coeffs_t(None, None, bp, p.lambda2)
+    for k, v in over.items():
+        setattr(g if hasattr(g, k) else c, k, v)
+    o = pkg.pcg_opts_t(0, 0.0, 0, 0, 0, None)
+    h = ctypes.c_void_p()
+    lib = pkg.load_library()
+    rc = lib.pcg_create(ctypes.byref(g), ctypes.byref(c), ctypes.byref(o), ctypes.byref(h))
+    return rc, h, lib.pcg_last_error(None).decode(), (z, be)
+
+
+@pytest.mark.parametrize("field,value", [("n_x", 0), ("n_z", 0), ("nrhs", 0), ("lambda2", -1.0),
+                                         ("geometry", 7), ("lambda2", float("nan"))])
+def test_create_rejects_bad_arguments(lib, field, value):
+    rc, h, msg, _ = _create(W.small_box(), **{field: value})
+    assert rc == pkg.PCG_ERR_INVALID_ARG and not h.value, (rc, msg)
+    assert msg
+
+
+def test_create_rejects_non_monotone_levels(lib):
+    p = W.small_box()
+    p.z_iface = p.z_iface.copy()
+    p.z_iface[3] = p.z_iface[2]
+    rc, h, msg, _ = _create(p)
+    assert rc == pkg.PCG_ERR_INVALID_ARG and "increasing" in msg
+
+
+def test_create_rejects_bad_latitude_band(lib):
+    p = W.latlon_problem(8, 4, 4)
+    p.lat1 = 2.0
+    rc, h, msg, _ = _create(p)
+    assert rc == pkg.PCG_ERR_INVALID_ARG and "latitude" in msg
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    st = pkg.pcg_stats_t()
+    assert lib.pcg_solve(None, None, None, 1e-8, 10, ctypes.byref(st)) == pkg.PCG_ERR_INVALID_ARG
+    assert lib.pcg_apply_A(None, None, None) == pkg.PCG_ERR_INVALID_ARG
+    assert lib.pcg_precond(None, None, None) == pkg.PCG_ERR_INVALID_ARG
+    assert lib.pcg_device_bytes(None) == 0
+    lib.pcg_destroy(None)
+
+
+def test_binding_refuses_missing_library(tmp_path):
+    saved = pkg._lib
+    pkg._lib = None
+    try:
+        with pytest.raises(ImportError):
+            pkg.load_library(str(tmp_path / "libpcg.so"))
+    finally:
+        pkg._lib = saved
+
+
+def test_structs_match_header_layout():
+    # field order and sizes of the ctypes mirrors equal the C structs
+    assert ctypes.sizeof(pkg.pcg_stats_t) == 4 * 4 + 3 * 8
+    assert ctypes.sizeof(pkg.pcg_opts_t) == 8 + 8 + 4 + 4 + 4 + 4 + 8

@@ -1,0 +1,268 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Tolerances:
+* Operator and preconditioner: componentwise rounding-error bounds of the
+  flux-form evaluation (|terms| summed) and of the LDL^T solve of an M-matrix
+  (backward error c eps |M| |z|; for an M-matrix |L| |D| |L^T| = |M|).
+* Solves: relative 1e-10 in x for the FP64 path and 1e-8 for the mixed path
+  (the bars of the solver's specification), on the same seeded inputs,
+  both at a fixed iteration count and after convergence.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import FluxOperator, LinePreconditioner, apply_rows, assemble_csr, pcg_interleaved
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = float(np.finfo(np.float64).eps)
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need cuda:0"
+    from paper_1302_7193_gb300 import build as B
+    B.build()
+    return torch
+
+
+def _solver(p, **kw):
+    import paper_1302_7193_gb300 as pkg
+    return pkg.Solver(p, **kw)
+
+
+def _case_list():
+    return [
+        ("box32x32x16", W.small_box()),
+        ("ragged37x13x9", W.box_problem(37, 13, 9, 0.02)),
+        ("sinalpha48x40x12", W.box_problem(48, 40, 12, 0.01, alpha="sin")),
+        ("latlon72x32x16", W.latlon_problem(72, 32, 16)),
+        ("box64x64x128_d0.004", W.medium_box(scale=4)),
+        ("tiny1x2x3", W.box_problem(1, 2, 3, 0.01)),
+        ("tiny3x1x1", W.box_problem(3, 1, 1, 0.01, lambda2=0.5)),
+    ]
+
+
+CASES = _case_list()
+IDS = [c[0] for c in CASES]
+SOLVE_CASES = [c for c in CASES if c[0] not in ("tiny3x1x1",)]
+
+
+def _flux_terms(op, x):
+    """mass |x| + sum |c (x_i - x_j)| per row: the scale of every rounding in A x."""
+    xf = x.ravel()
+    t = op.mass * np.abs(xf)
+    return t + np.bincount(op._rows, weights=np.abs(op.C.data * (xf[op._rows] - xf[op.C.indices])), minlength=xf.size)
+
+
+def _to_dev(torch, a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a).ravel().copy())
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_apply_fp64(torch_cuda, name, p):
+    torch = torch_cuda
+    op = FluxOperator(p)
+    rng = np.random.default_rng(1)
+    with _solver(p) as s:
+        for x in (rng.uniform(-1, 1, p.shape), 1e6 + rng.uniform(-1, 1, p.shape)):
+            y = torch.empty(p.n_cells, dtype=torch.float64, device="cuda")
+            s.apply_A(_to_dev(torch, x), y)
+            yg = y.cpu().numpy()
+            yo = op @ x
+            bound = 24 * EPS64 * _flux_terms(op, x) + 1e-300
+            assert (np.abs(yg - yo) <= bound).all(), np.max(np.abs(yg - yo) / bound)
+
+
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_apply_fp32(torch_cuda, name, p):
+    torch = torch_cuda
+    op = FluxOperator(p)
+    x = np.random.default_rng(2).uniform(-1, 1, p.shape).astype(np.float32)
+    with _solver(p) as s:
+        y = torch.empty(p.n_cells, dtype=torch.float32, device="cuda")
+        s.apply_A_f32(_to_dev(torch, x), y)
+        yg = y.cpu().numpy().astype(np.float64)
+    xd = x.astype(np.float64)
+    bound = 32 * EPS32 * _flux_terms(op, xd) + 1e-30
+    assert (np.abs(yg - op @ xd) <= bound).all()
+
+
+def _m_times(prec, z):
+    """M z with the oracle's column blocks (column-contiguous), and |M| |z|."""
+    zc = prec._to_columns(z).reshape(-1, prec.p.n_z)
+    lo, mn, up = prec.lower, prec.main, prec.upper
+    mz = mn * zc
+    amz = np.abs(mn) * np.abs(zc)
+    mz[:, 1:] += lo[:, 1:] * zc[:, :-1]
+    amz[:, 1:] += np.abs(lo[:, 1:] * zc[:, :-1])
+    mz[:, :-1] += up[:, :-1] * zc[:, 1:]
+    amz[:, :-1] += np.abs(up[:, :-1] * zc[:, 1:])
+    return prec._from_columns(mz.ravel()), prec._from_columns(amz.ravel())
+
+
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_precond_fp64(torch_cuda, name, p):
+    torch = torch_cuda
+    prec = LinePreconditioner(assemble_csr(p), p)
+    r = np.random.default_rng(3).uniform(-1, 1, p.shape)
+    with _solver(p) as s:
+        z = torch.empty(p.n_cells, dtype=torch.float64, device="cuda")
+        s.precond(_to_dev(torch, r), z)
+        zg = z.cpu().numpy().reshape(p.shape)
+    mz, amz = _m_times(prec, zg)
+    assert (np.abs(mz - r) <= 16 * p.n_z * EPS64 * amz).all()          # backward error
+    zo = prec(r)
+    assert np.linalg.norm(zg - zo) / np.linalg.norm(zo) < 1e-10          # forward, vs oracle
+
+
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_precond_fp32(torch_cuda, name, p):
+    torch = torch_cuda
+    prec = LinePreconditioner(assemble_csr(p), p)
+    r = np.random.default_rng(4).uniform(-1, 1, p.shape).astype(np.float32)
+    with _solver(p) as s:
+        z = torch.empty(p.n_cells, dtype=torch.float32, device="cuda")
+        s.precond_f32(_to_dev(torch, r), z)
+        zg = z.cpu().numpy().reshape(p.shape).astype(np.float64)
+    mz, amz = _m_times(prec, zg)
+    assert (np.abs(mz - r) <= 16 * p.n_z * EPS32 * amz).all()
+    zo = prec(r.astype(np.float64))
+    assert np.linalg.norm(zg - zo) / np.linalg.norm(zo) < 1e-4
+
+
+def _oracle_solve(p, b, **kw):
+    return pcg_interleaved(FluxOperator(p), LinePreconditioner(assemble_csr(p), p), b, **kw)
+
+
+@pytest.mark.parametrize("name,p", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_fp64_fixed_iterations(torch_cuda, name, p):
+    torch = torch_cuda
+    b = W.rhs_for(p, seed=0, smooth=(p.kind == W.GEOM_BOX))
+    with _solver(p) as s:
+        for k in (1, 4, 25):
+            ref = _oracle_solve(p, b, eps=0.0, maxiter=k)
+            x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+            st = s.solve(_to_dev(torch, b), x, tol=0.0, maxit=k)
+            assert st.iterations == k == ref.iterations
+            xg = x.cpu().numpy().reshape(p.shape)
+            err = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
+            assert err < 1e-10, (k, err)
+
+
+@pytest.mark.parametrize("name,p", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_fp64_converged(torch_cuda, name, p):
+    torch = torch_cuda
+    b = W.rhs_for(p, seed=0, smooth=(p.kind == W.GEOM_BOX))
+    ref = _oracle_solve(p, b, eps=1e-10, maxiter=20000)
+    with _solver(p) as s:
+        x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        st = s.solve(_to_dev(torch, b), x, tol=1e-10, maxit=20000)
+    assert st.status == 0 and st.relres_recursive < 1e-10
+    assert abs(st.iterations - ref.iterations) <= 2
+    xg = x.cpu().numpy().reshape(p.shape)
+    assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) < 1e-10
+    # reported true residual agrees with the oracle's evaluation
+    rt = np.linalg.norm(b.ravel() - FluxOperator(p) @ xg) / np.linalg.norm(b)
+    assert abs(rt - st.relres_true) <= 1e-3 * rt + 1e-15
+
+
+@pytest.mark.parametrize("name,p", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_mixed_matches_fp64_oracle(torch_cuda, name, p):
+    torch = torch_cuda
+    b = W.rhs_for(p, seed=0, smooth=(p.kind == W.GEOM_BOX))
+    ref = _oracle_solve(p, b, eps=1e-12, maxiter=20000)
+    with _solver(p, precision="mixed") as s:
+        x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        st = s.solve(_to_dev(torch, b), x, tol=1e-10, maxit=20000)
+    assert st.status == 0, st
+    xg = x.cpu().numpy().reshape(p.shape)
+    err = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
+    assert err < 1e-8, (err, st)
+
+
+def test_batch_equals_single_bitwise(torch_cuda):
+    torch = torch_cuda
+    p = W.box_problem(40, 24, 12, 0.01)
+    seeds = [0, 5, 9]
+    bs = W.batched_rhs(p, seeds)
+    bs[1] *= 1e-3                                    # different scales converge at different passes
+    with _solver(p, nrhs=3) as s:
+        xb = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
+        s.solve(_to_dev(torch, bs), xb, tol=1e-9, maxit=5000)
+        stats = [s.pcg_rhs_stats(r) for r in range(3)]
+    xb = xb.cpu().numpy().reshape(bs.shape)
+    with _solver(p) as s1:
+        for r in range(3):
+            x1 = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+            st = s1.solve(_to_dev(torch, bs[r]), x1, tol=1e-9, maxit=5000)
+            assert st.iterations == stats[r].iterations
+            assert np.array_equal(x1.cpu().numpy().reshape(p.shape), xb[r])
+
+
+def test_zero_rhs_and_warm_start_and_maxit0(torch_cuda):
+    torch = torch_cuda
+    p = W.small_box()
+    b = W.rhs_for(p, seed=3)
+    with _solver(p) as s:
+        x = torch.full((p.n_cells,), 7.0, dtype=torch.float64, device="cuda")
+        st = s.solve(torch.zeros(p.n_cells, dtype=torch.float64, device="cuda"), x, tol=1e-8, maxit=100)
+        assert st.status == 0 and st.iterations == 0 and not x.any()
+        x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        st = s.solve(_to_dev(torch, b), x, tol=1e-10, maxit=5000)
+        st2 = s.solve(_to_dev(torch, b), x, tol=1e-8, maxit=5000)   # warm start at the solution
+        assert st2.iterations <= 1
+        x0 = torch.full((p.n_cells,), 0.25, dtype=torch.float64, device="cuda")
+        st3 = s.solve(_to_dev(torch, b), x0, tol=1e-8, maxit=0)
+        assert st3.status == 4 and st3.iterations == 0
+        assert bool((x0 == 0.25).all())
+
+
+def test_host_entry_matches_device_entry(torch_cuda):
+    torch = torch_cuda
+    p = W.box_problem(32, 16, 8, 0.01)
+    b = W.rhs_for(p, seed=1)
+    with _solver(p) as s:
+        x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        st = s.solve(_to_dev(torch, b), x, tol=1e-9, maxit=5000)
+        xh = np.zeros(p.n_cells)
+        sth = s.solve_host(np.ascontiguousarray(b.ravel()), xh, tol=1e-9, maxit=5000)
+    assert st.iterations == sth.iterations
+    assert np.array_equal(xh, x.cpu().numpy())
+
+
+def test_medium_box_full_size(torch_cuda):
+    """256 x 256 x 128 (the benchmark grid) in the benchmark's launch configuration:
+    sampled operator rows, sampled column solves, three iterations against the
+    oracle, and the converged tol-1e-8 solve's residual checked by the oracle."""
+    torch = torch_cuda
+    p = W.medium_box()
+    b = W.medium_box_rhs(p)
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-1, 1, p.shape)
+    cells = np.stack([rng.integers(0, n, 4000) for n in p.shape])
+    with _solver(p) as s:
+        y = torch.empty(p.n_cells, dtype=torch.float64, device="cuda")
+        s.apply_A(_to_dev(torch, x), y)
+        yg = y.cpu().numpy().reshape(p.shape)[tuple(cells)]
+        yo = apply_rows(p, x, cells)
+        assert np.allclose(yg, yo, rtol=1e-12, atol=1e-12 * np.abs(yo).max())
+        # three fixed iterations against the oracle
+        xg = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        st = s.solve(_to_dev(torch, b), xg, tol=0.0, maxit=3)
+        ref = _oracle_solve(p, b, eps=0.0, maxiter=3)
+        assert np.linalg.norm(xg.cpu().numpy().reshape(p.shape) - ref.x) / np.linalg.norm(ref.x) < 1e-10
+        # converged solve
+        xg.zero_()
+        st = s.solve(_to_dev(torch, b), xg, tol=1e-8, maxit=20000)
+        assert st.status == 0 and st.relres_recursive < 1e-8
+        xs = xg.cpu().numpy()
+    rt = np.linalg.norm(b.ravel() - FluxOperator(p) @ xs) / np.linalg.norm(b)
+    assert abs(rt - st.relres_true) <= 1e-3 * rt
+    assert rt < 1e-4
