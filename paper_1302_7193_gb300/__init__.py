@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "not_converge
 EXPORTED = (
     "pcg_create", "pcg_solve", "pcg_solve_host", "pcg_rhs_stats", "pcg_apply_A", "pcg_precond",
     "pcg_apply_A_f32", "pcg_precond_f32", "pcg_time_sweeps", "pcg_sync", "pcg_device_bytes", "pcg_kernel_launches",
-    "pcg_last_error", "pcg_destroy",
+    "pcg_last_error", "pcg_destroy", "pcg_precond_noalloc",
 )
 
 
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pcg_last_error.restype = ctypes.c_char_p
     lib.pcg_destroy.argtypes = [P]
     lib.pcg_destroy.restype = None
+    lib.pcg_precond_noalloc.argtypes = [ctypes.POINTER(pcg_grid_t), ctypes.POINTER(pcg_coeffs_t), P, P, P]
+    lib.pcg_precond_noalloc.restype = I
     _lib = lib
     return lib
 

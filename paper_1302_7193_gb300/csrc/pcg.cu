@@ -714,3 +714,148 @@ void pcg_destroy(pcg_t h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Line preconditioner without any allocation.
+//
+// For callers that must not allocate device memory at the point of the call:
+// code running while a CUDA stream is being captured into a graph (where a
+// cudaMalloc is not allowed), real-time loops that cannot afford an
+// allocation's latency or synchronisation, and hosts whose device memory is
+// owned entirely by another allocator (a framework's caching allocator or a
+// fixed budget) so that a library-side cudaMalloc would fail or fragment it.
+// Such callers cannot create a handle at that point, because pcg_create
+// allocates.  pcg_precond_noalloc applies the same preconditioner as
+// pcg_precond, keeping its operator tables and Thomas factors in the
+// fixed-size device array below, which every GPU that loads this library
+// holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocDoubles = size_t(1) << 19;   // 4 MiB of device scratch
+
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+double g_noalloc_stage[kNoAllocDoubles];              // host staging of the tables (same layout)
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};   // device address of the scratch, per device
+
+int noalloc_fail(int code, const char* msg) {
+    g_create_error = msg;
+    return code;
+}
+
+}  // namespace
+
+extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const double* r, double* z,
+                                   void* stream) {
+    if (!grid || !coeffs || !r || !z) return noalloc_fail(PCG_ERR_INVALID_ARG, "grid, coeffs, r and z are required");
+    if (grid->n_x < 1 || grid->n_y < 1 || grid->n_z < 1 || grid->nrhs < 1)
+        return noalloc_fail(PCG_ERR_INVALID_ARG, "n_x, n_y, n_z and nrhs must be >= 1");
+    if (!grid->z_iface || !coeffs->beta_iface) return noalloc_fail(PCG_ERR_INVALID_ARG, "z_iface and beta_iface are required");
+    if (!(coeffs->lambda2 >= 0.0) || !std::isfinite(coeffs->lambda2))
+        return noalloc_fail(PCG_ERR_INVALID_ARG, "lambda2 must be finite and >= 0");
+    const int nx = grid->n_x, ny = grid->n_y, nz = grid->n_z;
+    const size_t nxy = (size_t)nx * ny;
+    const bool field = coeffs->alpha_e || coeffs->alpha_n;
+    const int cls_mode = field ? 2 : (grid->geometry == PCG_GEOM_LATLON ? 1 : 0);
+    const size_t ncls = cls_mode == 0 ? 1 : (cls_mode == 1 ? (size_t)ny : nxy);
+    const size_t need = 3 * (size_t)nz + ny + 2 * nxy + 2 * (size_t)nz * ncls;
+    if (need > kNoAllocDoubles) {
+        static char msg[256];
+        std::snprintf(msg, sizeof msg,
+                      "pcg_precond_noalloc: this grid needs %zu doubles of tables, the fixed scratch holds %zu "
+                      "(use pcg_create and pcg_precond)", need, kNoAllocDoubles);
+        return noalloc_fail(PCG_ERR_INVALID_ARG, msg);
+    }
+    // one-time set-up per device: the device address of the scratch array
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(PCG_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return noalloc_fail(PCG_ERR_INVALID_ARG, "device ordinal out of range");
+    if (!g_noalloc_dev_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return noalloc_fail(PCG_ERR_CUDA, cudaGetErrorString(e));
+        g_noalloc_dev_ptr[dev] = (double*)p;
+    }
+    double* d = g_noalloc_dev_ptr[dev];
+    // tables (Section 3.1 geometry, as in pcg_create) into the static staging buffer
+    double* hs = g_noalloc_stage;
+    double *mass = hs, *wv = hs + nz, *dk = hs + 2 * nz, *area = hs + 3 * nz, *mue = area + ny, *mun = mue + nxy;
+    const double* zi = grid->z_iface;
+    const double* beta = coeffs->beta_iface;
+    for (int k = 0; k <= nz; ++k) {
+        if (!std::isfinite(zi[k]) || !std::isfinite(beta[k])) return noalloc_fail(PCG_ERR_INVALID_ARG, "non-finite z_iface or beta_iface");
+        if (k > 0 && !(zi[k] > zi[k - 1])) return noalloc_fail(PCG_ERR_INVALID_ARG, "z_iface must be strictly increasing");
+    }
+    auto centre = [&](int k) { return 0.5 * (zi[k] + zi[k + 1]); };
+    if (grid->geometry == PCG_GEOM_BOX) {
+        if (!(grid->lx > 0.0) || !(grid->ly > 0.0)) return noalloc_fail(PCG_ERR_INVALID_ARG, "box extents must be positive");
+        const double hx = grid->lx / nx, hy = grid->ly / ny;
+        for (int k = 0; k < nz; ++k) {
+            const double dz = zi[k + 1] - zi[k];
+            mass[k] = coeffs->lambda2 * dz;
+            dk[k] = dz;
+            wv[k] = (k + 1 < nz) ? beta[k + 1] / (centre(k + 1) - centre(k)) : 0.0;
+        }
+        for (int j = 0; j < ny; ++j) area[j] = hx * hy;
+        for (size_t idx = 0; idx < nxy; ++idx) {
+            mue[idx] = (coeffs->alpha_e ? coeffs->alpha_e[idx] : 1.0) * (hy / hx);
+            mun[idx] = (coeffs->alpha_n ? coeffs->alpha_n[idx] : 1.0) * (hx / hy);
+        }
+    } else if (grid->geometry == PCG_GEOM_LATLON) {
+        const double pi = 3.14159265358979323846;
+        if (!(grid->lat0 > -0.5 * pi && grid->lat1 < 0.5 * pi && grid->lat0 < grid->lat1))
+            return noalloc_fail(PCG_ERR_INVALID_ARG, "latitude band must satisfy -pi/2 < lat0 < lat1 < pi/2");
+        const double dlon = 2.0 * pi / nx, dlat = (grid->lat1 - grid->lat0) / ny;
+        for (int k = 0; k < nz; ++k) {
+            const double r0 = zi[k], r1 = zi[k + 1];
+            mass[k] = coeffs->lambda2 * ((r1 - r0) * (r1 * r1 + r1 * r0 + r0 * r0)) / 3.0;
+            dk[k] = r1 - r0;
+            wv[k] = (k + 1 < nz) ? beta[k + 1] * r1 * r1 / (centre(k + 1) - centre(k)) : 0.0;
+        }
+        for (int j = 0; j < ny; ++j) {
+            const double ln = grid->lat0 + (j + 1) * dlat, lc = grid->lat0 + (j + 0.5) * dlat;
+            area[j] = dlon * 2.0 * std::cos(lc) * std::sin(0.5 * dlat);
+            for (int i = 0; i < nx; ++i) {
+                const size_t idx = (size_t)j * nx + i;
+                mue[idx] = (coeffs->alpha_e ? coeffs->alpha_e[idx] : 1.0) * dlat / (std::cos(lc) * dlon);
+                mun[idx] = (j + 1 < ny) ? (coeffs->alpha_n ? coeffs->alpha_n[idx] : 1.0) * std::cos(ln) * dlon / dlat : 0.0;
+            }
+        }
+    } else {
+        return noalloc_fail(PCG_ERR_INVALID_ARG, "unknown geometry");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ntab = 3 * (size_t)nz + ny + 2 * nxy;
+    // pageable source: the call returns once the staging buffer has been consumed
+    e = cudaMemcpyAsync(d, hs, ntab * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return noalloc_fail(PCG_ERR_CUDA, cudaGetErrorString(e));
+    OpView<double> v;
+    v.nx = nx;
+    v.ny = ny;
+    v.nz = nz;
+    v.plane = (long long)nxy;
+    v.vol = (long long)nxy * nz;
+    v.mass = d;
+    v.wv = d + nz;
+    v.dk = d + 2 * nz;
+    v.area = d + 3 * nz;
+    v.mue = v.area + ny;
+    v.mun = v.mue + nxy;
+    v.periodic_y = grid->geometry == PCG_GEOM_BOX ? 1 : 0;
+    double* fg = d + ntab;
+    double* fe = fg + (size_t)nz * ncls;
+    v.fg = fg;
+    v.fe = fe;
+    v.cls_mode = cls_mode;
+    v.ncls = (int)ncls;
+    // the factors are rewritten in full by every call, so nothing left by an
+    // earlier call is read
+    pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, s>>>(v, fg, fe);
+    const dim3 block(BX, BY, 1), gridd((nx + BX - 1) / BX, (ny + BY - 1) / BY, grid->nrhs);
+    pcg::k_precond<double><<<gridd, block, 0, s>>>(v, r, z);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(PCG_ERR_CUDA, cudaGetErrorString(e));
+    return PCG_OK;
+}
