@@ -160,9 +160,12 @@ __device__ __forceinline__ T horiz(const Col<T>& col, const T* __restrict__ zl, 
 // ---------------------------------------------------------------------------
 // Block / grid reductions with a deterministic order.
 // ---------------------------------------------------------------------------
+constexpr int MAXW = 8;   // blocks of at most 256 threads
+
 template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[NT / 32]) {
-    const int tid = threadIdx.y * BX + threadIdx.x;
+__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[MAXW]) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
     for (int n = 0; n < N; ++n) {
         double a = v[n];
@@ -175,23 +178,22 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[NT / 32])
 #pragma unroll
         for (int n = 0; n < N; ++n) {
             double a = 0.0;
-#pragma unroll
-            for (int w = 0; w < NT / 32; ++w) a += sh[n][w];
+            for (int w = 0; w < nw; ++w) a += sh[n][w];
             v[n] = a;
         }
     }
 }
 
-// Each block stores its N partial sums; the last block to arrive sums all
-// partials of its right-hand side in block order and returns true on thread 0
-// (with the totals in v).  Other threads of the last block return false.
+// Each block stores its N partial sums at index `bid`; the last block to
+// arrive sums all partials of its right-hand side in block order and returns
+// true on thread 0 (with the totals in v).  Other threads return false.
 template <int N>
-__device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsigned* counter, int nblocks) {
-    __shared__ double sh[N][NT / 32];
+__device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsigned* counter, int nblocks, int bid) {
+    __shared__ double sh[N][MAXW];
     __shared__ bool am_last;
-    __shared__ double tot[N][NT / 32];
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    __shared__ double tot[N][MAXW];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
     block_sum<N>(v, sh);
     if (tid == 0) {
 #pragma unroll
@@ -206,7 +208,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsig
     double acc[N];
 #pragma unroll
     for (int n = 0; n < N; ++n) acc[n] = 0.0;
-    for (int b = tid; b < nblocks; b += NT) {
+    for (int b = tid; b < nblocks; b += nthr) {
 #pragma unroll
         for (int n = 0; n < N; ++n) acc[n] += __ldcg(partials + (long long)b * N + n);
     }
@@ -218,6 +220,124 @@ __device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsig
         *counter = 0u;
     }
     return tid == 0;
+}
+
+__device__ __forceinline__ int bid2() { return blockIdx.y * gridDim.x + blockIdx.x; }
+
+// Block-level sum of per-thread accumulators, then the cross-block FP64 sum
+// of grid_sum.  FP32 accumulators are combined as compensated (sum, error)
+// pairs with TwoSum so that FP32 kernels issue no FP64 instruction until one
+// conversion per block (the FP64 pipe of this part is 1/64 of the FP32 rate).
+__device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2) {
+    const float t = s + s2;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    c = c + c2 + e;
+}
+
+template <int N>
+__device__ __forceinline__ bool grid_sum_acc(Acc<float> (&a)[N], double* partials, unsigned* counter, int nblocks,
+                                             int bid, double (&out)[N]) {
+    __shared__ float shs[N][MAXW], shc[N][MAXW];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        float s = a[n].s, c = a[n].c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+            const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+            pair_add(s, c, s2, c2);
+        }
+        if ((tid & 31) == 0) {
+            shs[n][tid >> 5] = s;
+            shc[n][tid >> 5] = c;
+        }
+    }
+    __syncthreads();
+    double v[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) v[n] = 0.0;
+    if (tid == 0) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            float s = shs[n][0], c = shc[n][0];
+            for (int w = 1; w < nw; ++w) pair_add(s, c, shs[n][w], shc[n][w]);
+            v[n] = (double)s + (double)c;
+        }
+    }
+    // cross-block part (only thread 0's v is meaningful, as in grid_sum)
+    __shared__ bool am_last;
+    __shared__ double tot[N][MAXW];
+    const int nthr = blockDim.x * blockDim.y;
+    if (tid == 0) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) partials[(long long)bid * N + n] = v[n];
+        __threadfence();
+        const unsigned prev = atomicAdd(counter, 1u);
+        am_last = (prev == (unsigned)nblocks - 1u);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    double acc[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) acc[n] = 0.0;
+    for (int b = tid; b < nblocks; b += nthr) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) acc[n] += __ldcg(partials + (long long)b * N + n);
+    }
+    block_sum<N>(acc, tot);
+    if (tid == 0) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) out[n] = acc[n];
+        *counter = 0u;
+    }
+    return tid == 0;
+}
+
+template <int N>
+__device__ __forceinline__ bool grid_sum_acc(Acc<double> (&a)[N], double* partials, unsigned* counter, int nblocks,
+                                             int bid, double (&out)[N]) {
+#pragma unroll
+    for (int n = 0; n < N; ++n) out[n] = a[n].value();
+    return grid_sum<N>(out, partials, counter, nblocks, bid);
+}
+
+
+// Scalar steps of Algorithm 1 after the preconditioner sweep (lines 3-4):
+// the stopping test on the updated residual and beta = kappa / kappa_old.
+__device__ __forceinline__ void prec_epilogue(SolveState* st, double rrv, double kv) {
+    st->rr = rrv;
+    st->kappa = kv;
+    st->pass += 1;
+    if (!(isfinite(rrv) && isfinite(kv)) || kv < 0.0) {
+        st->done = 1;
+        st->status = 5;   // PCG_BREAKDOWN
+    } else if (rrv == 0.0 || rrv < st->thresh2) {
+        st->done = 1;
+        st->status = 0;   // PCG_OK
+    } else if (st->pass > st->maxit) {
+        st->done = 1;
+        st->status = 4;   // PCG_NOT_CONVERGED
+    } else {
+        st->beta = kv / st->kappa_old;
+        st->kappa_old = kv;
+    }
+}
+
+// Scalar step after the SpMV sweep (line 6): alpha = kappa_old / sigma.
+__device__ __forceinline__ void spmv_epilogue(SolveState* st, double s) {
+    st->sigma = s;
+    if (!(s > 0.0) || !isfinite(s)) {
+        st->done = 1;
+        st->status = 5;   // PCG_BREAKDOWN
+        st->alpha = 0.0;
+    } else {
+        st->alpha = st->kappa_old / s;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -320,24 +440,8 @@ __global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__
         }
     }
     double v[2] = {rr.value(), kap.value()};
-    if (grid_sum<2>(v, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks)) {
-        const double rrv = v[0], kv = v[1];
-        st->rr = rrv;
-        st->kappa = kv;
-        st->pass += 1;
-        if (!(isfinite(rrv) && isfinite(kv)) || kv < 0.0) {
-            st->done = 1;
-            st->status = 5;   // PCG_BREAKDOWN
-        } else if (rrv == 0.0 || rrv < st->thresh2) {
-            st->done = 1;
-            st->status = 0;   // PCG_OK
-        } else if (st->pass > st->maxit) {
-            st->done = 1;
-            st->status = 4;   // PCG_NOT_CONVERGED
-        } else {
-            st->beta = kv / st->kappa_old;
-            st->kappa_old = kv;
-        }
+    if (grid_sum<2>(v, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2())) {
+        prec_epilogue(st, v[0], v[1]);
     }
 }
 
@@ -386,17 +490,270 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
         }
     }
     double v[1] = {sig.value()};
-    if (grid_sum<1>(v, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks)) {
-        const double s = v[0];
-        st->sigma = s;
-        if (!(s > 0.0) || !isfinite(s)) {
-            st->done = 1;
-            st->status = 5;   // PCG_BREAKDOWN
-            st->alpha = 0.0;
-        } else {
-            st->alpha = st->kappa_old / s;
+    if (grid_sum<1>(v, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2())) {
+        spmv_epilogue(st, v[0]);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// The same two sweeps with each column split into chunks of LZ levels.
+//
+// One thread per (column, chunk) multiplies the number of threads by
+// n_z / LZ, and every load of a chunk is issued before any arithmetic (into
+// registers, and for the stencil's neighbours into a shared-memory tile), so
+// many more bytes are in flight per SM than with one thread per column.
+// The Thomas sweeps are linear recurrences with known coefficients, so a
+// chunk solves its part with zero carry-in and is corrected afterwards:
+//   forward   y_k = yl_k + P_k Y,   P_k = prod_{j=k0..k} (W_{j-1}/D_{j-1}),
+//   backward  z_k = zl_k + Q_k Z,   Q_k = prod_{j=k..k1-1} (W_j/D_j),
+// where Y (Z) is the true value just below (above) the chunk, obtained by a
+// scan over the chunks of the column in shared memory.  The products are
+// carried as C = 1 - P and D = 1 - Q built as C + e (1 - C) with
+// e = E/D_pivot, so no quantity close to 1 is subtracted from 1: this is the
+// excess form of the sweeps above, reassociated.
+// Preconditioner sweep: block = 32 columns of one row x (n_z/LZ) chunks.
+// ---------------------------------------------------------------------------
+template <typename T, int LZ>
+__global__ __launch_bounds__(256) void k_sweep_prec_chunked(OpView<T> op, T* __restrict__ r, const T* __restrict__ q,
+                                                            T* __restrict__ z, SolveState* __restrict__ states,
+                                                            double* __restrict__ partials,
+                                                            unsigned* __restrict__ counters, int nblocks) {
+    __shared__ T sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
+    const int rhs = blockIdx.z;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const T alpha = (T)st->alpha;
+    const int lane = threadIdx.x, ch = threadIdx.y, nch = blockDim.y;
+    const Col<T> col = make_col(op, blockIdx.x * 32 + lane, blockIdx.y);
+    const int k0 = ch * LZ;
+    const int kn = min(LZ, op.nz - k0);          // levels in this chunk (<= 0: none)
+    const bool act = col.valid && kn > 0;
+    const bool full = act && kn == LZ;
+    const long long base = (long long)rhs * op.vol + col.c;
+    T* rb = r + base + (long long)k0 * op.plane;
+    const T* qb = q + base + (long long)k0 * op.plane;
+    T* zb = z + base + (long long)k0 * op.plane;
+    const long long fs = op.ncls;
+    const T* fg = op.fg + col.cls + (long long)k0 * fs;
+    const T* fe = op.fe + col.cls + (long long)k0 * fs;
+    const long long pl = op.plane;
+    Acc<T> acc[2];
+    T yv[LZ], gv[LZ], ev[LZ];
+    // all loads of the chunk first
+    if (full) {
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            yv[t] = fma(-alpha, qb[t * pl], rb[t * pl]);
+            gv[t] = ldro(fg + t * fs);
+            ev[t] = ldro(fe + t * fs);
+        }
+    } else if (act) {
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            if (t < kn) {
+                yv[t] = fma(-alpha, qb[t * pl], rb[t * pl]);
+                gv[t] = ldro(fg + t * fs);
+                ev[t] = ldro(fe + t * fs);
+            }
         }
     }
+    const T e_in = (act && k0 > 0) ? ldro(fe - fs) * ldro(fg - fs) : T(0);
+    // updated residual, ||r||^2, local forward sweep with zero carry-in
+    T yl = T(0), cp = T(0);
+    if (act) {
+        T ep = e_in;
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            if (t < kn) {
+                const T rn = yv[t];
+                rb[t * pl] = rn;
+                acc[0].add_prod(rn, rn);
+                yl = fma(-ep, yl, rn) + yl;
+                cp = (t == 0) ? ep : fma(ep, T(1) - cp, cp);
+                yv[t] = yl;
+                ep = ev[t] * gv[t];
+            }
+        }
+    }
+    sh_y[ch][lane] = yl;
+    sh_c[ch][lane] = cp;
+    __syncthreads();
+    T Y = T(0);
+    for (int cc = 0; cc < ch; ++cc) Y = fma(-sh_c[cc][lane], Y, sh_y[cc][lane]) + Y;
+    // corrected y, kappa, then the local backward sweep with zero carry-in
+    T zl = T(0), dp = T(0);
+    if (act) {
+        T ep = e_in;
+        cp = T(0);
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            if (t < kn) {
+                cp = (t == 0) ? ep : fma(ep, T(1) - cp, cp);
+                const T y = fma(-cp, Y, yv[t]) + Y;
+                yv[t] = y;
+                acc[1].add_prod(gv[t] * y, y);
+                ep = ev[t] * gv[t];
+            }
+        }
+        bool first = true;
+#pragma unroll
+        for (int t = LZ - 1; t >= 0; --t) {
+            if (t < kn) {
+                zl = fma(gv[t], fma(-ev[t], zl, yv[t]), zl);
+                const T e = ev[t] * gv[t];
+                dp = first ? e : fma(e, T(1) - dp, dp);
+                first = false;
+                yv[t] = zl;
+            }
+        }
+    }
+    sh_z[ch][lane] = zl;
+    sh_d[ch][lane] = dp;
+    __syncthreads();
+    T Z = T(0);
+    for (int cc = nch - 1; cc > ch; --cc) Z = fma(-sh_d[cc][lane], Z, sh_z[cc][lane]) + Z;
+    if (act) {
+        dp = T(0);
+        bool first = true;
+#pragma unroll
+        for (int t = LZ - 1; t >= 0; --t) {
+            if (t < kn) {
+                const T e = ev[t] * gv[t];
+                dp = first ? e : fma(e, T(1) - dp, dp);
+                first = false;
+                zb[t * pl] = fma(-dp, Z, yv[t]) + Z;
+            }
+        }
+    }
+    double v[2];
+    if (grid_sum_acc<2>(acc, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
+        prec_epilogue(st, v[0], v[1]);
+}
+
+// SpMV sweep: block = 32 x 4 columns, one chunk of LZ levels;
+// blockIdx.z = rhs * nchunks + chunk.  TILE = true stages the z values the
+// stencil needs (levels k0-1 .. k0+LZ, the block's columns plus a one-cell
+// halo, wrapped periodically or clamped at a Neumann edge where the face
+// weight is 0) in shared memory, one 34-wide row per warp load; TILE = false
+// reads the neighbours through the read-only cache.  Either way every load
+// of a full chunk is issued before the arithmetic.
+template <typename T, int LZ, bool TILE>
+__global__ __launch_bounds__(NT) void k_sweep_spmv_chunked(OpView<T> op, T* __restrict__ u, T* __restrict__ p,
+                                                           T* __restrict__ q, const T* __restrict__ z,
+                                                           SolveState* __restrict__ states,
+                                                           double* __restrict__ partials,
+                                                           unsigned* __restrict__ counters, int nblocks, int nchunks) {
+    constexpr int TX = BX + 2, TY = BY + 2, TP = TX * TY, NROW = (LZ + 2) * TY;
+    __shared__ T zt[TILE ? (LZ + 2) * TP : 1];
+    const int rhs = blockIdx.z / nchunks;
+    const int ch = blockIdx.z - rhs * nchunks;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const T alpha = (T)st->alpha;
+    const T beta = (T)st->beta;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const Col<T> col = make_col(op, i0 + tx, j0 + ty);
+    const int k0 = ch * LZ;
+    const int kn = min(LZ, op.nz - k0);
+    const long long pl = op.plane;
+    const long long base = (long long)rhs * op.vol;
+    const T* __restrict__ zb = z + base;
+    if (TILE) {
+        // lane tx loads tile columns tx and (tx < 2) 32 + tx: x indices wrapped once per thread
+        int ia = (i0 - 1 + tx) % op.nx;
+        if (ia < 0) ia += op.nx;
+        int ib = (i0 + 31 + tx) % op.nx;
+        for (int row = ty; row < NROW; row += BY) {
+            const int kk = row / TY, jj = row - kk * TY;
+            const int k = k0 - 1 + kk;
+            int j = j0 - 1 + jj;
+            if (op.periodic_y) {
+                j %= op.ny;
+                if (j < 0) j += op.ny;
+            } else {
+                j = j < 0 ? 0 : (j >= op.ny ? op.ny - 1 : j);
+            }
+            T* dst = zt + kk * TP + jj * TX;
+            if (k >= 0 && k < op.nz) {
+                const T* src = zb + (long long)k * pl + (long long)j * op.nx;
+                dst[tx] = ldro(src + ia);
+                if (tx < 2) dst[32 + tx] = ldro(src + ib);
+            } else {
+                dst[tx] = T(0);
+                if (tx < 2) dst[32 + tx] = T(0);
+            }
+        }
+    }
+    T ur[LZ], pr[LZ], qr[LZ], zr[LZ + 2];
+    const bool act = col.valid && kn > 0;
+    T* ub = u + base + col.c + (long long)k0 * pl;
+    T* pb = p + base + col.c + (long long)k0 * pl;
+    T* qb = q + base + col.c + (long long)k0 * pl;
+    if (act && kn == LZ) {
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            ur[t] = ub[t * pl];
+            pr[t] = pb[t * pl];
+            qr[t] = qb[t * pl];
+            if (!TILE) zr[t + 1] = ldro(zb + (long long)(k0 + t) * pl + col.c);
+        }
+        if (!TILE) {
+            zr[0] = k0 > 0 ? ldro(zb + (long long)(k0 - 1) * pl + col.c) : T(0);
+            zr[LZ + 1] = (k0 + LZ < op.nz) ? ldro(zb + (long long)(k0 + LZ) * pl + col.c) : zr[LZ];
+        }
+    } else if (act) {
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            if (t < kn) {
+                ur[t] = ub[t * pl];
+                pr[t] = pb[t * pl];
+                qr[t] = qb[t * pl];
+                if (!TILE) zr[t + 1] = ldro(zb + (long long)(k0 + t) * pl + col.c);
+            }
+        }
+        if (!TILE) zr[0] = k0 > 0 ? ldro(zb + (long long)(k0 - 1) * pl + col.c) : T(0);
+    }
+    if (TILE) __syncthreads();
+    Acc<T> sig[1];
+    if (act) {
+        const int c0 = (ty + 1) * TX + (tx + 1);
+        T zc = TILE ? zt[TP + c0] : zr[1];
+        T fprev = (k0 > 0) ? ldro(op.wv + k0 - 1) * ((TILE ? zt[c0] : zr[0]) - zc) : T(0);
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            if (t < kn) {
+                const int k = k0 + t;
+                const T zu = (k + 1 < op.nz) ? (TILE ? zt[(t + 2) * TP + c0] : (t + 1 < kn ? zr[t + 2] : zr[LZ + 1]))
+                                             : zc;
+                ub[t * pl] = fma(alpha, pr[t], ur[t]);
+                const T pn = fma(beta, pr[t], zc);
+                pb[t * pl] = pn;
+                const T f = ldro(op.wv + k) * (zc - zu);
+                T hz;
+                if (TILE) {
+                    const T* zl = zt + (t + 1) * TP;
+                    hz = col.me * (zc - zl[c0 + 1]);
+                    hz = fma(col.mw, zc - zl[c0 - 1], hz);
+                    hz = fma(col.mn, zc - zl[c0 + TX], hz);
+                    hz = fma(col.ms, zc - zl[c0 - TX], hz);
+                } else {
+                    hz = horiz(col, zb + (long long)k * pl, zc);
+                }
+                const T az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+                const T qn = fma(beta, qr[t], az);
+                qb[t * pl] = qn;
+                sig[0].add_prod(pn, qn);
+                fprev = f;
+                zc = zu;
+            }
+        }
+    }
+    double v[1];
+    const int bid = (ch * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (grid_sum_acc<1>(sig, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid, v))
+        spmv_epilogue(st, v[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -445,7 +802,7 @@ __global__ __launch_bounds__(NT) void k_residual(OpView<double> op, const double
         }
     }
     double v[3] = {bb, rr, rs};
-    if (grid_sum<3>(v, partials + (long long)rhs * nblocks * 3, counters + rhs, nblocks)) {
+    if (grid_sum<3>(v, partials + (long long)rhs * nblocks * 3, counters + rhs, nblocks, bid2())) {
         if (mode == 0) {
             st->bnorm2 = v[0];
             st->rr = v[1];

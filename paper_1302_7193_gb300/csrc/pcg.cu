@@ -71,6 +71,11 @@ struct pcg_ctx {
     unsigned* counters = nullptr;          // [nrhs]
     int nblocks = 0;
     dim3 grid, block;
+    // chunked sweeps (levels split across threads): launch shapes
+    int chunked32 = 0, chunked64 = 0, lz_a = 16, lz_b = 16, nch_b = 1;
+    int spmv32 = 0, spmv64 = 0;          // SpMV sweep variant: 0 per column, 1 chunked, 2 chunked + smem tile
+    dim3 grid_a, block_a, grid_b, block_b;
+    int nblk_a = 0, nblk_b = 0;
 
     cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -266,14 +271,42 @@ int ensure_ws32(pcg_t h) {
     return PCG_OK;
 }
 
+// Launch the preconditioner sweep / SpMV sweep in the variant chosen at creation.
+template <typename T>
+bool use_chunked(pcg_t h) { return sizeof(T) == 4 ? h->chunked32 != 0 : h->chunked64 != 0; }
+
+template <typename T>
+void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, SolveState* st) {
+    const bool chunked = use_chunked<T>(h);
+    if (chunked && h->lz_a == 16)
+        pcg::k_sweep_prec_chunked<T, 16><<<h->grid_a, h->block_a, 0, s>>>(v, r, q, z, st, h->partials, h->counters, h->nblk_a);
+    else if (chunked)
+        pcg::k_sweep_prec_chunked<T, 32><<<h->grid_a, h->block_a, 0, s>>>(v, r, q, z, st, h->partials, h->counters, h->nblk_a);
+    else
+        pcg::k_sweep_prec<T><<<h->grid, h->block, 0, s>>>(v, r, q, z, st, h->partials, h->counters, h->nblocks);
+}
+
+template <typename T>
+void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, T* z, SolveState* st) {
+    const int mode = sizeof(T) == 4 ? h->spmv32 : h->spmv64;
+    if (mode == 2)
+        pcg::k_sweep_spmv_chunked<T, 16, true><<<h->grid_b, h->block_b, 0, s>>>(v, u, p, q, z, st, h->partials,
+                                                                                h->counters, h->nblk_b, h->nch_b);
+    else if (mode == 1)
+        pcg::k_sweep_spmv_chunked<T, 16, false><<<h->grid_b, h->block_b, 0, s>>>(v, u, p, q, z, st, h->partials,
+                                                                                 h->counters, h->nblk_b, h->nch_b);
+    else
+        pcg::k_sweep_spmv<T><<<h->grid, h->block, 0, s>>>(v, u, p, q, z, st, h->partials, h->counters, h->nblocks);
+}
+
 // Capture `ppl` passes of Algorithm 1 (preconditioner sweep + SpMV sweep).
 template <typename T>
 int capture_passes(pcg_t h, OpView<T> v, T* u, T* r, T* z, T* p, T* q, SolveState* st, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     PCG_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < h->ppl; ++i) {
-        pcg::k_sweep_prec<T><<<h->grid, h->block, 0, h->cap_stream>>>(v, r, q, z, st, h->partials, h->counters, h->nblocks);
-        pcg::k_sweep_spmv<T><<<h->grid, h->block, 0, h->cap_stream>>>(v, u, p, q, z, st, h->partials, h->counters, h->nblocks);
+        launch_prec<T>(h, h->cap_stream, v, r, q, z, st);
+        launch_spmv<T>(h, h->cap_stream, v, u, p, q, z, st);
     }
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess) return fail(h, PCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -525,6 +558,39 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->block = dim3(BX, BY, 1);
     h->grid = dim3((h->nx + BX - 1) / BX, (h->ny + BY - 1) / BY, h->nrhs);
     h->nblocks = (int)(h->grid.x * h->grid.y);
+    // Sweep variants: the FP32 sweeps split every column into chunks of 16 or 32
+    // levels (up to 8 chunks; HBM latency needs the extra parallelism), the FP64
+    // sweeps keep one thread per column (they are bound by the FP64 pipe, which
+    // the chunk corrections would load further).  PCG_KERNELS=column|chunked
+    // overrides both.
+    h->chunked32 = h->nz <= 256 ? 1 : 0;
+    h->chunked64 = 0;
+    if (const char* kv = std::getenv("PCG_KERNELS")) {
+        if (!std::strcmp(kv, "column")) h->chunked32 = h->chunked64 = 0;
+        if (!std::strcmp(kv, "chunked") && h->nz <= 256) h->chunked32 = h->chunked64 = 1;
+    }
+    h->lz_a = h->nz <= 128 ? 16 : 32;
+    const int nch_a = (h->nz + h->lz_a - 1) / h->lz_a;
+    h->block_a = dim3(32, nch_a, 1);
+    h->grid_a = dim3((h->nx + 31) / 32, h->ny, h->nrhs);
+    h->nblk_a = (int)(h->grid_a.x * h->grid_a.y);
+    h->lz_b = 16;
+    h->nch_b = (h->nz + h->lz_b - 1) / h->lz_b;
+    h->block_b = dim3(BX, BY, 1);
+    h->grid_b = dim3((h->nx + BX - 1) / BX, (h->ny + BY - 1) / BY, h->nrhs * h->nch_b);
+    h->nblk_b = (int)(h->grid_b.x * h->grid_b.y) * h->nch_b;
+    if ((long long)h->nrhs * h->nch_b > 65535 || h->grid_a.y > 65535) h->chunked32 = h->chunked64 = 0;
+    // FP32 SpMV sweep: chunked while the grid has few columns (65536 columns:
+    // 76 us vs 124 us per sweep at 128 levels); one thread per column once there
+    // are enough columns to hide latency (2^20 columns: 902 us vs 1062 us).
+    // A shared-memory z tile with halo measured slower than both at both
+    // sizes and is kept only as an experiment (PCG_SPMV=tile).
+    h->spmv32 = (h->chunked32 && h->plane * (long long)h->nrhs < (1LL << 19)) ? 1 : 0;
+    h->spmv64 = h->chunked64 ? 1 : 0;
+    if (const char* sv = std::getenv("PCG_SPMV")) {            // experiments: column|chunked|tile
+        const int m = !std::strcmp(sv, "tile") ? 2 : (!std::strcmp(sv, "chunked") ? 1 : 0);
+        if (h->nz <= 256 && (long long)h->nrhs * h->nch_b <= 65535) h->spmv32 = h->spmv64 = m;
+    }
 
     auto bail = [&](int rc) {
         g_create_error = h->err;
@@ -543,7 +609,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if ((rc = dmalloc(h, &h->st, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->st_in, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->d_active, h->nrhs))) return bail(rc);
-    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * h->nblocks * 3))) return bail(rc);
+    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(h->nblocks, std::max(h->nblk_a, h->nblk_b)) * 3))) return bail(rc);
     if ((rc = dmalloc(h, &h->counters, h->nrhs))) return bail(rc);
     e = cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * h->nrhs, h->stream);
     if (e != cudaSuccess) { h->err = std::string("cudaMemset: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
@@ -657,18 +723,14 @@ int pcg_time_sweeps(pcg_t h, const double* b, int precision, int passes, double*
     for (int i = 0; i < passes; ++i) {
         PCG_CK(h, cudaEventRecord(ev[0], s));
         if (precision == PCG_FP64)
-            pcg::k_sweep_prec<double><<<h->grid, h->block, 0, s>>>(v, h->r64, h->q64, h->z64, h->st, h->partials,
-                                                                  h->counters, h->nblocks);
+            launch_prec<double>(h, s, v, h->r64, h->q64, h->z64, h->st);
         else
-            pcg::k_sweep_prec<float><<<h->grid, h->block, 0, s>>>(v32, h->r32, h->q32, h->z32, h->st_in,
-                                                                 h->partials, h->counters, h->nblocks);
+            launch_prec<float>(h, s, v32, h->r32, h->q32, h->z32, h->st_in);
         PCG_CK(h, cudaEventRecord(ev[1], s));
         if (precision == PCG_FP64)
-            pcg::k_sweep_spmv<double><<<h->grid, h->block, 0, s>>>(v, h->u64, h->p64, h->q64, h->z64, h->st,
-                                                                  h->partials, h->counters, h->nblocks);
+            launch_spmv<double>(h, s, v, h->u64, h->p64, h->q64, h->z64, h->st);
         else
-            pcg::k_sweep_spmv<float><<<h->grid, h->block, 0, s>>>(v32, h->u32, h->p32, h->q32, h->z32, h->st_in,
-                                                                 h->partials, h->counters, h->nblocks);
+            launch_spmv<float>(h, s, v32, h->u32, h->p32, h->q32, h->z32, h->st_in);
         PCG_CK(h, cudaEventRecord(ev[2], s));
         PCG_CK(h, cudaGetLastError());
         PCG_CK(h, cudaEventSynchronize(ev[2]));
