@@ -34,6 +34,21 @@ TOL = 1e-8
 WORKLOAD = "box256x256x128_fp64_tol1e-8"
 
 
+def _captured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or
+    None when the kernel source has changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1302_7193_gb300", "csrc", "kernels.cuh"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != d.get("kernels_cuh_sha256_16"):
+            return None
+        return d["kernels"][kernel]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -188,6 +203,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--profile-sweeps", choices=["fp64", "mixed"], default=None,
+                    help="profiling case: 3 passes of the fused sweeps on the benchmark grid, then exit")
     args = ap.parse_args()
     world, rank, local = dist_init()
 
@@ -202,6 +219,12 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.profile_sweeps:
+        p = W.medium_box()
+        bp = torch.from_numpy(W.medium_box_rhs(p).ravel()).to(dev)
+        with pkg.Solver(p) as s:
+            print(s.pcg_time_sweeps(bp, args.profile_sweeps, passes=3))
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
@@ -269,6 +292,7 @@ def main():
                 "frac": frac_alu, "traffic": None}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm, "traffic": None}
+    roof["traffic"] = _captured_traffic(f"k_sweep_{dom}<double>")
     roof.update({"kernel": f"k_sweep_{dom}<double>", "ms_per_launch": t_dom,
                  "hbm_gbs_algorithmic": gbs, "hbm_frac": frac_hbm, "peak_source": peak_kind,
                  "iteration_gbs_algorithmic": (bytes_prec + bytes_spmv) / ((ms_prec + ms_spmv) * 1e-3) / 1e9,

@@ -103,10 +103,14 @@ typedef struct {
     int status;                /* pcg_status of the solve                         */
     int iterations;            /* FP64: CG iterations (updates of u); MIXED: inner iterations summed over sweeps */
     int outer_sweeps;          /* MIXED: refinement sweeps taken; FP64: 0         */
-    int stagnated;             /* MIXED: 1 if refinement stopped because the FP64 residual stopped falling */
+    int stagnated;             /* MIXED: 1 if refinement stopped at the FP64 rounding floor (relres_floor) or
+                                  because the FP64 residual stopped falling      */
     double relres_recursive;   /* FP64: ||r_k||/||b|| of the updated residual at exit */
     double relres_true;        /* ||b - A x||/||b|| recomputed in FP64 after exit  */
     double elapsed_ms;         /* wall time of the call on the host               */
+    double relres_floor;       /* estimate of ||b - A fl(x)||/||b|| for x rounded to FP64,
+                                  sqrt(sum_i ulp(x_i)^2/12 ||A e_i||^2)/||b||: the smallest true
+                                  residual an FP64 vector can show for this solution */
 } pcg_stats_t;
 
 /* Create a solver for one grid and coefficient set (Section 4.2: the level

@@ -29,10 +29,10 @@ dense direct solves, manufactured-solution convergence).
 from .discretisation import (OperatorTerms, operator_terms, assemble_csr, apply_rows,
                              column_blocks, cell_volumes, FluxOperator)
 from .linesolve import LinePreconditioner
-from .pcg import pcg_textbook, pcg_interleaved, PCGResult
+from .pcg import pcg_textbook, pcg_interleaved, PCGResult, rounding_floor
 
 __all__ = [
     "OperatorTerms", "operator_terms", "assemble_csr", "apply_rows", "column_blocks", "cell_volumes",
     "FluxOperator",
-    "LinePreconditioner", "pcg_textbook", "pcg_interleaved", "PCGResult",
+    "LinePreconditioner", "pcg_textbook", "pcg_interleaved", "PCGResult", "rounding_floor",
 ]

@@ -132,3 +132,20 @@ def pcg_interleaved(A, precond: Callable, b: np.ndarray, u0: Optional[np.ndarray
         alpha = kappa_old / sigma
     u = u + alpha * p
     return PCGResult(u.reshape(shape), passes - 1, converged, hist, _true_relres(A, b, u))
+
+
+def rounding_floor(A, x: np.ndarray, b: np.ndarray) -> float:
+    """Expected ||b - A fl(x)|| / ||b|| when x is rounded to FP64.
+
+    Rounding perturbs each x_j by an independent error uniform in
+    [-ulp(x_j)/2, ulp(x_j)/2] (variance ulp^2/12), so
+    E ||A dx||^2 = sum_j ulp(x_j)^2/12 ||A e_j||^2.  No FP64 vector near the
+    solution can show a smaller true residual than about this value.
+    ``A`` is the assembled matrix (its column norms are used).
+    """
+    xf = np.asarray(x, dtype=np.float64).ravel()
+    ulp = np.spacing(np.abs(xf))
+    a2 = A.multiply(A)
+    col2 = np.asarray(a2.sum(axis=0)).ravel()
+    bn = float(np.linalg.norm(np.asarray(b).ravel()))
+    return float(np.sqrt(np.sum(ulp * ulp / 12.0 * col2)) / bn) if bn > 0 else 0.0

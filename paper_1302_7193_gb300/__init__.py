@@ -49,7 +49,8 @@ class pcg_opts_t(ctypes.Structure):
 class pcg_stats_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_sweeps", ctypes.c_int),
                 ("stagnated", ctypes.c_int), ("relres_recursive", ctypes.c_double),
-                ("relres_true", ctypes.c_double), ("elapsed_ms", ctypes.c_double)]
+                ("relres_true", ctypes.c_double), ("elapsed_ms", ctypes.c_double),
+                ("relres_floor", ctypes.c_double)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -108,6 +109,7 @@ class Stats:
     relres_recursive: float
     relres_true: float
     elapsed_ms: float
+    relres_floor: float = 0.0
 
     @property
     def status_name(self) -> str:
@@ -115,7 +117,8 @@ class Stats:
 
 
 def _stats(s: pcg_stats_t) -> Stats:
-    return Stats(s.status, s.iterations, s.outer_sweeps, s.stagnated, s.relres_recursive, s.relres_true, s.elapsed_ms)
+    return Stats(s.status, s.iterations, s.outer_sweeps, s.stagnated, s.relres_recursive, s.relres_true, s.elapsed_ms,
+                 s.relres_floor)
 
 
 def _dptr(arr, dtype_name: str, n: int) -> int:

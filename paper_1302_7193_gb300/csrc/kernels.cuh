@@ -55,6 +55,7 @@ struct SolveState {
     double rsum;        // sum_i (b - A x)_i (refinement: constant-mode projection)
     double coarse;      // constant added to x by the refinement's coarse correction
     double rr_emit;     // <r', r'> of the inner right-hand side r' = b - A x - coarse A 1
+    double floor2;      // sum_i ulp(x_i)^2/12 ||A e_i||^2: expected ||A (fl(x) - x)||^2 of rounding x to FP64
     int done;           // 1 once the solve of this rhs has stopped
     int status;         // pcg_status of this rhs
     int pass;           // preconditioner sweeps completed
@@ -757,13 +758,20 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv_chunked(OpView<T> op, T* __re
 }
 
 // ---------------------------------------------------------------------------
-// Residual r = b - A x in FP64, with reductions of <b,b>, <r,r> and sum(r).
+// Residual r = b - A x in FP64, with reductions of <b,b>, <r,r>, sum(r) and
+// the rounding floor sum_i ulp(x_i)^2/12 ||A e_i||^2 (the expected squared
+// residual of x rounded to FP64: no FP64 vector gets closer to b than this).
 // mode 0: start of an FP64 solve: also u = x, writes r; sets the stopping threshold.
-// mode 1: true residual after a solve: writes nothing, stores rr_true.
-// mode 2: refinement, measure: writes nothing, stores bnorm2, rr and rsum.
+// mode 1: true residual after a solve: writes nothing, stores rr_true and floor2.
+// mode 2: refinement, measure: writes nothing, stores bnorm2, rr, rsum, floor2.
 // mode 3: refinement, emit: writes r' = b - A x - coarse * m (the inner
 //         right-hand side, in TO) and stores <r', r'> in rr_emit.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double ulp64(double x) {
+    const long long e = (__double_as_longlong(x) >> 52) & 0x7ff;
+    return e > 52 ? __longlong_as_double((e - 52) << 52) : 0.0;
+}
+
 template <typename TO>
 __global__ __launch_bounds__(NT) void k_residual(OpView<double> op, const double* __restrict__ b,
                                                  const double* __restrict__ x, double* __restrict__ u,
@@ -774,35 +782,48 @@ __global__ __launch_bounds__(NT) void k_residual(OpView<double> op, const double
     SolveState* st = states + rhs;
     const Col<double> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
     const double coarse = (mode == 3) ? st->coarse : 0.0;
-    double bb = 0.0, rr = 0.0, rs = 0.0;
+    const bool want_floor = (mode == 1 || mode == 2);
+    double bb = 0.0, rr = 0.0, rs = 0.0, fl = 0.0;
     if (col.valid) {
         const long long base = (long long)rhs * op.vol;
         const double* __restrict__ xb = x + base;
         const double* __restrict__ bbp = b + base + col.c;
+        const double hsum2 = col.me * col.me + col.mw * col.mw + col.mn * col.mn + col.ms * col.ms;
+        const double hsum = (col.me + col.mw) + (col.mn + col.ms);
         double zc = xb[col.c];
-        double fprev = 0.0;
+        double fprev = 0.0, wprev = 0.0;
 #pragma unroll 4
         for (int k = 0; k < op.nz; ++k) {
             const long long o = (long long)k * op.plane;
             const double* xl = xb + o;
             const double zu = (k + 1 < op.nz) ? ldro(xl + op.plane + col.c) : zc;
-            const double f = ldro(op.wv + k) * (zc - zu);
+            const double wk = ldro(op.wv + k);
+            const double f = wk * (zc - zu);
             const double hz = horiz(col, xl, zc);
+            const double dk = ldro(op.dk + k);
             const double cm = col.area * ldro(op.mass + k);
-            const double az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+            const double az = fma(dk, hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
             const double bv = bbp[o];
             const double rv = fma(-coarse, cm, bv - az);
             bb = fma(bv, bv, bb);
             rr = fma(rv, rv, rr);
             rs += rv;
+            if (want_floor) {
+                const double wu = col.area * wk, wd = col.area * wprev;
+                const double diag = cm + dk * hsum + wu + wd;
+                const double cn2 = diag * diag + dk * dk * hsum2 + wu * wu + wd * wd;
+                const double ul = ulp64(zc);
+                fl = fma(ul * ul, cn2, fl);
+            }
             if (mode == 0) u[base + o + col.c] = zc;
             if (mode == 0 || mode == 3) rout[base + o + col.c] = (TO)rv;
             fprev = f;
+            wprev = wk;
             zc = zu;
         }
     }
-    double v[3] = {bb, rr, rs};
-    if (grid_sum<3>(v, partials + (long long)rhs * nblocks * 3, counters + rhs, nblocks, bid2())) {
+    double v[4] = {bb, rr, rs, fl / 12.0};
+    if (grid_sum<4>(v, partials + (long long)rhs * nblocks * 4, counters + rhs, nblocks, bid2())) {
         if (mode == 0) {
             st->bnorm2 = v[0];
             st->rr = v[1];
@@ -814,10 +835,12 @@ __global__ __launch_bounds__(NT) void k_residual(OpView<double> op, const double
             }
         } else if (mode == 1) {
             st->rr_true = v[1];
+            st->floor2 = v[3];
         } else if (mode == 2) {
             st->bnorm2 = v[0];
             st->rr = v[1];
             st->rsum = v[2];
+            st->floor2 = v[3];
         } else {
             st->rr_emit = v[1];
         }
@@ -847,6 +870,7 @@ __global__ void k_init_state(SolveState* states, int nrhs, double tol2, int maxi
     s.rsum = 0.0;
     s.coarse = 0.0;
     s.rr_emit = 0.0;
+    s.floor2 = 0.0;
     s.pad_ = 0;
     states[r] = s;
 }

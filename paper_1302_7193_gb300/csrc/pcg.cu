@@ -67,7 +67,7 @@ struct pcg_ctx {
     SolveState* st_in = nullptr;           // [nrhs] inner FP32 state
     SolveState* h_st = nullptr;            // pinned [2][nrhs] poll slots
     int* d_active = nullptr;               // [nrhs]
-    double* partials = nullptr;            // [nrhs][nblocks][3]
+    double* partials = nullptr;            // [nrhs][nblocks][4]
     unsigned* counters = nullptr;          // [nrhs]
     int nblocks = 0;
     dim3 grid, block;
@@ -385,6 +385,7 @@ int solve_fp64(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_s
         o.outer_sweeps = 0;
         o.relres_recursive = q.bnorm2 > 0 ? std::sqrt(q.rr / q.bnorm2) : 0.0;
         o.relres_true = q.bnorm2 > 0 ? std::sqrt(q.rr_true / q.bnorm2) : 0.0;
+        o.relres_floor = q.bnorm2 > 0 ? std::sqrt(q.floor2 / q.bnorm2) : 0.0;
         if (o.status != PCG_OK && worst == PCG_OK) worst = o.status;
         if (o.status == PCG_BREAKDOWN) worst = PCG_BREAKDOWN;
     }
@@ -406,7 +407,7 @@ int solve_mixed(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_
     h->launches = 0;
     std::vector<int> active(nr, 1), done(nr, 0), status(nr, PCG_NOT_CONVERGED), stag(nr, 0), sweeps(nr, 0), inner_it(nr, 0);
     std::vector<std::vector<double>> hist(nr);
-    std::vector<double> bb(nr, 0.0), last_rr(nr, 0.0);
+    std::vector<double> bb(nr, 0.0), last_rr(nr, 0.0), floor_rel(nr, 0.0);
     pcg::k_init_state<<<(nr + 63) / 64, 64, 0, s>>>(h->st, nr, tol * tol, 0, nullptr);
     h->launches += 1;
     for (int m = 0; m <= h->max_outer; ++m) {
@@ -432,10 +433,13 @@ int solve_mixed(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_
                 continue;
             }
             const double rel = std::sqrt(rrv / bb[r]);
+            floor_rel[r] = std::sqrt(h->h_st[r].floor2 / bb[r]);
             hist[r].push_back(rel);
-            if (h->trace) std::fprintf(stderr, "[pcg] rhs %d sweep %d relres_true %.3e inner_its_so_far %d\n", r, m, rel, inner_it[r]);
+            if (h->trace) std::fprintf(stderr, "[pcg] rhs %d sweep %d relres_true %.3e floor %.3e inner_its_so_far %d\n", r, m, rel, floor_rel[r], inner_it[r]);
             if (!std::isfinite(rel)) { done[r] = 1; status[r] = PCG_BREAKDOWN; continue; }
             if (rel < tol) { done[r] = 1; status[r] = PCG_OK; continue; }
+            // within twice the residual of x rounded to FP64: no FP64 vector does better
+            if (rel <= 2.0 * floor_rel[r]) { done[r] = 1; status[r] = PCG_OK; stag[r] = 1; continue; }
             const size_t n = hist[r].size();
             if (n >= 3) {
                 // stop when the best residual so far has not fallen tenfold over two sweeps:
@@ -488,6 +492,7 @@ int solve_mixed(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_
         o.outer_sweeps = sweeps[r];
         o.stagnated = stag[r];
         o.relres_true = bb[r] > 0 ? std::sqrt(last_rr[r] / bb[r]) : 0.0;
+        o.relres_floor = floor_rel[r];
         o.relres_recursive = o.relres_true;
         if (o.status != PCG_OK && worst == PCG_OK) worst = o.status;
         if (o.status == PCG_BREAKDOWN) worst = PCG_BREAKDOWN;
@@ -507,6 +512,7 @@ void summarise(pcg_t h, pcg_stats_t* stats, int rc, double t0) {
         s.stagnated = std::max(s.stagnated, o.stagnated);
         s.relres_recursive = std::max(s.relres_recursive, o.relres_recursive);
         s.relres_true = std::max(s.relres_true, o.relres_true);
+        s.relres_floor = std::max(s.relres_floor, o.relres_floor);
     }
     s.elapsed_ms = now_ms() - t0;
     *stats = s;
@@ -609,7 +615,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if ((rc = dmalloc(h, &h->st, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->st_in, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->d_active, h->nrhs))) return bail(rc);
-    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(h->nblocks, std::max(h->nblk_a, h->nblk_b)) * 3))) return bail(rc);
+    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(h->nblocks, std::max(h->nblk_a, h->nblk_b)) * 4))) return bail(rc);
     if ((rc = dmalloc(h, &h->counters, h->nrhs))) return bail(rc);
     e = cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * h->nrhs, h->stream);
     if (e != cudaSuccess) { h->err = std::string("cudaMemset: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }

@@ -98,5 +98,5 @@ def test_binding_refuses_missing_library(tmp_path):
 
 def test_structs_match_header_layout():
     # field order and sizes of the ctypes mirrors equal the C structs
-    assert ctypes.sizeof(pkg.pcg_stats_t) == 4 * 4 + 3 * 8
+    assert ctypes.sizeof(pkg.pcg_stats_t) == 4 * 4 + 4 * 8
     assert ctypes.sizeof(pkg.pcg_opts_t) == 8 + 8 + 4 + 4 + 4 + 4 + 8

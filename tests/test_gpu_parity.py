@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import FluxOperator, LinePreconditioner, apply_rows, assemble_csr, pcg_interleaved
+from oracle import FluxOperator, LinePreconditioner, apply_rows, assemble_csr, pcg_interleaved, rounding_floor
 
 pytestmark = pytest.mark.gpu
 
@@ -266,3 +266,22 @@ def test_medium_box_full_size(torch_cuda):
     rt = np.linalg.norm(b.ravel() - FluxOperator(p) @ xs) / np.linalg.norm(b)
     assert abs(rt - st.relres_true) <= 1e-3 * rt
     assert rt < 1e-4
+
+
+@pytest.mark.parametrize("name,p", [c for c in SOLVE_CASES if c[0] in ("box32x32x16", "box64x64x128_d0.004", "latlon72x32x16")],
+                         ids=["box32x32x16", "box64x64x128_d0.004", "latlon72x32x16"])
+def test_reported_rounding_floor(torch_cuda, name, p):
+    """The floor reported with each solve equals the oracle's rounding-floor
+    model for the returned x, and the mixed solve stops within twice it."""
+    torch = torch_cuda
+    b = W.rhs_for(p, seed=0, smooth=(p.kind == W.GEOM_BOX))
+    a = assemble_csr(p)
+    for precision in ("fp64", "mixed"):
+        with _solver(p, precision=precision) as s:
+            x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+            st = s.solve(_to_dev(torch, b), x, tol=1e-12, maxit=20000)
+        xg = x.cpu().numpy()
+        model = rounding_floor(a, xg, b)
+        assert abs(st.relres_floor - model) <= 0.05 * model, (precision, st.relres_floor, model)
+        if precision == "mixed":
+            assert st.relres_true <= 2.0 * st.relres_floor or st.relres_true < 1e-12

@@ -15,7 +15,8 @@ import pytest
 import scipy.linalg as sla
 
 import workloads as W
-from oracle import FluxOperator, LinePreconditioner, assemble_csr, column_blocks, pcg_interleaved, pcg_textbook
+from oracle import (FluxOperator, LinePreconditioner, assemble_csr, column_blocks, pcg_interleaved,
+                    pcg_textbook, rounding_floor)
 
 
 def _problems():
@@ -199,3 +200,20 @@ def test_oracle_solution_matches_refined_reference(p):
     res = pcg_interleaved(op, m, b, eps=1e-10, maxiter=5000)
     err = np.linalg.norm(res.x.ravel() - x) / np.linalg.norm(x)
     assert res.converged and err < 1e-11, err
+
+
+@pytest.mark.parametrize("p", [W.small_box(), W.medium_box(scale=8, n_z=64)], ids=["box32x32x16", "box32x32x64"])
+def test_rounding_floor_predicts_residual_of_rounded_solution(p):
+    """The floor model equals the measured true residual of the (refined)
+    solution rounded to FP64, evaluated with compensated arithmetic."""
+    op = FluxOperator(p)
+    a = assemble_csr(p)
+    m = LinePreconditioner(a, p)
+    b = W.rhs_for(p, seed=0, smooth=True)
+    x = np.zeros(p.n_cells)
+    for _ in range(4):
+        r = _accurate_residual(op, b, x)
+        x = x + pcg_textbook(op, m, r.reshape(p.shape), tol=1e-13, maxit=5000).x.ravel()
+    measured = np.linalg.norm(_accurate_residual(op, b, x)) / np.linalg.norm(b)
+    model = rounding_floor(a, x, b)
+    assert 0.8 < measured / model < 1.25, (measured, model)
