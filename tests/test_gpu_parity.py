@@ -285,3 +285,30 @@ def test_reported_rounding_floor(torch_cuda, name, p):
         assert abs(st.relres_floor - model) <= 0.05 * model, (precision, st.relres_floor, model)
         if precision == "mixed":
             assert st.relres_true <= 2.0 * st.relres_floor or st.relres_true < 1e-12
+
+
+def test_shell_batch_of_sixteen(torch_cuda):
+    """A reduced lat-lon band with 16 right-hand sides solved together: the
+    mixed batch matches the FP64 oracle per right-hand side, and each FP64
+    right-hand side equals its own single solve bitwise."""
+    torch = torch_cuda
+    p = W.latlon_problem(96, 40, 32)
+    seeds = list(range(16))
+    bs = W.batched_rhs(p, seeds)
+    with _solver(p, nrhs=16, precision="mixed") as s:
+        xm = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
+        st = s.solve(_to_dev(torch, bs), xm, tol=1e-10, maxit=20000)
+        assert st.status == 0
+    with _solver(p, nrhs=16) as s:
+        xf = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
+        s.solve(_to_dev(torch, bs), xf, tol=1e-10, maxit=20000)
+    xm = xm.cpu().numpy().reshape(bs.shape)
+    xf = xf.cpu().numpy().reshape(bs.shape)
+    with _solver(p) as s1:
+        for r in (0, 7, 15):
+            ref = _oracle_solve(p, bs[r], eps=1e-12, maxiter=20000)
+            assert np.linalg.norm(xm[r] - ref.x) / np.linalg.norm(ref.x) < 1e-8
+            assert np.linalg.norm(xf[r] - ref.x) / np.linalg.norm(ref.x) < 1e-10
+            x1 = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+            s1.solve(_to_dev(torch, bs[r]), x1, tol=1e-10, maxit=20000)
+            assert np.array_equal(x1.cpu().numpy().reshape(p.shape), xf[r])
