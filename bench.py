@@ -195,6 +195,61 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, dev, pkg, W, torch):
+    """Served batch: Poisson arrivals (200 requests/s, seed 1) of solves with
+    random sizes {64..512}^2 x {32,64,128}, anisotropy 1e2-1e5 and lambda^2 in
+    [1e-4, 1], tol 1e-8, mixed precision, admission bounded by 60 GB.  Each
+    request is submitted at its arrival time; latency = submission to
+    retirement.  Right-hand sides are generated before the clock starts."""
+    import numpy as np
+    reqs = W.request_stream(duration_s=args.serve_seconds, rate_hz=200.0, seed=1)
+    rhs = [W.rhs_for(r.problem, seed=r.rhs_seed) for r in reqs]
+    stream = torch.cuda.current_stream(dev)
+    srv = pkg.Server(budget_bytes=60 * 10 ** 9, max_slots=256, stream=stream.cuda_stream)
+    # warm-up: one small request (graph capture, lazy module load)
+    w = W.box_problem(64, 64, 32, 0.001, lambda2=0.1)
+    wid = srv.submit(w, W.rhs_for(w, seed=5), tol=1e-8)
+    while srv.poll(wid, want_x=False) is None:
+        srv.step(8)
+    e0 = srv.info()["epochs"]
+    t0 = time.perf_counter()
+    i, live, done = 0, {}, []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        while i < len(reqs) or live:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i].arrival_s <= now:
+                live[srv.submit(reqs[i].problem, rhs[i], tol=reqs[i].tol)] = reqs[i]
+                rhs[i] = None
+                i += 1
+            if not live:
+                time.sleep(max(0.0, reqs[i].arrival_s - (time.perf_counter() - t0)))
+                continue
+            srv.step(8)
+            for rid in list(live):
+                got = srv.poll(rid, want_x=False)
+                if got is not None:
+                    done.append((live.pop(rid), got[1]))
+    elapsed = time.perf_counter() - t0
+    clocks = clk.summary()
+    epochs = srv.info()["epochs"] - e0
+    srv.close()
+    lat = np.array([st.elapsed_ms for _, st in done])
+    ok = sum(1 for _, st in done if st.status == 0)
+    inner_bytes = sum(44.0 * r.problem.n_cells * st.iterations for r, st in done)
+    unknowns = sum(r.problem.n_cells for r, _ in done)
+    line = {"metric": "PCG solves/s", "value": len(done) / elapsed, "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "workload": "serve",
+            "config": {"arrivals": "Poisson 200/s, seed 1", "seconds_of_arrivals": args.serve_seconds,
+                       "requests": len(reqs), "budget_gb": 60, "max_slots": 256, "tol": 1e-8,
+                       "mean_unknowns": unknowns / max(1, len(done))},
+            "completed": len(done), "converged": ok, "elapsed_s": elapsed,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "inner_epochs": epochs, "fp32_inner_gbs_algorithmic": inner_bytes / elapsed / 1e9,
+            "worst_relres_true": max(st.relres_true for _, st in done), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_other_workload(args, dev, pkg, W, torch):
     """The larger configurations, one JSON line each: FP64 and mixed solves of
     the same batch, device-timed, with the error of the mixed solution against
@@ -250,9 +305,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", choices=["box256", "box1024", "shell-batch"], default="box256",
+    ap.add_argument("--workload", choices=["box256", "box1024", "shell-batch", "serve"], default="box256",
                     help="box256: the benchmark (default); box1024: 1024x1024x128 box with variable alpha, "
-                         "FP64 and mixed; shell-batch: 1440x640x64 lat-lon band, 16 right-hand sides, FP64 and mixed")
+                         "FP64 and mixed; shell-batch: 1440x640x64 lat-lon band, 16 right-hand sides, FP64 and mixed; "
+                         "serve: Poisson request stream through the served batch")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: seconds of arrivals (200 req/s)")
     ap.add_argument("--profile-sweeps", choices=["fp64", "mixed"], default=None,
                     help="profiling case: 3 passes of the fused sweeps on the benchmark grid, then exit")
     args = ap.parse_args()
@@ -269,6 +326,9 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "serve":
+        run_serve(args, dev, pkg, W, torch)
+        return
     if args.workload != "box256":
         run_other_workload(args, dev, pkg, W, torch)
         return

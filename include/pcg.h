@@ -51,7 +51,8 @@ enum pcg_status {
     PCG_ERR_CUDA = 3,          /* a CUDA runtime call failed (text in last_error) */
     PCG_NOT_CONVERGED = 4,     /* maxit reached before the stopping test passed  */
     PCG_BREAKDOWN = 5,         /* <p,Ap> <= 0, <r,z> < 0 or a non-finite scalar    */
-    PCG_TIMEOUT = 6            /* a bounded device wait gave up (serving only)    */
+    PCG_TIMEOUT = 6,           /* reserved: no entry point waits on the device without a bound */
+    PCG_PENDING = 7            /* pcg_serve_poll: the request has not finished yet */
 };
 
 /* ---- geometry / precision selectors ------------------------------------- */
@@ -65,6 +66,7 @@ enum pcg_precision {
 };
 
 typedef struct pcg_ctx* pcg_t;
+typedef struct pcg_server* pcg_server_t;
 
 /* Grid (Section 3.1: tensor product of a horizontal grid and a graded
  * vertical grid).  z_iface: host array of n_z+1 strictly increasing
@@ -181,6 +183,55 @@ int pcg_time_sweeps(pcg_t h, const double* b, int precision, int passes, double*
  * thread-safe on the host.  Errors: PCG_ERR_INVALID_ARG, PCG_ERR_CUDA (text
  * in pcg_last_error(NULL)). */
 int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const double* r, double* z, void* stream);
+
+/* ---- served batch (continuous batching of many solves) ------------------ */
+
+/* Create a server that solves many independent problems of different grids,
+ * coefficients and right-hand sides together in the mixed-precision form
+ * (FP32 inner Algorithm 1 inside FP64 refinement, as pcg_solve with
+ * PCG_MIXED).  budget_bytes bounds the device memory of admitted requests
+ * (tables, FP64 x and b, five FP32 inner vectors; about 36 bytes per unknown);
+ * max_slots bounds how many are admitted at once (<= 4096).  opts (may be
+ * NULL): inner_tol, inner_maxit, max_outer as for pcg_create;
+ * passes_per_launch = epochs per CUDA-graph launch (default 8); stream.
+ * Errors: PCG_ERR_INVALID_ARG, PCG_ERR_OOM, PCG_ERR_CUDA. */
+int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts, pcg_server_t* out);
+
+/* Queue one solve (nrhs must be 1).  grid, coeffs, b_host (n_z*n_y*n_x
+ * values, layout as everywhere) are copied; tol as for pcg_solve with
+ * PCG_MIXED.  The request is admitted by a later pcg_serve_step when a slot
+ * and the byte budget allow (first in, first out).  A request larger than
+ * the whole budget fails here with PCG_ERR_OOM; invalid geometry with
+ * PCG_ERR_INVALID_ARG.  *req_id identifies the request. */
+int pcg_serve_submit(pcg_server_t s, const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const double* b_host,
+                     double tol, uint64_t* req_id);
+
+/* Advance the served batch: admit waiting requests, run the FP64
+ * refinement steps that are due, and run inner PCG epochs (one epoch = one
+ * pass of Algorithm 1 for every request in its inner phase, executed by
+ * persistent kernels over the work list of (request, 32x4-column tile)
+ * items) until at least max_epochs epochs have run or no request has inner
+ * work; requests that finish are retired and their memory returned.
+ * Blocks the host.  *n_active / *n_pending (may be NULL): requests admitted /
+ * still queued afterwards. */
+int pcg_serve_step(pcg_server_t s, int max_epochs, int* n_active, int* n_pending);
+
+/* PCG_PENDING while request req_id is unfinished; once finished, copies x
+ * (host, n_z*n_y*n_x values; may be NULL) and the statistics (elapsed_ms =
+ * submission to retirement) and returns PCG_OK, after which the id is
+ * forgotten.  The request's own outcome is stats->status. */
+int pcg_serve_poll(pcg_server_t s, uint64_t req_id, double* x_host, pcg_stats_t* stats);
+
+/* Counters of the server: admitted and queued requests, device bytes held
+ * by admitted requests, inner epochs run so far.  Any pointer may be NULL. */
+int pcg_serve_info(pcg_server_t s, int* n_active, int* n_pending, size_t* used_bytes, long long* epochs);
+
+/* Text of the last error of the server (or of the last failed
+ * pcg_server_create on this thread when s is NULL). */
+const char* pcg_server_last_error(pcg_server_t s);
+
+/* Free all device and host memory of the server, finished or not. */
+void pcg_server_destroy(pcg_server_t s);
 
 /* Block the host until all work enqueued on the handle's stream is done. */
 int pcg_sync(pcg_t h);

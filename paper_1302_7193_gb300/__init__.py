@@ -18,15 +18,18 @@ from typing import Optional
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpcg.so")
 
-PCG_OK, PCG_ERR_INVALID_ARG, PCG_ERR_OOM, PCG_ERR_CUDA, PCG_NOT_CONVERGED, PCG_BREAKDOWN, PCG_TIMEOUT = range(7)
+PCG_OK, PCG_ERR_INVALID_ARG, PCG_ERR_OOM, PCG_ERR_CUDA, PCG_NOT_CONVERGED, PCG_BREAKDOWN, PCG_TIMEOUT, PCG_PENDING = range(8)
 PCG_GEOM_BOX, PCG_GEOM_LATLON = 0, 1
 PCG_FP64, PCG_MIXED = 0, 1
-STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "not_converged", 5: "breakdown", 6: "timeout"}
+STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "not_converged", 5: "breakdown", 6: "timeout",
+                7: "pending"}
 
 EXPORTED = (
     "pcg_create", "pcg_solve", "pcg_solve_host", "pcg_rhs_stats", "pcg_apply_A", "pcg_precond",
     "pcg_apply_A_f32", "pcg_precond_f32", "pcg_time_sweeps", "pcg_sync", "pcg_device_bytes", "pcg_kernel_launches",
     "pcg_last_error", "pcg_destroy", "pcg_precond_noalloc",
+    "pcg_server_create", "pcg_serve_submit", "pcg_serve_step", "pcg_serve_poll", "pcg_serve_info",
+    "pcg_server_last_error", "pcg_server_destroy",
 )
 
 
@@ -90,6 +93,22 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pcg_destroy.restype = None
     lib.pcg_precond_noalloc.argtypes = [ctypes.POINTER(pcg_grid_t), ctypes.POINTER(pcg_coeffs_t), P, P, P]
     lib.pcg_precond_noalloc.restype = I
+    lib.pcg_server_create.argtypes = [ctypes.c_size_t, I, ctypes.POINTER(pcg_opts_t), ctypes.POINTER(ctypes.c_void_p)]
+    lib.pcg_server_create.restype = I
+    lib.pcg_serve_submit.argtypes = [P, ctypes.POINTER(pcg_grid_t), ctypes.POINTER(pcg_coeffs_t), P, D,
+                                     ctypes.POINTER(ctypes.c_uint64)]
+    lib.pcg_serve_submit.restype = I
+    lib.pcg_serve_step.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.pcg_serve_step.restype = I
+    lib.pcg_serve_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(pcg_stats_t)]
+    lib.pcg_serve_poll.restype = I
+    lib.pcg_serve_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t),
+                                   ctypes.POINTER(ctypes.c_longlong)]
+    lib.pcg_serve_info.restype = I
+    lib.pcg_server_last_error.argtypes = [P]
+    lib.pcg_server_last_error.restype = ctypes.c_char_p
+    lib.pcg_server_destroy.argtypes = [P]
+    lib.pcg_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -252,6 +271,107 @@ class Solver:
     def close(self):
         if self.h:
             self.lib.pcg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def problem_structs(problem, nrhs: int = 1):
+    """pcg_grid_t / pcg_coeffs_t of a problem description, with the arrays
+    they point to (keep the third value alive while the structs are used)."""
+    z, zp = _dbl(problem.z_iface)
+    be, bp = _dbl(problem.beta_iface)
+    ae, aep = _dbl(getattr(problem, "alpha_e", None))
+    an, anp = _dbl(getattr(problem, "alpha_n", None))
+    g = pcg_grid_t(int(problem.kind), int(problem.n_x), int(problem.n_y), int(problem.n_z), int(nrhs), zp,
+                   float(getattr(problem, "lx", 1.0)), float(getattr(problem, "ly", 1.0)),
+                   float(getattr(problem, "lat0", 0.0)), float(getattr(problem, "lat1", 0.0)))
+    c = pcg_coeffs_t(aep, anp, bp, float(problem.lambda2))
+    return g, c, (z, be, ae, an)
+
+
+class Server:
+    """One pcg_server_t: a served batch of mixed-precision solves."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, inner_tol: float = 0.0, inner_maxit: int = 0,
+                 max_outer: int = 0, epochs_per_launch: int = 0, stream: Optional[int] = None):
+        self.lib = load_library()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:
+                stream = 0
+        o = pcg_opts_t(PCG_MIXED, float(inner_tol), int(inner_maxit), int(max_outer), int(epochs_per_launch),
+                       ctypes.c_void_p(stream or 0))
+        h = ctypes.c_void_p()
+        rc = self.lib.pcg_server_create(ctypes.c_size_t(int(budget_bytes)), int(max_slots), ctypes.byref(o),
+                                        ctypes.byref(h))
+        if rc != PCG_OK:
+            raise PCGError(rc, self.lib.pcg_server_last_error(None).decode())
+        self.h = h
+        self.sizes = {}
+
+    def pcg_serve_submit(self, problem, b, tol: float = 1e-8) -> int:
+        import numpy as np
+        g, c, keep = problem_structs(problem)
+        n = int(problem.n_x) * int(problem.n_y) * int(problem.n_z)
+        bb = np.ascontiguousarray(b, dtype=np.float64).ravel()
+        rid = ctypes.c_uint64()
+        rc = self.lib.pcg_serve_submit(self.h, ctypes.byref(g), ctypes.byref(c), _hptr(bb, n), float(tol),
+                                       ctypes.byref(rid))
+        if rc != PCG_OK:
+            raise PCGError(rc, self.lib.pcg_server_last_error(self.h).decode())
+        self.sizes[rid.value] = n
+        return rid.value
+
+    submit = pcg_serve_submit
+
+    def pcg_serve_step(self, max_epochs: int = 8):
+        a, q = ctypes.c_int(), ctypes.c_int()
+        rc = self.lib.pcg_serve_step(self.h, int(max_epochs), ctypes.byref(a), ctypes.byref(q))
+        if rc != PCG_OK:
+            raise PCGError(rc, self.lib.pcg_server_last_error(self.h).decode())
+        return a.value, q.value
+
+    step = pcg_serve_step
+
+    def pcg_serve_poll(self, rid: int, want_x: bool = True):
+        """(x, Stats) once the request has finished, else None."""
+        import numpy as np
+        x = np.empty(self.sizes[rid]) if want_x else None
+        st = pcg_stats_t()
+        rc = self.lib.pcg_serve_poll(self.h, ctypes.c_uint64(rid), x.ctypes.data_as(ctypes.c_void_p) if want_x else None,
+                                     ctypes.byref(st))
+        if rc == PCG_PENDING:
+            return None
+        if rc != PCG_OK:
+            raise PCGError(rc, self.lib.pcg_server_last_error(self.h).decode())
+        del self.sizes[rid]
+        return x, _stats(st)
+
+    poll = pcg_serve_poll
+
+    def pcg_serve_info(self):
+        a, q, u, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t(), ctypes.c_longlong()
+        self.lib.pcg_serve_info(self.h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(u), ctypes.byref(e))
+        return {"active": a.value, "pending": q.value, "used_bytes": u.value, "epochs": e.value}
+
+    info = pcg_serve_info
+
+    def close(self):
+        if self.h:
+            self.lib.pcg_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -400,6 +400,37 @@ __global__ __launch_bounds__(NT) void k_precond(OpView<T> op, const T* __restric
 // <r, r>, z = M^{-1} r, kappa = <r, z>; the last block applies the stopping
 // test and forms beta = kappa / kappa_old.
 // ---------------------------------------------------------------------------
+// One column of the preconditioner sweep; r, q, z point at the column's
+// level-0 entry.
+template <typename T>
+__device__ __forceinline__ void prec_column(const OpView<T>& op, const Col<T>& col, T* __restrict__ rb,
+                                            const T* __restrict__ qb, T* __restrict__ zb, T alpha, Acc<T>& rr,
+                                            Acc<T>& kap) {
+    const T* fg = op.fg + col.cls;
+    const T* fe = op.fe + col.cls;
+    const long long fs = op.ncls;
+    T y = T(0), eprev = T(0);
+#pragma unroll 4
+    for (int k = 0; k < op.nz; ++k) {
+        const long long o = (long long)k * op.plane;
+        const T rn = fma(-alpha, qb[o], rb[o]);
+        rb[o] = rn;
+        rr.add_prod(rn, rn);
+        y = fma(-eprev, y, rn) + y;
+        zb[o] = y;
+        const T g = ldro(fg + k * fs);
+        kap.add_prod(g * y, y);
+        eprev = ldro(fe + k * fs) * g;
+    }
+    T zn = T(0);
+#pragma unroll 4
+    for (int k = op.nz - 1; k >= 0; --k) {
+        const long long o = (long long)k * op.plane;
+        zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, zb[o]), zn);
+        zb[o] = zn;
+    }
+}
+
 template <typename T>
 __global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__ r, const T* __restrict__ q,
                                                    T* __restrict__ z, SolveState* __restrict__ states,
@@ -410,46 +441,50 @@ __global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__
     if (st->done) return;
     const T alpha = (T)st->alpha;
     const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
-    Acc<T> rr, kap;
+    Acc<T> acc[2];
     if (col.valid) {
         const long long base = (long long)rhs * op.vol + col.c;
-        T* rb = r + base;
-        const T* qb = q + base;
-        T* zb = z + base;
-        const T* fg = op.fg + col.cls;
-        const T* fe = op.fe + col.cls;
-        const long long fs = op.ncls;
-        T y = T(0), eprev = T(0);
-#pragma unroll 4
-        for (int k = 0; k < op.nz; ++k) {
-            const long long o = (long long)k * op.plane;
-            const T rn = fma(-alpha, qb[o], rb[o]);
-            rb[o] = rn;
-            rr.add_prod(rn, rn);
-            y = fma(-eprev, y, rn) + y;
-            zb[o] = y;
-            const T g = ldro(fg + k * fs);
-            kap.add_prod(g * y, y);
-            eprev = ldro(fe + k * fs) * g;
-        }
-        T zn = T(0);
-#pragma unroll 4
-        for (int k = op.nz - 1; k >= 0; --k) {
-            const long long o = (long long)k * op.plane;
-            zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, zb[o]), zn);
-            zb[o] = zn;
-        }
+        prec_column<T>(op, col, r + base, q + base, z + base, alpha, acc[0], acc[1]);
     }
-    double v[2] = {rr.value(), kap.value()};
-    if (grid_sum<2>(v, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2())) {
+    double v[2];
+    if (grid_sum_acc<2>(acc, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
         prec_epilogue(st, v[0], v[1]);
-    }
 }
 
 // ---------------------------------------------------------------------------
 // SpMV sweep of Algorithm 1 (Algorithm 2): u <- u + alpha p, p <- z + beta p,
 // q <- A z + beta q, sigma = <p, q>; the last block forms alpha = kappa_old/sigma.
 // ---------------------------------------------------------------------------
+// One column of the SpMV sweep; u, p, q point at the column's level-0
+// entry, zb at level 0 of the right-hand side's z (the stencil reads
+// neighbouring columns).
+template <typename T>
+__device__ __forceinline__ void spmv_column(const OpView<T>& op, const Col<T>& col, T* __restrict__ ub,
+                                            T* __restrict__ pb, T* __restrict__ qb, const T* __restrict__ zb,
+                                            T alpha, T beta, Acc<T>& sig) {
+    T zc = zb[col.c];
+    T fprev = T(0);
+#pragma unroll 4
+    for (int k = 0; k < op.nz; ++k) {
+        const long long o = (long long)k * op.plane;
+        const T* zl = zb + o;
+        const T zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
+        const T pk = pb[o];
+        const T qk = qb[o];
+        ub[o] = fma(alpha, pk, ub[o]);
+        const T pn = fma(beta, pk, zc);
+        pb[o] = pn;
+        const T f = ldro(op.wv + k) * (zc - zu);
+        const T hz = horiz(col, zl, zc);
+        const T az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+        const T qn = fma(beta, qk, az);
+        qb[o] = qn;
+        sig.add_prod(pn, qn);
+        fprev = f;
+        zc = zu;
+    }
+}
+
 template <typename T>
 __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__ u, T* __restrict__ p,
                                                    T* __restrict__ q, const T* __restrict__ z,
@@ -461,41 +496,15 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
     const T alpha = (T)st->alpha;
     const T beta = (T)st->beta;
     const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
-    Acc<T> sig;
+    Acc<T> sig[1];
     if (col.valid) {
         const long long base = (long long)rhs * op.vol;
-        const T* __restrict__ zb = z + base;
-        T* ub = u + base + col.c;
-        T* pb = p + base + col.c;
-        T* qb = q + base + col.c;
-        T zc = zb[col.c];
-        T fprev = T(0);
-#pragma unroll 4
-        for (int k = 0; k < op.nz; ++k) {
-            const long long o = (long long)k * op.plane;
-            const T* zl = zb + o;
-            const T zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
-            const T pk = pb[o];
-            const T qk = qb[o];
-            ub[o] = fma(alpha, pk, ub[o]);
-            const T pn = fma(beta, pk, zc);
-            pb[o] = pn;
-            const T f = ldro(op.wv + k) * (zc - zu);
-            const T hz = horiz(col, zl, zc);
-            const T az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
-            const T qn = fma(beta, qk, az);
-            qb[o] = qn;
-            sig.add_prod(pn, qn);
-            fprev = f;
-            zc = zu;
-        }
+        spmv_column<T>(op, col, u + base + col.c, p + base + col.c, q + base + col.c, z + base, alpha, beta, sig[0]);
     }
-    double v[1] = {sig.value()};
-    if (grid_sum<1>(v, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2())) {
+    double v[1];
+    if (grid_sum_acc<1>(sig, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
         spmv_epilogue(st, v[0]);
-    }
 }
-
 
 // ---------------------------------------------------------------------------
 // The same two sweeps with each column split into chunks of LZ levels.
@@ -755,6 +764,68 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv_chunked(OpView<T> op, T* __re
     const int bid = (ch * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     if (grid_sum_acc<1>(sig, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid, v))
         spmv_epilogue(st, v[0]);
+}
+
+
+// ---------------------------------------------------------------------------
+// Served batch: persistent sweeps over a work list of (request slot, tile).
+//
+// Every admitted request owns a slot with its own tables, vectors, partials,
+// arrival counter and scalar state.  One launch of each kernel walks all
+// items of all requests (grid-stride, one 32 x 4-column tile per item, the
+// column loop above), so many small solves fill the GPU together; the last
+// tile of a request to finish forms that request's scalars exactly as the
+// per-solve kernels do, so a request's arithmetic does not depend on which
+// other requests share the launch.
+// ---------------------------------------------------------------------------
+struct ServeSlot {
+    OpView<float> op;           // FP32 tables of the request
+    float *u, *r, *z, *p, *q;   // inner FP32 vectors
+    SolveState* st;             // inner state
+    double* partials;           // [ntiles][4]
+    unsigned* counter;
+    int gx, ntiles;             // tiles per row (ceil(nx/32)) and in total
+};
+
+__global__ __launch_bounds__(NT) void k_serve_prec(const ServeSlot* __restrict__ slots, const int2* __restrict__ items,
+                                                   const int* __restrict__ n_items) {
+    const int n = *n_items;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
+        const int2 w = items[it];
+        const ServeSlot& s = slots[w.x];
+        SolveState* st = s.st;
+        if (!st->done) {
+            const float alpha = (float)st->alpha;
+            const int bx = w.y % s.gx, by = w.y / s.gx;
+            const Col<float> col = make_col(s.op, bx * BX + threadIdx.x, by * BY + threadIdx.y);
+            Acc<float> acc[2];
+            if (col.valid) prec_column<float>(s.op, col, s.r + col.c, s.q + col.c, s.z + col.c, alpha, acc[0], acc[1]);
+            double v[2];
+            if (grid_sum_acc<2>(acc, s.partials, s.counter, s.ntiles, w.y, v)) prec_epilogue(st, v[0], v[1]);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ __launch_bounds__(NT) void k_serve_spmv(const ServeSlot* __restrict__ slots, const int2* __restrict__ items,
+                                                   const int* __restrict__ n_items) {
+    const int n = *n_items;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
+        const int2 w = items[it];
+        const ServeSlot& s = slots[w.x];
+        SolveState* st = s.st;
+        if (!st->done) {
+            const float alpha = (float)st->alpha;
+            const float beta = (float)st->beta;
+            const int bx = w.y % s.gx, by = w.y / s.gx;
+            const Col<float> col = make_col(s.op, bx * BX + threadIdx.x, by * BY + threadIdx.y);
+            Acc<float> sig[1];
+            if (col.valid) spmv_column<float>(s.op, col, s.u + col.c, s.p + col.c, s.q + col.c, s.z, alpha, beta, sig[0]);
+            double v[1];
+            if (grid_sum_acc<1>(sig, s.partials, s.counter, s.ntiles, w.y, v)) spmv_epilogue(st, v[0]);
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -146,7 +146,9 @@ struct HostTables {
     std::vector<double> mass, wv, dk, area, mue, mun;
 };
 
-int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t) {
+int build_tables_core(const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t, std::string& err,
+                      double& total_mass) {
+    auto bad = [&](const char* m) { err = m; return PCG_ERR_INVALID_ARG; };
     const int nx = g->n_x, ny = g->n_y, nz = g->n_z;
     const double* z = g->z_iface;
     const double* beta = c->beta_iface;
@@ -157,12 +159,12 @@ int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables
     t.mue.assign((size_t)nx * ny, 0.0);
     t.mun.assign((size_t)nx * ny, 0.0);
     for (int k = 0; k <= nz; ++k) {
-        if (!std::isfinite(z[k]) || !std::isfinite(beta[k])) return fail(h, PCG_ERR_INVALID_ARG, "non-finite z_iface or beta_iface");
-        if (k > 0 && !(z[k] > z[k - 1])) return fail(h, PCG_ERR_INVALID_ARG, "z_iface must be strictly increasing");
+        if (!std::isfinite(z[k]) || !std::isfinite(beta[k])) return bad("non-finite z_iface or beta_iface");
+        if (k > 0 && !(z[k] > z[k - 1])) return bad("z_iface must be strictly increasing");
     }
     auto centre = [&](int k) { return 0.5 * (z[k] + z[k + 1]); };
     if (g->geometry == PCG_GEOM_BOX) {
-        if (!(g->lx > 0.0) || !(g->ly > 0.0)) return fail(h, PCG_ERR_INVALID_ARG, "box extents must be positive");
+        if (!(g->lx > 0.0) || !(g->ly > 0.0)) return bad("box extents must be positive");
         const double hx = g->lx / nx, hy = g->ly / ny;
         for (int k = 0; k < nz; ++k) {
             const double dz = z[k + 1] - z[k];
@@ -180,7 +182,7 @@ int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables
     } else if (g->geometry == PCG_GEOM_LATLON) {
         const double pi = 3.14159265358979323846;
         if (!(g->lat0 > -0.5 * pi && g->lat1 < 0.5 * pi && g->lat0 < g->lat1))
-            return fail(h, PCG_ERR_INVALID_ARG, "latitude band must satisfy -pi/2 < lat0 < lat1 < pi/2");
+            return bad("latitude band must satisfy -pi/2 < lat0 < lat1 < pi/2");
         const double dlon = 2.0 * pi / nx, dlat = (g->lat1 - g->lat0) / ny;
         for (int k = 0; k < nz; ++k) {
             // shell volume per unit solid angle, (r1^3 - r0^3)/3 without cancellation
@@ -202,13 +204,20 @@ int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables
             }
         }
     } else {
-        return fail(h, PCG_ERR_INVALID_ARG, "unknown geometry");
+        return bad("unknown geometry");
     }
     // sum over all cells of |T_j| a_k = sum_i (A 1)_i, the Galerkin coarse operator on the constant vector
     double sa = 0.0, sm = 0.0;
     for (int j = 0; j < ny; ++j) sa += t.area[j];
     for (int k = 0; k < nz; ++k) sm += t.mass[k];
-    h->total_mass = (double)nx * sa * sm;
+    total_mass = (double)nx * sa * sm;
+    return PCG_OK;
+}
+
+int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t) {
+    std::string err;
+    const int rc = build_tables_core(g, c, t, err, h->total_mass);
+    if (rc) return fail(h, rc, err);
     return PCG_OK;
 }
 
@@ -927,3 +936,5 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
     if (e != cudaSuccess) return noalloc_fail(PCG_ERR_CUDA, cudaGetErrorString(e));
     return PCG_OK;
 }
+
+#include "serve.cuh"

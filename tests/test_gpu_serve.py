@@ -1,0 +1,118 @@
+"""The served batch (continuous batching of mixed-precision solves).
+
+* A request's result is the same alone and in a mix whose membership changes
+  while it runs (requests admitted and retired around it): bitwise, because
+  a request's arithmetic does not depend on the others; the bar asked of the
+  mixed path (1e-8 relative) is asserted as well.
+* Served results match the FP64 oracle to 1e-8.
+* Admission respects the device-byte budget; a request larger than the budget
+  is refused at submission; a request with a non-finite right-hand side ends
+  in breakdown without disturbing the others.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import FluxOperator, LinePreconditioner, assemble_csr, pcg_interleaved
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need cuda:0"
+    import paper_1302_7193_gb300 as pkg
+    from paper_1302_7193_gb300 import build as B
+    B.build()
+    return pkg
+
+
+def _mix():
+    reqs = W.request_stream(duration_s=1.0, rate_hz=50.0, seed=7, sizes=(16, 32, 48), levels=(8, 16, 32),
+                            max_requests=8)
+    return [(r.problem, W.rhs_for(r.problem, seed=r.rhs_seed)) for r in reqs]
+
+
+def _drain(srv, ids, max_steps=100000):
+    out = {}
+    for _ in range(max_steps):
+        for i in list(ids):
+            got = srv.poll(i)
+            if got is not None:
+                out[i] = got
+                ids.remove(i)
+        if not ids:
+            return out
+        srv.step(8)
+    raise AssertionError("served requests did not finish")
+
+
+def test_alone_equals_in_mix(pkg):
+    mix = _mix()
+    probe = 3
+    p, b = mix[probe]
+    with pkg.Server(budget_bytes=1 << 30, max_slots=4) as srv:
+        rid = srv.submit(p, b, tol=1e-10)
+        alone = _drain(srv, [rid])[rid]
+    with pkg.Server(budget_bytes=1 << 30, max_slots=4) as srv:
+        ids = [srv.submit(q, bq, tol=1e-10) for q, bq in mix[:5]]       # probe is the fourth of five
+        srv.step(8)
+        ids += [srv.submit(q, bq, tol=1e-10) for q, bq in mix[5:]]      # arrive while the others run
+        res = _drain(srv, list(ids))
+    x_mix, st_mix = res[ids[probe]]
+    x_alone, st_alone = alone
+    assert st_mix.status == st_alone.status == 0
+    assert st_mix.iterations == st_alone.iterations and st_mix.outer_sweeps == st_alone.outer_sweeps
+    assert np.linalg.norm(x_mix - x_alone) <= 1e-8 * np.linalg.norm(x_alone)
+    assert np.array_equal(x_mix, x_alone)
+
+
+def test_served_results_match_oracle(pkg):
+    mix = _mix()[:4]
+    with pkg.Server(budget_bytes=1 << 30, max_slots=8) as srv:
+        ids = [srv.submit(q, bq, tol=1e-10) for q, bq in mix]
+        res = _drain(srv, list(ids))
+    for (p, b), rid in zip(mix, ids):
+        x, st = res[rid]
+        assert st.status == 0
+        ref = pcg_interleaved(FluxOperator(p), LinePreconditioner(assemble_csr(p), p), b, eps=1e-12, maxiter=20000)
+        assert np.linalg.norm(x - ref.x.ravel()) / np.linalg.norm(ref.x) < 1e-8
+
+
+def test_budget_bounds_admission(pkg):
+    p = W.box_problem(64, 64, 32, 0.01, lambda2=0.1)
+    per = 36 * p.n_cells + 2 * 8 * (3 * 32 + 64 + 2 * 64 * 64 + 2 * 32) + 16 * 1024
+    with pkg.Server(budget_bytes=int(2.5 * per), max_slots=16) as srv:
+        ids = [srv.submit(p, W.rhs_for(p, seed=s), tol=1e-8) for s in range(5)]
+        peak = 0
+        out = {}
+        for _ in range(100000):
+            for i in list(ids):
+                got = srv.poll(i, want_x=False)
+                if got is not None:
+                    out[i] = got
+                    ids.remove(i)
+            if not ids:
+                break
+            active, pending = srv.step(4)
+            peak = max(peak, active)
+            assert srv.info()["used_bytes"] <= 2.5 * per
+        assert not ids and peak == 2
+        assert all(st.status == 0 for _, st in out.values())
+
+
+def test_oversize_and_bad_requests(pkg):
+    small = W.box_problem(16, 16, 8, 0.01)
+    with pkg.Server(budget_bytes=64 << 20, max_slots=4) as srv:
+        big = W.box_problem(512, 512, 64, 0.01)
+        with pytest.raises(pkg.PCGError) as e:
+            srv.submit(big, np.zeros(big.n_cells))
+        assert e.value.code == pkg.PCG_ERR_OOM
+        bad = W.rhs_for(small, seed=1)
+        bad.ravel()[17] = np.nan
+        good_id = srv.submit(small, W.rhs_for(small, seed=2), tol=1e-8)
+        bad_id = srv.submit(small, bad, tol=1e-8)
+        res = _drain(srv, [good_id, bad_id])
+    assert res[good_id][1].status == 0
+    assert res[bad_id][1].status == pkg.PCG_BREAKDOWN
