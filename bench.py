@@ -204,6 +204,7 @@ def run_serve(args, dev, pkg, W, torch):
     import numpy as np
     reqs = W.request_stream(duration_s=args.serve_seconds, rate_hz=200.0, seed=1)
     rhs = [W.rhs_for(r.problem, seed=r.rhs_seed) for r in reqs]
+    rhs_keep = list(rhs) if args.serve_compare else None
     stream = torch.cuda.current_stream(dev)
     srv = pkg.Server(budget_bytes=60 * 10 ** 9, max_slots=256, stream=stream.cuda_stream)
     # warm-up: one small request (graph capture, lazy module load)
@@ -246,7 +247,28 @@ def run_serve(args, dev, pkg, W, torch):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "inner_epochs": epochs, "fp32_inner_gbs_algorithmic": inner_bytes / elapsed / 1e9,
-            "worst_relres_true": max(st.relres_true for _, st in done), "clocks": clocks}
+            "worst_relres_true": max(st.relres_true for _, st in done),
+            "met_tol_or_floor": sum(1 for r, st in done
+                                    if st.relres_true < r.tol or st.relres_true <= 2.0 * st.relres_floor),
+            "clocks": clocks}
+    if args.serve_compare:
+        # the same requests one at a time, FP64 and mixed solver handles (creation included)
+        for prec in ("fp64", "mixed"):
+            t = 0.0
+            its = 0
+            for r, bnp in zip(reqs, rhs_keep):
+                bt = torch.from_numpy(bnp.ravel()).to(dev)
+                x = torch.zeros_like(bt)
+                torch.cuda.synchronize(dev)
+                t1 = time.perf_counter()
+                with pkg.Solver(r.problem, precision=prec, stream=stream.cuda_stream) as s1:
+                    st = s1.solve(bt, x, tol=r.tol, maxit=200000)
+                torch.cuda.synchronize(dev)
+                t += time.perf_counter() - t1
+                its += st.iterations
+            line[f"sequential_{prec}"] = {"solves_per_s": len(reqs) / t, "seconds": t, "iterations": its}
+        line["served_speedup_vs_sequential_fp64"] = line["value"] / line["sequential_fp64"]["solves_per_s"]
+        line["served_speedup_vs_sequential_mixed"] = line["value"] / line["sequential_mixed"]["solves_per_s"]
     print(json.dumps(line), flush=True)
 
 
@@ -310,6 +332,8 @@ def main():
                          "FP64 and mixed; shell-batch: 1440x640x64 lat-lon band, 16 right-hand sides, FP64 and mixed; "
                          "serve: Poisson request stream through the served batch")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: seconds of arrivals (200 req/s)")
+    ap.add_argument("--serve-compare", action="store_true",
+                    help="serve: also solve the same requests one at a time with the FP64 and mixed solvers")
     ap.add_argument("--profile-sweeps", choices=["fp64", "mixed"], default=None,
                     help="profiling case: 3 passes of the fused sweeps on the benchmark grid, then exit")
     args = ap.parse_args()

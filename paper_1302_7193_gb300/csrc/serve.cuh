@@ -77,6 +77,7 @@ struct pcg_server {
     cudaGraphExec_t graph = nullptr;
     int persistent_blocks = 152 * 8;
     long long epochs = 0, launches = 0, retired = 0;
+    int trace = 0;                      // PCG_TRACE=1: refinement history per request on stderr
     std::string err = "no error";
 };
 
@@ -246,6 +247,9 @@ int measure_and_decide(pcg_server_t s) {
             const double rel = std::sqrt(o.rr / q->bb);
             q->floor_rel = std::sqrt(o.floor2 / q->bb);
             q->hist.push_back(rel);
+            if (s->trace)
+                std::fprintf(stderr, "[serve] req %llu slot %d sweep %d relres_true %.3e floor %.3e inner_its %d\n",
+                             (unsigned long long)q->id, q->slot, q->sweeps, rel, q->floor_rel, q->inner_its);
             if (!std::isfinite(rel)) { q->status = PCG_BREAKDOWN; stop = true; }
             else if (rel < q->tol) { q->status = PCG_OK; stop = true; }
             else if (rel <= 2.0 * q->floor_rel) { q->status = PCG_OK; q->stag = 1; stop = true; }
@@ -328,6 +332,7 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
     if (!s) return sfail(nullptr, PCG_ERR_OOM, "host allocation failed");
     s->budget = budget_bytes;
     s->max_slots = max_slots;
+    if (const char* tr = std::getenv("PCG_TRACE")) s->trace = std::atoi(tr);
     if (opts) {
         if (opts->inner_tol > 0) s->inner_tol = opts->inner_tol;
         if (opts->inner_maxit > 0) s->inner_maxit = opts->inner_maxit;
