@@ -117,6 +117,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate_replicas(total_ms: float, steps: int, world: int, device=None):
+    """Replicas only: each rank solved `steps` problems of its own in
+    `total_ms`; the job's throughput is all ranks' solves over the slowest
+    rank's time (max over ranks via an all-reduce when world > 1).
+    Returns (solves/s, max_ms)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1000.0), total_ms
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -400,13 +414,8 @@ def main():
             iters.append(stats.iterations)
             launches += solver.kernel_launches
     barrier()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = aggregate_replicas(sum(times), args.steps, world, dev)
     clocks = clk.summary()
-    value = world * args.steps / (total_ms / 1000.0)
     ms_per_step = total_ms / args.steps
 
     # roofline of the fused sweeps (CUDA events around each launch, same stream)

@@ -524,8 +524,8 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
 // excess form of the sweeps above, reassociated.
 // Preconditioner sweep: block = 32 columns of one row x (n_z/LZ) chunks.
 // ---------------------------------------------------------------------------
-template <typename T, int LZ>
-__global__ __launch_bounds__(256) void k_sweep_prec_chunked(OpView<T> op, T* __restrict__ r, const T* __restrict__ q,
+template <typename T, int LZ, int MINB = 1>
+__global__ __launch_bounds__(256, MINB) void k_sweep_prec_chunked(OpView<T> op, T* __restrict__ r, const T* __restrict__ q,
                                                             T* __restrict__ z, SolveState* __restrict__ states,
                                                             double* __restrict__ partials,
                                                             unsigned* __restrict__ counters, int nblocks) {
@@ -648,8 +648,8 @@ __global__ __launch_bounds__(256) void k_sweep_prec_chunked(OpView<T> op, T* __r
 // weight is 0) in shared memory, one 34-wide row per warp load; TILE = false
 // reads the neighbours through the read-only cache.  Either way every load
 // of a full chunk is issued before the arithmetic.
-template <typename T, int LZ, bool TILE>
-__global__ __launch_bounds__(NT) void k_sweep_spmv_chunked(OpView<T> op, T* __restrict__ u, T* __restrict__ p,
+template <typename T, int LZ, bool TILE, int MINB = 1>
+__global__ __launch_bounds__(NT, MINB) void k_sweep_spmv_chunked(OpView<T> op, T* __restrict__ u, T* __restrict__ p,
                                                            T* __restrict__ q, const T* __restrict__ z,
                                                            SolveState* __restrict__ states,
                                                            double* __restrict__ partials,

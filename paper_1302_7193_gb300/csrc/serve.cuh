@@ -253,10 +253,10 @@ int measure_and_decide(pcg_server_t s) {
             if (!std::isfinite(rel)) { q->status = PCG_BREAKDOWN; stop = true; }
             else if (rel < q->tol) { q->status = PCG_OK; stop = true; }
             else if (rel <= 2.0 * q->floor_rel) { q->status = PCG_OK; q->stag = 1; stop = true; }
-            else if (q->hist.size() >= 3) {
+            else if (q->hist.size() >= 4) {
                 const double best_now = *std::min_element(q->hist.begin(), q->hist.end());
-                const double best_before = *std::min_element(q->hist.begin(), q->hist.end() - 2);
-                if (best_now > 0.1 * best_before) { q->status = PCG_OK; q->stag = 1; stop = true; }
+                const double best_before = *std::min_element(q->hist.begin(), q->hist.end() - 3);
+                if (best_now > 0.5 * best_before) { q->status = PCG_OK; q->stag = 1; stop = true; }
             }
             if (!stop && q->sweeps >= s->max_outer) { q->status = PCG_NOT_CONVERGED; stop = true; }
         }
