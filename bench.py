@@ -286,6 +286,47 @@ def run_serve(args, dev, pkg, W, torch):
     print(json.dumps(line), flush=True)
 
 
+def run_paper_panel(args, dev, pkg, W, torch):
+    """The paper's problem (one gnomonic cubed-sphere panel, 256 x 256 x 128,
+    omega^2 = 6.71e-4, lambda^2 = 3.32e-2, Section 7.2): residual reduced by
+    five orders, FP64 and the FP32 sweeps, next to the paper's interleaved
+    matrix-free times on an M2090 (Table 6: 8.8 ms DP, 5.6 ms SP per
+    iteration; Table 5: 0.96 s DP for 100 iterations including set-up and
+    transfers)."""
+    p = W.panel_problem(256, 256, 128)
+    bnp = W.rhs_for(p, seed=0)
+    b = torch.from_numpy(bnp.ravel()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    with pkg.Solver(p, stream=stream.cuda_stream) as s:
+        x = torch.zeros_like(b)
+        s.solve(b, x, tol=1e-5, maxit=10000)
+        x.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = s.solve(b, x, tol=1e-5, maxit=10000)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        tp64, ts64 = s.pcg_time_sweeps(b, "fp64", passes=10)
+        tp32, ts32 = s.pcg_time_sweeps(b, "mixed", passes=10)
+        xh = torch.zeros(p.n_cells, dtype=torch.float64).pin_memory().numpy()
+        bh = torch.from_numpy(bnp.ravel().copy()).pin_memory().numpy()
+        t0 = time.perf_counter()
+        s.solve_host(bh, xh, tol=1e-5, maxit=10000)
+        e2e_s = time.perf_counter() - t0
+    it64, it32 = tp64 + ts64, tp32 + ts32
+    line = {"workload": "paper-panel", "metric": "ms per PCG iteration", "unit": "ms", "higher_is_better": False,
+            "value": it64, "data": "synthetic",
+            "config": {"grid": [256, 256, 128], "omega2": 6.71e-4, "lambda2": 3.32e-2, "thickness": 0.01,
+                       "tol": 1e-5},
+            "fp64": {"iterations_to_1e-5": st.iterations, "solve_ms": ms, "ms_per_iteration": it64,
+                     "relres_true": st.relres_true, "e2e_with_copies_s": e2e_s,
+                     "vs_paper_m2090_dp_8.8ms": 8.8 / it64},
+            "fp32_sweeps": {"ms_per_iteration": it32, "vs_paper_m2090_sp_5.6ms": 5.6 / it32}}
+    print(json.dumps(line), flush=True)
+
+
 def run_other_workload(args, dev, pkg, W, torch):
     """The larger configurations, one JSON line each: FP64 and mixed solves of
     the same batch, device-timed, with the error of the mixed solution against
@@ -341,10 +382,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", choices=["box256", "box1024", "shell-batch", "serve"], default="box256",
+    ap.add_argument("--workload", choices=["box256", "box1024", "shell-batch", "serve", "paper-panel"],
+                    default="box256",
                     help="box256: the benchmark (default); box1024: 1024x1024x128 box with variable alpha, "
                          "FP64 and mixed; shell-batch: 1440x640x64 lat-lon band, 16 right-hand sides, FP64 and mixed; "
-                         "serve: Poisson request stream through the served batch")
+                         "serve: Poisson request stream through the served batch; paper-panel: the paper's own "
+                         "cubed-sphere panel problem, 256x256x128, residual reduced by 1e5")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: seconds of arrivals (200 req/s)")
     ap.add_argument("--serve-compare", action="store_true",
                     help="serve: also solve the same requests one at a time with the FP64 and mixed solvers")
@@ -366,6 +409,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.workload == "serve":
         run_serve(args, dev, pkg, W, torch)
+        return
+    if args.workload == "paper-panel":
+        run_paper_panel(args, dev, pkg, W, torch)
         return
     if args.workload != "box256":
         run_other_workload(args, dev, pkg, W, torch)

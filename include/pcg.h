@@ -9,10 +9,11 @@
  *
  *     -div_h(alpha grad_h u) - (1/S) d_z(S beta d_z u) + lambda^2 u = f
  *
- * on a tensor-product column grid: a periodic rectangle (S = 1) or a
+ * on a tensor-product column grid: a periodic rectangle (S = 1), a
  * latitude-longitude band of a spherical shell (S = r^2, Neumann at the
- * latitude edges), with Neumann conditions at the bottom and top of every
- * column.  The operator is never stored: each application recomputes the
+ * latitude edges) or one panel of a gnomonic cubed sphere (the paper's grid,
+ * S = r^2, Neumann at the panel edges), with Neumann conditions at the bottom
+ * and top of every column.  The operator is never stored: each application recomputes the
  * stencil from per-level profiles and per-column metric terms (Section 4.2).
  * The preconditioner is the vertical-line (block-Jacobi) preconditioner
  * M = block-diag(A), one tridiagonal solve per column (Section 4.1).  The
@@ -58,7 +59,9 @@ enum pcg_status {
 /* ---- geometry / precision selectors ------------------------------------- */
 enum pcg_geometry {
     PCG_GEOM_BOX = 0,          /* periodic lx x ly rectangle, heights z_iface    */
-    PCG_GEOM_LATLON = 1        /* lon periodic over 2 pi, lat in [lat0, lat1]    */
+    PCG_GEOM_LATLON = 1,       /* lon periodic over 2 pi, lat in [lat0, lat1]    */
+    PCG_GEOM_CUBED_PANEL = 2   /* one panel of an equidistant gnomonic cubed sphere (Section 3.2):
+                                  tangent coordinates [-1,1]^2, radii z_iface, Neumann panel edges */
 };
 enum pcg_precision {
     PCG_FP64 = 0,              /* FP64 storage and arithmetic throughout          */

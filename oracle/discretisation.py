@@ -41,6 +41,12 @@ latlon  longitude periodic over 2 pi (dlon = 2 pi/n_x), latitude
         mu_N(j) = alpha_n cos lat_{j+1/2} dlon / dlat (0 on the northern edge).
         The alpha_{T,T'} of the paper is the ratio of edge length to centre
         distance (Section 3.1); |T| is the cell area on the unit sphere.
+panel   one panel of an equidistant gnomonic cubed sphere (Section 3.2): cell
+        (i, j) covers [x_i, x_{i+1}] x [y_j, y_{j+1}] of the tangent plane
+        [-1, 1]^2, mapped to the unit sphere by P(x, y) = (1, x, y)/|(1, x, y)|;
+        |T_ij| = its solid angle, mu_E = alpha (arc of the east edge)/(arc
+        between the two cell centres), likewise north; radial factors as for
+        latlon; the four panel edges are Neumann (zero face weight).
 """
 from __future__ import annotations
 
@@ -49,14 +55,14 @@ import dataclasses
 import numpy as np
 import scipy.sparse as sp
 
-from workloads import GEOM_BOX, GEOM_LATLON, Problem
+from workloads import GEOM_BOX, GEOM_LATLON, GEOM_PANEL, Problem
 
 
 @dataclasses.dataclass
 class OperatorTerms:
     """Per-level and per-column factors of the tensor-product operator."""
 
-    area: np.ndarray      # (n_y,)       |T| per latitude row (constant for the box)
+    area: np.ndarray      # (n_y, n_x)   |T| of every column
     d: np.ndarray         # (n_z,)       horizontal-coupling weight per level
     mass: np.ndarray      # (n_z,)       a_k (zero-order term per unit area)
     w_up: np.ndarray      # (n_z,)       w_{k+1/2} per unit area (0 at the top level)
@@ -78,7 +84,7 @@ def operator_terms(p: Problem) -> OperatorTerms:
     if p.kind == GEOM_BOX:
         hx = p.lx / p.n_x
         hy = p.ly / p.n_y
-        area = np.full(p.n_y, hx * hy)
+        area = np.full((p.n_y, p.n_x), hx * hy)
         d = dz.copy()
         mass = p.lambda2 * dz
         w_up[:-1] = beta[1:-1] / gap
@@ -93,7 +99,7 @@ def operator_terms(p: Problem) -> OperatorTerms:
         # sin(a) - sin(b) = 2 cos((a+b)/2) sin((a-b)/2) and
         # r1^3 - r0^3 = (r1 - r0)(r1^2 + r1 r0 + r0^2): the same quantities
         # without the cancellation of two nearly equal numbers
-        area = dlon * 2.0 * np.cos(lat_c) * np.sin(0.5 * dlat)
+        area = np.broadcast_to((dlon * 2.0 * np.cos(lat_c) * np.sin(0.5 * dlat))[:, None], (p.n_y, p.n_x)).copy()
         d = dz.copy()
         mass = p.lambda2 * dz * (z[1:] * z[1:] + z[1:] * z[:-1] + z[:-1] * z[:-1]) / 3.0
         w_up[:-1] = beta[1:-1] * z[1:-1] ** 2 / gap
@@ -102,6 +108,50 @@ def operator_terms(p: Problem) -> OperatorTerms:
         mu_n = mu_n.copy()
         mu_n[-1, :] = 0.0                                       # northern edge: Neumann
         periodic_y = False
+    elif p.kind == GEOM_PANEL:
+        xf = -1.0 + 2.0 * np.arange(p.n_x + 1) / p.n_x
+        yf = -1.0 + 2.0 * np.arange(p.n_y + 1) / p.n_y
+        xc = 0.5 * (xf[1:] + xf[:-1])
+        yc = 0.5 * (yf[1:] + yf[:-1])
+
+        # all from unnormalised points (1, x, y) and exact coordinate
+        # differences, so that nothing small is taken as a difference of
+        # nearly equal quantities
+        def nrm(x, y):
+            return np.sqrt(1.0 + x * x + y * y)
+
+        def arc_same_y(x1, x2, y):          # points (1, x1, y), (1, x2, y)
+            return np.arctan2(np.abs(x2 - x1) * np.sqrt(1.0 + y * y), 1.0 + x1 * x2 + y * y)
+
+        def arc_same_x(x, y1, y2):          # points (1, x, y1), (1, x, y2)
+            return np.arctan2(np.abs(y2 - y1) * np.sqrt(1.0 + x * x), 1.0 + x * x + y1 * y2)
+
+        def tri(xa, ya, xb, yb, xc_, yc_):
+            # solid angle of a spherical triangle from unnormalised vertices
+            # (Van Oosterom and Strackee, 1983)
+            det = np.abs((xb - xa) * (yc_ - ya) - (xc_ - xa) * (yb - ya))
+            na, nb, nc = nrm(xa, ya), nrm(xb, yb), nrm(xc_, yc_)
+            ab = 1.0 + xa * xb + ya * yb
+            bc = 1.0 + xb * xc_ + yb * yc_
+            ca = 1.0 + xc_ * xa + yc_ * ya
+            return 2.0 * np.arctan2(det, na * nb * nc + ab * nc + bc * na + ca * nb)
+
+        X0, Y0 = np.meshgrid(xf[:-1], yf[:-1])
+        X1, Y1 = np.meshgrid(xf[1:], yf[1:])
+        area = tri(X0, Y0, X1, Y0, X1, Y1) + tri(X0, Y0, X1, Y1, X0, Y1)
+        XC, YC = np.meshgrid(xc, yc)
+        mu_e = np.zeros((p.n_y, p.n_x))
+        mu_e[:, :-1] = (arc_same_x(X1, Y0, Y1)[:, :-1]
+                        / arc_same_y(XC[:, :-1], XC[:, 1:], YC[:, :-1]))
+        mu_n = np.zeros((p.n_y, p.n_x))
+        mu_n[:-1, :] = (arc_same_y(X0, X1, Y1)[:-1, :]
+                        / arc_same_x(XC[:-1, :], YC[:-1, :], YC[1:, :]))
+        mu_e = ae * mu_e
+        mu_n = an * mu_n
+        d = dz.copy()
+        mass = p.lambda2 * dz * (z[1:] * z[1:] + z[1:] * z[:-1] + z[:-1] * z[:-1]) / 3.0
+        w_up[:-1] = beta[1:-1] * z[1:-1] ** 2 / gap
+        periodic_y = True       # the wrapped faces carry weight 0: Neumann edges
     else:
         raise ValueError(f"unknown geometry kind {p.kind}")
     return OperatorTerms(area=area, d=d, mass=mass, w_up=w_up, mu_e=mu_e, mu_n=mu_n,
@@ -116,7 +166,7 @@ def cell_volumes(p: Problem) -> np.ndarray:
         vz = z[1:] - z[:-1]
     else:
         vz = (z[1:] - z[:-1]) * (z[1:] * z[1:] + z[1:] * z[:-1] + z[:-1] * z[:-1]) / 3.0
-    return np.broadcast_to(vz[:, None, None] * t.area[None, :, None], p.shape).copy()
+    return np.broadcast_to(vz[:, None, None] * t.area[None, :, :], p.shape).copy()
 
 
 def _row_entries(p: Problem, t: OperatorTerms, k, j, i):
@@ -129,7 +179,7 @@ def _row_entries(p: Problem, t: OperatorTerms, k, j, i):
     k = np.asarray(k, dtype=np.int64)
     j = np.asarray(j, dtype=np.int64)
     i = np.asarray(i, dtype=np.int64)
-    area = t.area[j]
+    area = t.area[j, i]
     dk = t.d[k]
     ie = (i + 1) % nx
     iw = (i - 1) % nx
@@ -197,7 +247,7 @@ class FluxOperator:
         kk, jj, ii = np.meshgrid(np.arange(p.n_z), np.arange(p.n_y), np.arange(p.n_x), indexing="ij")
         k, j = kk.ravel(), jj.ravel()
         cols, vals = _row_entries(p, t, k, j, ii.ravel())
-        self.mass = t.area[j] * t.mass[k]
+        self.mass = t.area[j, ii.ravel()] * t.mass[k]
         rows = np.broadcast_to(np.arange(n, dtype=np.int64), cols[1:].shape)
         c = -vals[1:]
         keep = c != 0.0
@@ -234,7 +284,7 @@ def apply_rows(p: Problem, x: np.ndarray, cells) -> np.ndarray:
     cols, vals = _row_entries(p, t, k, j, i)
     xf = np.asarray(x, dtype=np.float64).reshape(-1)
     xi = xf[cols[0]]
-    y = t.area[j] * t.mass[k] * xi
+    y = t.area[j, i] * t.mass[k] * xi
     for f in range(1, 7):
         y = y + (-vals[f]) * (xi - xf[cols[f]])
     return y

@@ -40,7 +40,7 @@ class LinePreconditioner:
         kk, jj, ii = np.meshgrid(np.arange(p.n_z), np.arange(p.n_y), np.arange(p.n_x), indexing="ij")
         cols, vals = _row_entries(p, t, kk.ravel(), jj.ravel(), ii.ravel())
         own_col = cols[0] % (p.n_x * p.n_y)
-        rem = t.area[jj.ravel()] * t.mass[kk.ravel()]
+        rem = t.area[jj.ravel(), ii.ravel()] * t.mass[kk.ravel()]
         for f in range(1, 5):                       # horizontal neighbours in other columns
             other = (cols[f] % (p.n_x * p.n_y)) != own_col
             rem = rem + np.where(other, -vals[f], 0.0)

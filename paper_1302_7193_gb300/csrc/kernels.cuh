@@ -73,7 +73,7 @@ struct OpView {
     const T* mass;              // [nz] zero-order term per unit area
     const T* wv;                // [nz] vertical coupling per unit area between k and k+1 (0 at the top)
     const T* dk;                // [nz] weight of the horizontal couplings per level
-    const T* area;              // [ny] |T_j|
+    const T* area;              // [ny] |T_j|, or [ny][nx] |T_ij| when area_percol
     const T* mue;               // [ny][nx] east-face weight
     const T* mun;               // [ny][nx] north-face weight (0 on a Neumann edge)
     int periodic_y;
@@ -81,6 +81,7 @@ struct OpView {
     const T* fe;                // [nz][ncls] E_k = D_k - W_k
     int cls_mode;               // 0: one factor set; 1: per row j; 2: per column
     int ncls;
+    int area_percol;            // 1: area indexed by column (cubed-sphere panel)
 };
 
 // Per-thread accumulators: plain FP64, or compensated FP32 (exact product
@@ -139,7 +140,7 @@ __device__ __forceinline__ Col<T> make_col(const OpView<T>& op, int i, int j) {
     col.cw = (long long)jj * nx + iw;
     col.cn = (long long)jn * nx + ii;
     col.cs = (long long)js * nx + ii;
-    col.area = ldro(op.area + jj);
+    col.area = ldro(op.area + (op.area_percol ? col.c : (long long)jj));
     col.me = ldro(op.mue + col.c);
     col.mw = ldro(op.mue + col.cw);
     col.mn = ldro(op.mun + col.c);

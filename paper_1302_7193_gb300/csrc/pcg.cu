@@ -111,6 +111,7 @@ struct pcg_ctx {
         v.fe = (const T*)t.fe;
         v.cls_mode = cls_mode;
         v.ncls = ncls;
+        v.area_percol = geometry == PCG_GEOM_CUBED_PANEL ? 1 : 0;
         return v;
     }
 };
@@ -207,14 +208,54 @@ int build_tables_core(const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t,
                 t.mun[idx] = (j + 1 < ny) ? an * std::cos(ln) * dlon / dlat : 0.0;
             }
         }
+    } else if (g->geometry == PCG_GEOM_CUBED_PANEL) {
+        // equidistant gnomonic panel: tangent-plane cell [x_i, x_i+1] x [y_j, y_j+1] mapped by
+        // P(x, y) = (1, x, y)/|(1, x, y)|.  Area = solid angle of two spherical triangles by Van
+        // Oosterom and Strackee's formula for unnormalised vertices, face weight = alpha (edge
+        // arc)/(centre arc); every small quantity comes from exact coordinate differences.
+        auto nrm = [](double x, double y) { return std::sqrt(1.0 + x * x + y * y); };
+        auto arc_same_y = [](double x1, double x2, double y) {
+            return std::atan2(std::fabs(x2 - x1) * std::sqrt(1.0 + y * y), 1.0 + x1 * x2 + y * y);
+        };
+        auto arc_same_x = [](double x, double y1, double y2) {
+            return std::atan2(std::fabs(y2 - y1) * std::sqrt(1.0 + x * x), 1.0 + x * x + y1 * y2);
+        };
+        auto tri = [&](double xa, double ya, double xb, double yb, double xc_, double yc_) {
+            const double det = std::fabs((xb - xa) * (yc_ - ya) - (xc_ - xa) * (yb - ya));
+            const double na = nrm(xa, ya), nb = nrm(xb, yb), nc = nrm(xc_, yc_);
+            const double ab = 1.0 + xa * xb + ya * yb, bc = 1.0 + xb * xc_ + yb * yc_, ca = 1.0 + xc_ * xa + yc_ * ya;
+            return 2.0 * std::atan2(det, na * nb * nc + ab * nc + bc * na + ca * nb);
+        };
+        for (int k = 0; k < nz; ++k) {
+            const double r0 = z[k], r1 = z[k + 1];
+            t.mass[k] = c->lambda2 * ((r1 - r0) * (r1 * r1 + r1 * r0 + r0 * r0)) / 3.0;
+            t.dk[k] = r1 - r0;
+            t.wv[k] = (k + 1 < nz) ? beta[k + 1] * r1 * r1 / (centre(k + 1) - centre(k)) : 0.0;
+        }
+        t.area.assign((size_t)nx * ny, 0.0);
+        auto xf = [&](int i) { return -1.0 + 2.0 * i / nx; };
+        auto yf = [&](int j) { return -1.0 + 2.0 * j / ny; };
+        auto xc = [&](int i) { return 0.5 * (xf(i) + xf(i + 1)); };
+        auto yc = [&](int j) { return 0.5 * (yf(j) + yf(j + 1)); };
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                const size_t idx = (size_t)j * nx + i;
+                const double x0 = xf(i), x1 = xf(i + 1), y0 = yf(j), y1 = yf(j + 1);
+                t.area[idx] = tri(x0, y0, x1, y0, x1, y1) + tri(x0, y0, x1, y1, x0, y1);
+                const double ae = c->alpha_e ? c->alpha_e[idx] : 1.0;
+                const double an = c->alpha_n ? c->alpha_n[idx] : 1.0;
+                t.mue[idx] = (i + 1 < nx) ? ae * (arc_same_x(x1, y0, y1) / arc_same_y(xc(i), xc(i + 1), yc(j))) : 0.0;
+                t.mun[idx] = (j + 1 < ny) ? an * (arc_same_y(x0, x1, y1) / arc_same_x(xc(i), yc(j), yc(j + 1))) : 0.0;
+            }
+        }
     } else {
         return bad("unknown geometry");
     }
     // sum over all cells of |T_j| a_k = sum_i (A 1)_i, the Galerkin coarse operator on the constant vector
     double sa = 0.0, sm = 0.0;
-    for (int j = 0; j < ny; ++j) sa += t.area[j];
+    for (double a : t.area) sa += a;
     for (int k = 0; k < nz; ++k) sm += t.mass[k];
-    total_mass = (double)nx * sa * sm;
+    total_mass = (t.area.size() == (size_t)ny ? (double)nx : 1.0) * sa * sm;
     return PCG_OK;
 }
 
@@ -226,7 +267,7 @@ int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables
 }
 
 int upload_tables(pcg_t h, const HostTables& t) {
-    const size_t nz = h->nz, ny = h->ny, nxy = (size_t)h->nx * h->ny, nf = (size_t)nz * h->ncls;
+    const size_t nz = h->nz, ny = t.area.size(), nxy = (size_t)h->nx * h->ny, nf = (size_t)nz * h->ncls;
     const size_t n64 = 3 * nz + ny + 2 * nxy + 2 * nf;
     double* b64 = nullptr;
     float* b32 = nullptr;
@@ -570,9 +611,10 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->plane = plane;
     h->vol = plane * grid->n_z;
     h->ntot = h->vol * grid->nrhs;
-    h->periodic_y = grid->geometry == PCG_GEOM_BOX ? 1 : 0;
+    // the panel's edge faces carry weight 0, so its axes are walked as if periodic
+    h->periodic_y = grid->geometry == PCG_GEOM_LATLON ? 0 : 1;
     const bool field = coeffs->alpha_e || coeffs->alpha_n;
-    h->cls_mode = field ? 2 : (grid->geometry == PCG_GEOM_LATLON ? 1 : 0);
+    h->cls_mode = (field || grid->geometry == PCG_GEOM_CUBED_PANEL) ? 2 : (grid->geometry == PCG_GEOM_LATLON ? 1 : 0);
     h->ncls = h->cls_mode == 0 ? 1 : (h->cls_mode == 1 ? h->ny : (int)plane);
     if (opts) {
         h->precision = opts->precision;
@@ -948,6 +990,7 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
     v.fe = fe;
     v.cls_mode = cls_mode;
     v.ncls = (int)ncls;
+    v.area_percol = 0;
     // the factors are rewritten in full by every call, so nothing left by an
     // earlier call is read
     pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, s>>>(v, fg, fe);

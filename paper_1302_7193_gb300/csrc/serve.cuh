@@ -99,10 +99,18 @@ int sfail(pcg_server_t s, int code, const std::string& msg) {
 
 // Bytes one request needs on the device (tables in both precisions, FP64 x
 // and b, five FP32 inner vectors, partials and the arrival counter).
+int serve_cls_mode(const pcg_grid_t& g, bool field) {
+    return (field || g.geometry == PCG_GEOM_CUBED_PANEL) ? 2 : (g.geometry == PCG_GEOM_LATLON ? 1 : 0);
+}
+
+size_t area_count(const pcg_grid_t& g) {
+    return g.geometry == PCG_GEOM_CUBED_PANEL ? (size_t)g.n_x * g.n_y : (size_t)g.n_y;
+}
+
 size_t request_bytes(const pcg_grid_t& g, int cls_mode) {
     const size_t nx = g.n_x, ny = g.n_y, nz = g.n_z, nxy = nx * ny, vol = nxy * nz;
     const size_t ncls = cls_mode == 0 ? 1 : (cls_mode == 1 ? ny : nxy);
-    const size_t ntab = 3 * nz + ny + 2 * nxy + 2 * nz * ncls;
+    const size_t ntab = 3 * nz + area_count(g) + 2 * nxy + 2 * nz * ncls;
     const size_t ntiles = ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY);
     return align_up(ntab * 8) + align_up(ntab * 4) + 2 * align_up(vol * 8) + 5 * align_up(vol * 4) +
            align_up(ntiles * 4 * 8) + 256;
@@ -120,10 +128,11 @@ int admit(pcg_server_t s, ServeReq* q) {
     std::string err;
     int rc = build_tables_core(&g, &c, t, err, q->total_mass);
     if (rc) return sfail(s, rc, err);
-    const int cls_mode = (c.alpha_e || c.alpha_n) ? 2 : (g.geometry == PCG_GEOM_LATLON ? 1 : 0);
+    const int cls_mode = serve_cls_mode(g, c.alpha_e || c.alpha_n);
     const size_t nx = g.n_x, ny = g.n_y, nz = g.n_z, nxy = nx * ny, vol = nxy * nz;
     const size_t ncls = cls_mode == 0 ? 1 : (cls_mode == 1 ? ny : nxy);
-    const size_t ntab = 3 * nz + ny + 2 * nxy + 2 * nz * ncls;
+    const size_t na = area_count(g);
+    const size_t ntab = 3 * nz + na + 2 * nxy + 2 * nz * ncls;
     q->gx = (int)((nx + BX - 1) / BX);
     q->gy = (int)((ny + BY - 1) / BY);
     q->ntiles = q->gx * q->gy;
@@ -153,11 +162,12 @@ int admit(pcg_server_t s, ServeReq* q) {
         auto nxt = [&](size_t n) { T* p = base + off; off += n; return p; };
         op.nx = (int)nx; op.ny = (int)ny; op.nz = (int)nz;
         op.plane = (long long)nxy; op.vol = (long long)vol;
-        op.mass = nxt(nz); op.wv = nxt(nz); op.dk = nxt(nz); op.area = nxt(ny);
+        op.mass = nxt(nz); op.wv = nxt(nz); op.dk = nxt(nz); op.area = nxt(na);
         op.mue = nxt(nxy); op.mun = nxt(nxy);
         op.fg = nxt(nz * ncls); op.fe = nxt(nz * ncls);
-        op.periodic_y = g.geometry == PCG_GEOM_BOX ? 1 : 0;
+        op.periodic_y = g.geometry == PCG_GEOM_LATLON ? 0 : 1;
         op.cls_mode = cls_mode; op.ncls = (int)ncls;
+        op.area_percol = g.geometry == PCG_GEOM_CUBED_PANEL ? 1 : 0;
     };
     carve(q->op64, t64);
     carve(q->op32, t32);
@@ -165,7 +175,7 @@ int admit(pcg_server_t s, ServeReq* q) {
     SRV_CK(s, cudaMemcpyAsync((void*)q->op64.mass, t.mass.data(), nz * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemcpyAsync((void*)q->op64.wv, t.wv.data(), nz * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemcpyAsync((void*)q->op64.dk, t.dk.data(), nz * 8, cudaMemcpyHostToDevice, st));
-    SRV_CK(s, cudaMemcpyAsync((void*)q->op64.area, t.area.data(), ny * 8, cudaMemcpyHostToDevice, st));
+    SRV_CK(s, cudaMemcpyAsync((void*)q->op64.area, t.area.data(), na * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemcpyAsync((void*)q->op64.mue, t.mue.data(), nxy * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemcpyAsync((void*)q->op64.mun, t.mun.data(), nxy * 8, cudaMemcpyHostToDevice, st));
     pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, st>>>(q->op64, (double*)q->op64.fg, (double*)q->op64.fe);
@@ -401,7 +411,7 @@ int pcg_serve_submit(pcg_server_t s, const pcg_grid_t* grid, const pcg_coeffs_t*
         const int rc = build_tables_core(grid, coeffs, t, err, tm);
         if (rc) return sfail(s, rc, err);
     }
-    const int cls_mode = (coeffs->alpha_e || coeffs->alpha_n) ? 2 : (grid->geometry == PCG_GEOM_LATLON ? 1 : 0);
+    const int cls_mode = serve_cls_mode(*grid, coeffs->alpha_e || coeffs->alpha_n);
     const size_t need = request_bytes(*grid, cls_mode);
     if (need > s->budget) return sfail(s, PCG_ERR_OOM, "request needs more device memory than the server's budget");
     ServeReq* q = new (std::nothrow) ServeReq();
@@ -437,8 +447,7 @@ int pcg_serve_step(pcg_server_t s, int max_epochs, int* n_active, int* n_pending
             ServeReq* q = s->pending.front();
             bool free_slot = false;
             for (ServeReq* r : s->slot_req) if (!r) { free_slot = true; break; }
-            const int cls_mode = (!q->alpha_e.empty() || !q->alpha_n.empty()) ? 2
-                                 : (q->grid.geometry == PCG_GEOM_LATLON ? 1 : 0);
+            const int cls_mode = serve_cls_mode(q->grid, !q->alpha_e.empty() || !q->alpha_n.empty());
             if (!free_slot || s->used + request_bytes(q->grid, cls_mode) > s->budget) break;
             s->pending.pop_front();
             int rc = admit(s, q);

@@ -29,6 +29,7 @@ def _problems():
         W.box_problem(3, 3, 4, 0.01, lambda2=0.5, name="box-3"),
         W.latlon_problem(8, 5, 4, thickness=0.01, name="latlon"),
         W.box_problem(1, 2, 3, 0.01, name="box-1x2"),
+        W.panel_problem(6, 6, 5, thickness=0.05, name="panel"),
     ]
 
 
@@ -125,7 +126,7 @@ def test_latlon_band_area_and_volume():
     p = W.latlon_problem(36, 20, 6, thickness=0.05, lat_deg=70.0)
     t = operator_terms(p)
     band = 2 * np.pi * (math.sin(p.lat1) - math.sin(p.lat0))
-    assert abs(t.area.sum() * p.n_x - band) < 1e-13 * band
+    assert abs(t.area.sum() - band) < 1e-13 * band
     r0, r1 = p.z_iface[0], p.z_iface[-1]
     shell = band * (r1 ** 3 - r0 ** 3) / 3
     assert abs(cell_volumes(p).sum() - shell) < 1e-12 * shell
@@ -207,3 +208,32 @@ def test_manufactured_solution_latlon_second_order():
     e = [_mms_latlon(n) for n in (8, 16, 32)]
     ratios = [e[0] / e[1], e[1] / e[2]]
     assert all(3.3 < q < 4.8 for q in ratios), (e, ratios)
+
+
+# ---------------------------------------------------------------------------
+# Cubed-sphere panel (the paper's geometry, Section 3.2)
+# ---------------------------------------------------------------------------
+
+def test_panel_covers_a_sixth_of_the_sphere():
+    for n in (4, 17, 64):
+        t = operator_terms(W.panel_problem(n, n, 3))
+        assert abs(t.area.sum() - 4 * np.pi / 6) < 1e-12
+
+
+def test_panel_operator_commutes_with_the_panel_symmetries():
+    # the gnomonic panel is invariant under x <-> y and under x -> -x, y -> -y;
+    # the operator must commute with the induced permutations of the columns
+    p = W.panel_problem(7, 7, 4, thickness=0.05)
+    op = FluxOperator(p)
+    x = np.random.default_rng(9).standard_normal(p.shape)
+    ax = (op @ x).reshape(p.shape)
+    for perm in (lambda v: np.swapaxes(v, 1, 2), lambda v: v[:, :, ::-1], lambda v: v[:, ::-1, :]):
+        lhs = (op @ np.ascontiguousarray(perm(x))).reshape(p.shape)
+        np.testing.assert_allclose(lhs, perm(ax), rtol=1e-12, atol=1e-12 * np.abs(ax).max())
+
+
+def test_panel_edges_are_neumann():
+    p = W.panel_problem(5, 4, 3)
+    t = operator_terms(p)
+    assert (t.mu_e[:, -1] == 0).all() and (t.mu_n[-1, :] == 0).all()
+    assert (t.mu_e[:, :-1] > 0).all() and (t.mu_n[:-1, :] > 0).all()

@@ -25,6 +25,7 @@ import numpy as np
 
 GEOM_BOX = 0
 GEOM_LATLON = 1
+GEOM_PANEL = 2      # one panel of an equidistant gnomonic cubed sphere, tangent coordinates [-1, 1]^2
 
 
 @dataclasses.dataclass
@@ -126,6 +127,22 @@ def latlon_problem(n_lon, n_lat, n_z, *, thickness=0.002, lat_deg=80.0, ratio=1.
     return Problem(kind=GEOM_LATLON, n_x=n_lon, n_y=n_lat, n_z=n_z, z_iface=r,
                    beta_iface=exp_profile(r, beta_scale, origin=1.0), lambda2=float(lambda2),
                    lat0=-lat, lat1=lat, name=name)
+
+
+def panel_problem(n_x, n_y, n_z, *, thickness=0.01, omega2=6.71e-4, lambda2_vertical=3.32e-2,
+                  name="") -> Problem:
+    """The paper's test problem (Section 3, Eq. (ModelEquation); Section 7.2):
+    -omega^2 (Lap_2d + lambda^2 r^-2 d_r(r^2 d_r)) u + u = f on one panel of a
+    gnomonic cubed sphere times r in [1, 1 + H], with the quadratically graded
+    levels r_k = 1 + (k/n_z)^2 H of Section 3.1.  In the library's form this
+    is alpha = omega^2, beta = omega^2 lambda^2 and a zero-order coefficient 1.
+    The paper does not give H; ``thickness`` is that reading."""
+    k = np.arange(n_z + 1, dtype=np.float64)
+    r = 1.0 + (k / n_z) ** 2 * thickness
+    a = np.full((n_y, n_x), omega2)
+    return Problem(kind=GEOM_PANEL, n_x=n_x, n_y=n_y, n_z=n_z, z_iface=r,
+                   beta_iface=np.full(n_z + 1, omega2 * lambda2_vertical), lambda2=1.0,
+                   alpha_e=a, alpha_n=a.copy(), name=name or f"panel{n_x}x{n_y}x{n_z}")
 
 
 # ---------------------------------------------------------------------------
