@@ -468,11 +468,13 @@ def main():
     ms_prec, ms_spmv = solver.pcg_time_sweeps(b, "fp64", passes=20)
     hbm_peak, peak_kind = _peaks()
     sm_mhz = clocks.get("sm_mhz") or 1965.0
-    fp64_peak_ops = FP64_OPS_PER_CLK_SM * 152 * sm_mhz * 1e6
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64_peak_ops = FP64_OPS_PER_CLK_SM * n_sm * sm_mhz * 1e6
     # algorithmic traffic: prec sweep reads r, q, writes r, z; SpMV sweep reads u, p, q, z, writes u, p, q
     bytes_prec, bytes_spmv = 4 * 8 * n, 7 * 8 * n
-    # FP64 operations per unknown as written (flux-form stencil and excess-form Thomas)
-    ops_prec, ops_spmv = 9 * n, 18 * n
+    # FP64 operations per unknown as written: flux-form stencil 14 + updates 4;
+    # Thomas with the stored ratio c = W/D 4 + residual update and norm 2
+    ops_prec, ops_spmv = 6 * n, 18 * n
     dom = "spmv" if ms_spmv >= ms_prec else "prec"
     t_dom = ms_spmv if dom == "spmv" else ms_prec
     by, op_ = (bytes_spmv, ops_spmv) if dom == "spmv" else (bytes_prec, ops_prec)

@@ -173,7 +173,7 @@ int pcg_time_sweeps(pcg_t h, const double* b, int precision, int passes, double*
  * callers.  No handle is needed and nothing is allocated: the operator
  * tables and Thomas factors go into one fixed 4 MiB device array owned by
  * the library (every GPU that loads the library holds it until exit), so
- * the grid must satisfy 3 n_z + n_y + 2 n_x n_y + 2 n_z c <= 524288 with
+ * the grid must satisfy 3 n_z + n_y + 2 n_x n_y + 3 n_z c <= 524288 with
  * c = 1 (box, alpha NULL), n_y (latlon, alpha NULL) or n_x n_y (alpha
  * given); larger grids return PCG_ERR_INVALID_ARG with the sizes in
  * pcg_last_error(NULL).  grid, coeffs: host descriptions as for pcg_create

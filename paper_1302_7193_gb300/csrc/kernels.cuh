@@ -79,6 +79,7 @@ struct OpView {
     int periodic_y;
     const T* fg;                // [nz][ncls] 1 / D_k
     const T* fe;                // [nz][ncls] E_k = D_k - W_k
+    const T* fc;                // [nz][ncls] c_k = W_k / D_k (FP64 sweeps only; may be null in FP32 views)
     int cls_mode;               // 0: one factor set; 1: per row j; 2: per column
     int ncls;
     int area_percol;            // 1: area indexed by column (cubed-sphere panel)
@@ -378,21 +379,41 @@ __global__ __launch_bounds__(NT) void k_precond(OpView<T> op, const T* __restric
     const T* rb = r + base;
     T* zb = z + base;
     const T* fg = op.fg + col.cls;
-    const T* fe = op.fe + col.cls;
     const long long fs = op.ncls;
-    T y = T(0), eprev = T(0);
+    if constexpr (sizeof(T) == 8) {
+        // FP64: c form, as in prec_column
+        const T* fc = op.fc + col.cls;
+        T y = T(0), cprev = T(0);
 #pragma unroll 4
-    for (int k = 0; k < op.nz; ++k) {
-        y = fma(-eprev, y, rb[(long long)k * op.plane + col.c]) + y;
-        zb[(long long)k * op.plane + col.c] = y;
-        eprev = ldro(fe + k * fs) * ldro(fg + k * fs);
-    }
-    T zn = T(0);
+        for (int k = 0; k < op.nz; ++k) {
+            const long long o = (long long)k * op.plane + col.c;
+            y = fma(cprev, y, rb[o]);
+            zb[o] = ldro(fg + k * fs) * y;
+            cprev = ldro(fc + k * fs);
+        }
+        T zn = T(0);
 #pragma unroll 4
-    for (int k = op.nz - 1; k >= 0; --k) {
-        const long long o = (long long)k * op.plane + col.c;
-        zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, zb[o]), zn);
-        zb[o] = zn;
+        for (int k = op.nz - 1; k >= 0; --k) {
+            const long long o = (long long)k * op.plane + col.c;
+            zn = fma(ldro(fc + k * fs), zn, zb[o]);
+            zb[o] = zn;
+        }
+    } else {
+        const T* fe = op.fe + col.cls;
+        T y = T(0), eprev = T(0);
+#pragma unroll 4
+        for (int k = 0; k < op.nz; ++k) {
+            y = fma(-eprev, y, rb[(long long)k * op.plane + col.c]) + y;
+            zb[(long long)k * op.plane + col.c] = y;
+            eprev = ldro(fe + k * fs) * ldro(fg + k * fs);
+        }
+        T zn = T(0);
+#pragma unroll 4
+        for (int k = op.nz - 1; k >= 0; --k) {
+            const long long o = (long long)k * op.plane + col.c;
+            zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, zb[o]), zn);
+            zb[o] = zn;
+        }
     }
 }
 
@@ -408,27 +429,58 @@ __device__ __forceinline__ void prec_column(const OpView<T>& op, const Col<T>& c
                                             const T* __restrict__ qb, T* __restrict__ zb, T alpha, Acc<T>& rr,
                                             Acc<T>& kap) {
     const T* fg = op.fg + col.cls;
-    const T* fe = op.fe + col.cls;
     const long long fs = op.ncls;
-    T y = T(0), eprev = T(0);
+    if constexpr (sizeof(T) == 8) {
+        // FP64: the Thomas recurrences with the stored ratio c_k = W_k / D_k,
+        //   y_k = r_k + c_{k-1} y_{k-1},  t_k = y_k / D_k,  kappa += t_k y_k,
+        //   z_k = t_k + c_k z_{k+1},
+        // six FP64 operations per unknown with the residual update and norm.
+        // c_k is one rounding of the exact ratio, so the excess 1 - c_k keeps a
+        // relative accuracy of 2^-53 / (1 - c_k), ample in FP64 (the FP32
+        // sweeps below cannot afford it and carry E_k instead).
+        const T* fc = op.fc + col.cls;
+        T y = T(0), cprev = T(0);
 #pragma unroll 4
-    for (int k = 0; k < op.nz; ++k) {
-        const long long o = (long long)k * op.plane;
-        const T rn = fma(-alpha, qb[o], rb[o]);
-        rb[o] = rn;
-        rr.add_prod(rn, rn);
-        y = fma(-eprev, y, rn) + y;
-        zb[o] = y;
-        const T g = ldro(fg + k * fs);
-        kap.add_prod(g * y, y);
-        eprev = ldro(fe + k * fs) * g;
-    }
-    T zn = T(0);
+        for (int k = 0; k < op.nz; ++k) {
+            const long long o = (long long)k * op.plane;
+            const T rn = fma(-alpha, qb[o], rb[o]);
+            rb[o] = rn;
+            rr.add_prod(rn, rn);
+            y = fma(cprev, y, rn);
+            const T t = ldro(fg + k * fs) * y;
+            kap.add_prod(t, y);
+            zb[o] = t;
+            cprev = ldro(fc + k * fs);
+        }
+        T zn = T(0);
 #pragma unroll 4
-    for (int k = op.nz - 1; k >= 0; --k) {
-        const long long o = (long long)k * op.plane;
-        zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, zb[o]), zn);
-        zb[o] = zn;
+        for (int k = op.nz - 1; k >= 0; --k) {
+            const long long o = (long long)k * op.plane;
+            zn = fma(ldro(fc + k * fs), zn, zb[o]);
+            zb[o] = zn;
+        }
+    } else {
+        const T* fe = op.fe + col.cls;
+        T y = T(0), eprev = T(0);
+#pragma unroll 4
+        for (int k = 0; k < op.nz; ++k) {
+            const long long o = (long long)k * op.plane;
+            const T rn = fma(-alpha, qb[o], rb[o]);
+            rb[o] = rn;
+            rr.add_prod(rn, rn);
+            y = fma(-eprev, y, rn) + y;
+            zb[o] = y;
+            const T g = ldro(fg + k * fs);
+            kap.add_prod(g * y, y);
+            eprev = ldro(fe + k * fs) * g;
+        }
+        T zn = T(0);
+#pragma unroll 4
+        for (int k = op.nz - 1; k >= 0; --k) {
+            const long long o = (long long)k * op.plane;
+            zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, zb[o]), zn);
+            zb[o] = zn;
+        }
     }
 }
 
@@ -441,7 +493,7 @@ __global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__
     SolveState* st = states + rhs;
     if (st->done) return;
     const T alpha = (T)st->alpha;
-    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
     Acc<T> acc[2];
     if (col.valid) {
         const long long base = (long long)rhs * op.vol + col.c;
@@ -496,7 +548,7 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
     if (st->done) return;
     const T alpha = (T)st->alpha;
     const T beta = (T)st->beta;
-    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
     Acc<T> sig[1];
     if (col.valid) {
         const long long base = (long long)rhs * op.vol;
@@ -1003,8 +1055,10 @@ __global__ __launch_bounds__(NT) void k_refine_update(int nx, int ny, int nz, lo
 // W_k + E_k with the excess E_k = s_k + W_{k-1} E_{k-1} / D_{k-1} >= 0
 // (s_k: zero-order plus horizontal-diagonal part of row k).  No term is
 // subtracted, so the pivots keep full relative accuracy however small s_k is
-// next to the vertical couplings.
-__global__ void k_factors(OpView<double> op, double* __restrict__ fg, double* __restrict__ fe) {
+// next to the vertical couplings.  Stored per level and class: 1/D_k, E_k
+// and, when fc is given, c_k = W_k / D_k for the FP64 sweeps.
+__global__ void k_factors(OpView<double> op, double* __restrict__ fg, double* __restrict__ fe,
+                          double* __restrict__ fc) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= op.ncls) return;
     int i = 0, j = 0;
@@ -1023,6 +1077,7 @@ __global__ void k_factors(OpView<double> op, double* __restrict__ fg, double* __
         const double d = w + e;
         fg[(long long)k * op.ncls + c] = 1.0 / d;
         fe[(long long)k * op.ncls + c] = e;
+        if (fc) fc[(long long)k * op.ncls + c] = w / d;
         wprev = w;
         dprev = d;
     }

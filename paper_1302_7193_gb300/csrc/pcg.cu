@@ -40,6 +40,7 @@ struct DevTables {
     void* mun = nullptr;
     void* fg = nullptr;
     void* fe = nullptr;
+    void* fc = nullptr;
 };
 
 }  // namespace
@@ -80,6 +81,8 @@ struct pcg_ctx {
     int prec_minb = 3, spmv_minb = 1;
     dim3 grid_a, block_a, grid_b, block_b;
     int nblk_a = 0, nblk_b = 0;
+    dim3 grid_c, block_c;                 // one-thread-per-column sweeps: 32 x by column tiles
+    int nblk_c = 0;
 
     cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -109,6 +112,7 @@ struct pcg_ctx {
         v.periodic_y = periodic_y;
         v.fg = (const T*)t.fg;
         v.fe = (const T*)t.fe;
+        v.fc = (const T*)t.fc;
         v.cls_mode = cls_mode;
         v.ncls = ncls;
         v.area_percol = geometry == PCG_GEOM_CUBED_PANEL ? 1 : 0;
@@ -268,7 +272,7 @@ int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables
 
 int upload_tables(pcg_t h, const HostTables& t) {
     const size_t nz = h->nz, ny = t.area.size(), nxy = (size_t)h->nx * h->ny, nf = (size_t)nz * h->ncls;
-    const size_t n64 = 3 * nz + ny + 2 * nxy + 2 * nf;
+    const size_t n64 = 3 * nz + ny + 2 * nxy + 3 * nf;
     double* b64 = nullptr;
     float* b32 = nullptr;
     int rc = dmalloc(h, &b64, n64);
@@ -291,6 +295,7 @@ int upload_tables(pcg_t h, const HostTables& t) {
     carve(nxy, h->t64.mun, h->t32.mun);
     carve(nf, h->t64.fg, h->t32.fg);
     carve(nf, h->t64.fe, h->t32.fe);
+    carve(nf, h->t64.fc, h->t32.fc);
     cudaStream_t s = h->stream;
     PCG_CK(h, cudaMemcpyAsync(h->t64.mass, t.mass.data(), nz * 8, cudaMemcpyHostToDevice, s));
     PCG_CK(h, cudaMemcpyAsync(h->t64.wv, t.wv.data(), nz * 8, cudaMemcpyHostToDevice, s));
@@ -300,7 +305,8 @@ int upload_tables(pcg_t h, const HostTables& t) {
     PCG_CK(h, cudaMemcpyAsync(h->t64.mun, t.mun.data(), nxy * 8, cudaMemcpyHostToDevice, s));
     // Thomas factors of every class, in FP64 on the device
     const OpView<double> v = h->view64();
-    pcg::k_factors<<<(h->ncls + 127) / 128, 128, 0, s>>>(v, (double*)h->t64.fg, (double*)h->t64.fe);
+    pcg::k_factors<<<(h->ncls + 127) / 128, 128, 0, s>>>(v, (double*)h->t64.fg, (double*)h->t64.fe,
+                                                         (double*)h->t64.fc);
     PCG_CK(h, cudaGetLastError());
     const long long nconv = (long long)n64;
     pcg::k_to_float<<<1024, 256, 0, s>>>(b64, b32, nconv);
@@ -342,7 +348,7 @@ void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, 
     } else if (chunked) {
         PCG_PREC_CH(32, 1);
     } else {
-        pcg::k_sweep_prec<T><<<h->grid, h->block, 0, s>>>(v, r, q, z, st, h->partials, h->counters, h->nblocks);
+        pcg::k_sweep_prec<T><<<h->grid_c, h->block_c, 0, s>>>(v, r, q, z, st, h->partials, h->counters, h->nblk_c);
     }
 #undef PCG_PREC_CH
 }
@@ -362,7 +368,7 @@ void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, 
         if (h->spmv_minb == 6) PCG_SPMV_CH(16, false, 6);
         else PCG_SPMV_CH(16, false, 1);
     } else {
-        pcg::k_sweep_spmv<T><<<h->grid, h->block, 0, s>>>(v, u, p, q, z, st, h->partials, h->counters, h->nblocks);
+        pcg::k_sweep_spmv<T><<<h->grid_c, h->block_c, 0, s>>>(v, u, p, q, z, st, h->partials, h->counters, h->nblk_c);
     }
 #undef PCG_SPMV_CH
 }
@@ -633,6 +639,33 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->block = dim3(BX, BY, 1);
     h->grid = dim3((h->nx + BX - 1) / BX, (h->ny + BY - 1) / BY, h->nrhs);
     h->nblocks = (int)(h->grid.x * h->grid.y);
+    {
+        // The one-thread-per-column sweeps keep every tile resident at once, so
+        // the SM with the most tiles sets their duration: take the tile height
+        // (4, 2 or 1 rows of 32 columns) that spreads the tiles most evenly
+        // over the SMs (65 536 columns: 512 tiles of 4 rows put 4 on some SMs
+        // and 3.37 on average; 1024 tiles of 2 rows, 7 against 6.74).
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+        int by = BY;
+        double best = -1.0;
+        for (int cand : {4, 2, 1}) {
+            if ((h->ny + cand - 1) / cand > 65535) continue;   // grid y limit
+            const long long tiles = (long long)((h->nx + BX - 1) / BX) * ((h->ny + cand - 1) / cand) * h->nrhs;
+            const long long per_sm = (tiles + sms - 1) / sms;
+            const double bal = (double)tiles / (double)(per_sm * sms);
+            if (bal > best + 0.01) { best = bal; by = cand; }
+        }
+        if (const char* e = std::getenv("PCG_COL_BY")) {       // experiments: fixed tile height
+            const int v = std::atoi(e);
+            if (v == 1 || v == 2 || v == 4) by = v;
+        }
+        h->block_c = dim3(BX, by, 1);
+        h->grid_c = dim3((h->nx + BX - 1) / BX, (h->ny + by - 1) / by, h->nrhs);
+        h->nblk_c = (int)(h->grid_c.x * h->grid_c.y);
+    }
     // Sweep variants: the FP32 sweeps split every column into chunks of 16 or 32
     // levels (up to 8 chunks; HBM latency needs the extra parallelism), the FP64
     // sweeps keep one thread per column (they are bound by the FP64 pipe, which
@@ -687,7 +720,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if ((rc = dmalloc(h, &h->st, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->st_in, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->d_active, h->nrhs))) return bail(rc);
-    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(h->nblocks, std::max(h->nblk_a, h->nblk_b)) * 4))) return bail(rc);
+    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(std::max(h->nblocks, h->nblk_c), std::max(h->nblk_a, h->nblk_b)) * 4))) return bail(rc);
     if ((rc = dmalloc(h, &h->counters, h->nrhs))) return bail(rc);
     e = cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * h->nrhs, h->stream);
     if (e != cudaSuccess) { h->err = std::string("cudaMemset: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
@@ -899,7 +932,7 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
     const bool field = coeffs->alpha_e || coeffs->alpha_n;
     const int cls_mode = field ? 2 : (grid->geometry == PCG_GEOM_LATLON ? 1 : 0);
     const size_t ncls = cls_mode == 0 ? 1 : (cls_mode == 1 ? (size_t)ny : nxy);
-    const size_t need = 3 * (size_t)nz + ny + 2 * nxy + 2 * (size_t)nz * ncls;
+    const size_t need = 3 * (size_t)nz + ny + 2 * nxy + 3 * (size_t)nz * ncls;
     if (need > kNoAllocDoubles) {
         static char msg[256];
         std::snprintf(msg, sizeof msg,
@@ -986,14 +1019,16 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
     v.periodic_y = grid->geometry == PCG_GEOM_BOX ? 1 : 0;
     double* fg = d + ntab;
     double* fe = fg + (size_t)nz * ncls;
+    double* fc = fe + (size_t)nz * ncls;
     v.fg = fg;
     v.fe = fe;
+    v.fc = fc;
     v.cls_mode = cls_mode;
     v.ncls = (int)ncls;
     v.area_percol = 0;
     // the factors are rewritten in full by every call, so nothing left by an
     // earlier call is read
-    pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, s>>>(v, fg, fe);
+    pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, s>>>(v, fg, fe, fc);
     const dim3 block(BX, BY, 1), gridd((nx + BX - 1) / BX, (ny + BY - 1) / BY, grid->nrhs);
     pcg::k_precond<double><<<gridd, block, 0, s>>>(v, r, z);
     e = cudaGetLastError();

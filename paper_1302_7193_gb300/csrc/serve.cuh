@@ -164,7 +164,7 @@ int admit(pcg_server_t s, ServeReq* q) {
         op.plane = (long long)nxy; op.vol = (long long)vol;
         op.mass = nxt(nz); op.wv = nxt(nz); op.dk = nxt(nz); op.area = nxt(na);
         op.mue = nxt(nxy); op.mun = nxt(nxy);
-        op.fg = nxt(nz * ncls); op.fe = nxt(nz * ncls);
+        op.fg = nxt(nz * ncls); op.fe = nxt(nz * ncls); op.fc = nullptr;   // served sweeps are FP32
         op.periodic_y = g.geometry == PCG_GEOM_LATLON ? 0 : 1;
         op.cls_mode = cls_mode; op.ncls = (int)ncls;
         op.area_percol = g.geometry == PCG_GEOM_CUBED_PANEL ? 1 : 0;
@@ -178,7 +178,8 @@ int admit(pcg_server_t s, ServeReq* q) {
     SRV_CK(s, cudaMemcpyAsync((void*)q->op64.area, t.area.data(), na * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemcpyAsync((void*)q->op64.mue, t.mue.data(), nxy * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemcpyAsync((void*)q->op64.mun, t.mun.data(), nxy * 8, cudaMemcpyHostToDevice, st));
-    pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, st>>>(q->op64, (double*)q->op64.fg, (double*)q->op64.fe);
+    pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, st>>>(q->op64, (double*)q->op64.fg, (double*)q->op64.fe,
+                                                                    nullptr);
     pcg::k_to_float<<<256, 256, 0, st>>>(t64, t32, (long long)ntab);
     SRV_CK(s, cudaMemcpyAsync(q->bd, q->b.data(), vol * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemsetAsync(q->xd, 0, vol * 8, st));
