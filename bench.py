@@ -472,9 +472,10 @@ def main():
     fp64_peak_ops = FP64_OPS_PER_CLK_SM * n_sm * sm_mhz * 1e6
     # algorithmic traffic: prec sweep reads r, q, writes r, z; SpMV sweep reads u, p, q, z, writes u, p, q
     bytes_prec, bytes_spmv = 4 * 8 * n, 7 * 8 * n
-    # FP64 operations per unknown as written: flux-form stencil 14 + updates 4;
-    # Thomas with the stored ratio c = W/D 4 + residual update and norm 2
-    ops_prec, ops_spmv = 6 * n, 18 * n
+    # FP64 operations per unknown as written: flux-form stencil 13 (the box's
+    # uniform area folded into the level tables) + updates 4; Thomas with the
+    # stored ratio c = W/D 4 + residual update and norm 2
+    ops_prec, ops_spmv = 6 * n, 17 * n
     dom = "spmv" if ms_spmv >= ms_prec else "prec"
     t_dom = ms_spmv if dom == "spmv" else ms_prec
     by, op_ = (bytes_spmv, ops_spmv) if dom == "spmv" else (bytes_prec, ops_prec)

@@ -52,7 +52,7 @@ enum pcg_status {
     PCG_ERR_CUDA = 3,          /* a CUDA runtime call failed (text in last_error) */
     PCG_NOT_CONVERGED = 4,     /* maxit reached before the stopping test passed  */
     PCG_BREAKDOWN = 5,         /* <p,Ap> <= 0, <r,z> < 0 or a non-finite scalar    */
-    PCG_TIMEOUT = 6,           /* reserved: no entry point waits on the device without a bound */
+    PCG_TIMEOUT = 6,           /* a bounded device-side wait (staged copies of a sweep) gave up; the solve stopped */
     PCG_PENDING = 7            /* pcg_serve_poll: the request has not finished yet */
 };
 

@@ -31,6 +31,7 @@
 // rounds to 1 in FP32 and the column's near-constant mode would be lost.
 // <r, M^{-1} r> = sum_k g_k y_k^2 is accumulated in the forward sweep.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,6 +84,9 @@ struct OpView {
     int cls_mode;               // 0: one factor set; 1: per row j; 2: per column
     int ncls;
     int area_percol;            // 1: area indexed by column (cubed-sphere panel)
+    const T* amass;             // [rows][nz] |T| a_k with the area folded in, or null (area per column)
+    const T* awv;               // [rows][nz] |T| w_k
+    int arow_step;              // 0: one folded row (uniform area); 1: one per grid row j
 };
 
 // Per-thread accumulators: plain FP64, or compensated FP32 (exact product
@@ -115,6 +119,7 @@ template <typename T>
 struct Col {
     long long c, ce, cw, cn, cs;
     T area, me, mw, mn, ms;
+    int j;                      // grid row
     int cls;
     bool valid;
 };
@@ -147,6 +152,7 @@ __device__ __forceinline__ Col<T> make_col(const OpView<T>& op, int i, int j) {
     col.mn = ldro(op.mun + col.c);
     col.ms = (op.periodic_y || jj > 0) ? ldro(op.mun + col.cs) : T(0);
     col.cls = op.cls_mode == 0 ? 0 : (op.cls_mode == 1 ? jj : (int)col.c);
+    col.j = jj;
     return col;
 }
 
@@ -334,6 +340,11 @@ __device__ __forceinline__ void prec_epilogue(SolveState* st, double rrv, double
 // Scalar step after the SpMV sweep (line 6): alpha = kappa_old / sigma.
 __device__ __forceinline__ void spmv_epilogue(SolveState* st, double s) {
     st->sigma = s;
+    if (*(volatile int*)&st->status == 6) {   // a block's staged copies timed out (PCG_TIMEOUT)
+        st->done = 1;
+        st->alpha = 0.0;
+        return;
+    }
     if (!(s > 0.0) || !isfinite(s)) {
         st->done = 1;
         st->status = 5;   // PCG_BREAKDOWN
@@ -511,10 +522,14 @@ __global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__
 // One column of the SpMV sweep; u, p, q point at the column's level-0
 // entry, zb at level 0 of the right-hand side's z (the stencil reads
 // neighbouring columns).
-template <typename T>
+template <typename T, bool FOLD = false>
 __device__ __forceinline__ void spmv_column(const OpView<T>& op, const Col<T>& col, T* __restrict__ ub,
                                             T* __restrict__ pb, T* __restrict__ qb, const T* __restrict__ zb,
                                             T alpha, T beta, Acc<T>& sig) {
+    // FOLD: the area is folded into the level tables (|T| a_k, |T| w_k per
+    // row), one multiplication fewer per unknown for uniform or per-row areas
+    const T* am = FOLD ? op.amass + (op.arow_step ? (long long)col.j * op.nz : 0LL) : op.mass;
+    const T* aw = FOLD ? op.awv + (op.arow_step ? (long long)col.j * op.nz : 0LL) : op.wv;
     T zc = zb[col.c];
     T fprev = T(0);
 #pragma unroll 4
@@ -527,9 +542,10 @@ __device__ __forceinline__ void spmv_column(const OpView<T>& op, const Col<T>& c
         ub[o] = fma(alpha, pk, ub[o]);
         const T pn = fma(beta, pk, zc);
         pb[o] = pn;
-        const T f = ldro(op.wv + k) * (zc - zu);
+        const T f = ldro(aw + k) * (zc - zu);
         const T hz = horiz(col, zl, zc);
-        const T az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+        const T vz = fma(ldro(am + k), zc, f - fprev);
+        const T az = fma(ldro(op.dk + k), hz, FOLD ? vz : col.area * vz);
         const T qn = fma(beta, qk, az);
         qb[o] = qn;
         sig.add_prod(pn, qn);
@@ -552,7 +568,12 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
     Acc<T> sig[1];
     if (col.valid) {
         const long long base = (long long)rhs * op.vol;
-        spmv_column<T>(op, col, u + base + col.c, p + base + col.c, q + base + col.c, z + base, alpha, beta, sig[0]);
+        if (sizeof(T) == 8 && op.amass)
+            spmv_column<T, true>(op, col, u + base + col.c, p + base + col.c, q + base + col.c, z + base, alpha, beta,
+                                 sig[0]);
+        else
+            spmv_column<T, false>(op, col, u + base + col.c, p + base + col.c, q + base + col.c, z + base, alpha, beta,
+                                  sig[0]);
     }
     double v[1];
     if (grid_sum_acc<1>(sig, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
@@ -577,23 +598,25 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
 // excess form of the sweeps above, reassociated.
 // Preconditioner sweep: block = 32 columns of one row x (n_z/LZ) chunks.
 // ---------------------------------------------------------------------------
-template <typename T, int LZ, int MINB = 1>
-__global__ __launch_bounds__(256, MINB) void k_sweep_prec_chunked(OpView<T> op, T* __restrict__ r, const T* __restrict__ q,
-                                                            T* __restrict__ z, SolveState* __restrict__ states,
-                                                            double* __restrict__ partials,
-                                                            unsigned* __restrict__ counters, int nblocks) {
-    __shared__ T sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
-    const int rhs = blockIdx.z;
-    SolveState* st = states + rhs;
-    if (st->done) return;
-    const T alpha = (T)st->alpha;
-    const int lane = threadIdx.x, ch = threadIdx.y, nch = blockDim.y;
-    const Col<T> col = make_col(op, blockIdx.x * 32 + lane, blockIdx.y);
+// One (column, chunk) of the chunked preconditioner sweep.  The chunks of a
+// column are the warps w0 .. w0 + nch - 1 of the block (lane = column);
+// r, q, z point at level 0 of the right-hand side.  The chunk's r and q are
+// read from rsrc / qsrc (level t of the chunk at t * sstride; null: from r
+// and q themselves).  Every thread of the block must call this (it holds two
+// block barriers); threads with col.valid false take part in the barriers
+// only.
+template <typename T, int LZ>
+__device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col<T>& col, int lane, int ch, int nch,
+                                                  int w0, T* __restrict__ r, const T* __restrict__ q,
+                                                  T* __restrict__ z, T alpha, Acc<T> (&acc)[2], T (*sh_y)[32],
+                                                  T (*sh_c)[32], T (*sh_z)[32], T (*sh_d)[32],
+                                                  const T* rsrc = nullptr, const T* qsrc = nullptr,
+                                                  int sstride = 0) {
     const int k0 = ch * LZ;
     const int kn = min(LZ, op.nz - k0);          // levels in this chunk (<= 0: none)
     const bool act = col.valid && kn > 0;
     const bool full = act && kn == LZ;
-    const long long base = (long long)rhs * op.vol + col.c;
+    const long long base = col.c;
     T* rb = r + base + (long long)k0 * op.plane;
     const T* qb = q + base + (long long)k0 * op.plane;
     T* zb = z + base + (long long)k0 * op.plane;
@@ -601,10 +624,20 @@ __global__ __launch_bounds__(256, MINB) void k_sweep_prec_chunked(OpView<T> op, 
     const T* fg = op.fg + col.cls + (long long)k0 * fs;
     const T* fe = op.fe + col.cls + (long long)k0 * fs;
     const long long pl = op.plane;
-    Acc<T> acc[2];
     T yv[LZ], gv[LZ], ev[LZ];
     // all loads of the chunk first
-    if (full) {
+    if (rsrc) {
+        if (act) {
+#pragma unroll
+            for (int t = 0; t < LZ; ++t) {
+                if (t < kn) {
+                    yv[t] = fma(-alpha, qsrc[t * sstride], rsrc[t * sstride]);
+                    gv[t] = ldro(fg + t * fs);
+                    ev[t] = ldro(fe + t * fs);
+                }
+            }
+        }
+    } else if (full) {
 #pragma unroll
         for (int t = 0; t < LZ; ++t) {
             yv[t] = fma(-alpha, qb[t * pl], rb[t * pl]);
@@ -639,11 +672,11 @@ __global__ __launch_bounds__(256, MINB) void k_sweep_prec_chunked(OpView<T> op, 
             }
         }
     }
-    sh_y[ch][lane] = yl;
-    sh_c[ch][lane] = cp;
+    sh_y[w0 + ch][lane] = yl;
+    sh_c[w0 + ch][lane] = cp;
     __syncthreads();
     T Y = T(0);
-    for (int cc = 0; cc < ch; ++cc) Y = fma(-sh_c[cc][lane], Y, sh_y[cc][lane]) + Y;
+    for (int cc = 0; cc < ch; ++cc) Y = fma(-sh_c[w0 + cc][lane], Y, sh_y[w0 + cc][lane]) + Y;
     // corrected y, kappa, then the local backward sweep with zero carry-in
     T zl = T(0), dp = T(0);
     if (act) {
@@ -671,11 +704,11 @@ __global__ __launch_bounds__(256, MINB) void k_sweep_prec_chunked(OpView<T> op, 
             }
         }
     }
-    sh_z[ch][lane] = zl;
-    sh_d[ch][lane] = dp;
+    sh_z[w0 + ch][lane] = zl;
+    sh_d[w0 + ch][lane] = dp;
     __syncthreads();
     T Z = T(0);
-    for (int cc = nch - 1; cc > ch; --cc) Z = fma(-sh_d[cc][lane], Z, sh_z[cc][lane]) + Z;
+    for (int cc = nch - 1; cc > ch; --cc) Z = fma(-sh_d[w0 + cc][lane], Z, sh_z[w0 + cc][lane]) + Z;
     if (act) {
         dp = T(0);
         bool first = true;
@@ -689,6 +722,23 @@ __global__ __launch_bounds__(256, MINB) void k_sweep_prec_chunked(OpView<T> op, 
             }
         }
     }
+}
+
+template <typename T, int LZ, int MINB = 1>
+__global__ __launch_bounds__(256, MINB) void k_sweep_prec_chunked(OpView<T> op, T* __restrict__ r, const T* __restrict__ q,
+                                                            T* __restrict__ z, SolveState* __restrict__ states,
+                                                            double* __restrict__ partials,
+                                                            unsigned* __restrict__ counters, int nblocks) {
+    __shared__ T sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
+    const int rhs = blockIdx.z;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const T alpha = (T)st->alpha;
+    const int lane = threadIdx.x, ch = threadIdx.y, nch = blockDim.y;
+    const Col<T> col = make_col(op, blockIdx.x * 32 + lane, blockIdx.y);
+    const long long rb = (long long)rhs * op.vol;
+    Acc<T> acc[2];
+    prec_chunked_body<T, LZ>(op, col, lane, ch, nch, 0, r + rb, q + rb, z + rb, alpha, acc, sh_y, sh_c, sh_z, sh_d);
     double v[2];
     if (grid_sum_acc<2>(acc, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
         prec_epilogue(st, v[0], v[1]);
@@ -821,63 +871,422 @@ __global__ __launch_bounds__(NT, MINB) void k_sweep_spmv_chunked(OpView<T> op, T
 
 
 // ---------------------------------------------------------------------------
-// Served batch: persistent sweeps over a work list of (request slot, tile).
+// FP32 SpMV sweep with TMA-staged tiles.
+//
+// Block = 32 x BYT columns, one chunk of LZ levels (blockIdx.z = rhs *
+// nchunks + chunk).  One thread issues four bulk tensor copies into shared
+// memory, all completing on one mbarrier:
+//   z: levels k0-1 .. k0+LZ, columns i0-4 .. i0+35, rows j0-1 .. j0+BYT
+//      (the stencil's one-cell halo; x starts 4 columns early so that the
+//      copy starts on a 16-byte boundary),
+//   u, p, q: levels k0 .. k0+LZ-1 of the block's own columns.
+// Cells outside the grid arrive as zeros; a neighbour that wraps around a
+// periodic edge (or is clamped at a Neumann edge) is read from global memory
+// instead.  The right-hand side index is folded into the level coordinate,
+// so the tensor maps describe [nrhs * n_z][n_y][n_x] arrays.  Arithmetic as
+// in spmv_column<float>.
+// ---------------------------------------------------------------------------
+constexpr int TMA_HALO_X = 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int c0, int c1, int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(bar) : "memory");
+}
+
+// Wait for the phase with parity `parity` of the mbarrier at `bar`, giving up
+// after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ bool mbar_wait0(uint32_t bar, int limit) { return mbar_wait(bar, 0u, limit); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+
+template <int LZ, int BYT>
+struct SpmvTmaTile {
+    static constexpr int ZX = BX + 2 * TMA_HALO_X, ZY = BYT + 2, ZZ = LZ + 2;
+    static constexpr int ZN = ZX * ZY * ZZ, VN = BX * BYT * LZ;
+    static constexpr uint32_t BYTES = (uint32_t)(ZN + 3 * VN) * 4u;
+    static constexpr size_t SMEM = (size_t)BYTES + 16 + 128;   // + the mbarrier, + alignment slack
+};
+
+// The SpMV arithmetic of one thread on a staged tile (spmv_column<float>'s
+// order of operations): zs holds levels k0-1 .. k0+LZ of the tile with halo,
+// us/ps/qs levels k0 .. k0+LZ-1 of the block's own columns; z, u, p, q point
+// at level 0 of the right-hand side.
+template <int LZ, int BYT>
+__device__ __forceinline__ void spmv_tile_compute(const OpView<float>& op, const Col<float>& col, int tx, int ty,
+                                                  int k0, int kn, const float* zs, const float* us, const float* ps,
+                                                  const float* qs, const float* __restrict__ z, float* __restrict__ u,
+                                                  float* __restrict__ p, float* __restrict__ q, float alpha,
+                                                  float beta, bool in_e, bool in_w, bool in_n, bool in_s,
+                                                  Acc<float>& sig) {
+    using TT = SpmvTmaTile<LZ, BYT>;
+    const long long pl = op.plane;
+    float* ub = u + col.c + (long long)k0 * pl;
+    float* pb = p + col.c + (long long)k0 * pl;
+    float* qb = q + col.c + (long long)k0 * pl;
+    constexpr int ZX = TT::ZX, ZP = TT::ZX * TT::ZY;
+    const int c0 = (ty + 1) * ZX + (tx + TMA_HALO_X);
+    const int v0 = ty * BX + tx;
+    float zc = zs[ZP + c0];
+    float fprev = (k0 > 0) ? ldro(op.wv + k0 - 1) * (zs[c0] - zc) : 0.f;
+#pragma unroll 4
+    for (int t = 0; t < LZ; ++t) {
+        if (t < kn) {
+            const int k = k0 + t;
+            const float* zl = zs + (t + 1) * ZP;
+            const float zu = (k + 1 < op.nz) ? zl[ZP + c0] : zc;
+            const float pk = ps[t * BX * BYT + v0];
+            ub[t * pl] = fmaf(alpha, pk, us[t * BX * BYT + v0]);
+            const float pn = fmaf(beta, pk, zc);
+            pb[t * pl] = pn;
+            const float f = ldro(op.wv + k) * (zc - zu);
+            const float* zk = z + (long long)k * pl;
+            const float ze = in_e ? zl[c0 + 1] : ldro(zk + col.ce);
+            const float zw = in_w ? zl[c0 - 1] : ldro(zk + col.cw);
+            const float zn = in_n ? zl[c0 + ZX] : ldro(zk + col.cn);
+            const float zs_ = in_s ? zl[c0 - ZX] : ldro(zk + col.cs);
+            float hz = col.me * (zc - ze);
+            hz = fmaf(col.mw, zc - zw, hz);
+            hz = fmaf(col.mn, zc - zn, hz);
+            hz = fmaf(col.ms, zc - zs_, hz);
+            const float az = fmaf(ldro(op.dk + k), hz, col.area * fmaf(ldro(op.mass + k), zc, f - fprev));
+            const float qn = fmaf(beta, qs[t * BX * BYT + v0], az);
+            qb[t * pl] = qn;
+            sig.add_prod(pn, qn);
+            fprev = f;
+            zc = zu;
+        }
+    }
+}
+
+template <int LZ, int BYT>
+__global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma(
+    OpView<float> op, const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
+    const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_z, float* __restrict__ u,
+    float* __restrict__ p, float* __restrict__ q, const float* __restrict__ z, SolveState* __restrict__ states,
+    double* __restrict__ partials, unsigned* __restrict__ counters, int nblocks, int nchunks) {
+    using TT = SpmvTmaTile<LZ, BYT>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // bulk tensor copies land on 128-byte aligned addresses
+    float* zs = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));   // [ZZ][ZY][ZX]
+    float* us = zs + TT::ZN;                // [LZ][BYT][32]
+    float* ps = us + TT::VN;
+    float* qs = ps + TT::VN;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(qs + TT::VN);
+    const int rhs = blockIdx.z / nchunks;
+    const int ch = blockIdx.z - rhs * nchunks;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BYT;
+    const int k0 = ch * LZ;
+    const int kn = min(LZ, op.nz - k0);
+    const int lev0 = rhs * op.nz + k0;      // level coordinate of the chunk in the folded arrays
+    const uint32_t b = smem_u32(bar);
+    if (tx == 0 && ty == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tx == 0 && ty == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(TT::BYTES) : "memory");
+        tma_load_3d(smem_u32(zs), &tm_z, i0 - TMA_HALO_X, j0 - 1, lev0 - 1, b);
+        tma_load_3d(smem_u32(us), &tm_u, i0, j0, lev0, b);
+        tma_load_3d(smem_u32(ps), &tm_p, i0, j0, lev0, b);
+        tma_load_3d(smem_u32(qs), &tm_q, i0, j0, lev0, b);
+    }
+    const float alpha = (float)st->alpha;
+    const float beta = (float)st->beta;
+    const Col<float> col = make_col(op, i0 + tx, j0 + ty);
+    const bool act = col.valid && kn > 0;
+    // neighbours inside the staged tile (not wrapped, not clamped)
+    const bool in_e = col.ce == col.c + 1, in_w = col.cw == col.c - 1;
+    const bool in_n = col.cn == col.c + op.nx, in_s = col.cs == col.c - op.nx;
+    const bool landed = mbar_wait0(b, 1 << 22);
+    Acc<float> sig[1];
+    if (!landed) {
+        // the copies did not complete in time: record it (the last block ends
+        // the solve), wait (bounded) for them to land before the block's
+        // shared memory is released, and add nothing to sigma
+        if (tx == 0 && ty == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT
+        mbar_wait0(b, 1 << 22);
+    } else if (act) {
+        const long long base = (long long)rhs * op.vol;
+        spmv_tile_compute<LZ, BYT>(op, col, tx, ty, k0, kn, zs, us, ps, qs, z + base, u + base, p + base, q + base,
+                                   alpha, beta, in_e, in_w, in_n, in_s, sig[0]);
+    }
+    double v[1];
+    const int bid = (ch * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (grid_sum_acc<1>(sig, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid, v))
+        spmv_epilogue(st, v[0]);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 preconditioner sweep on a TMA pipeline: the chunked solve of
+// prec_chunked_body on tiles staged in shared memory.
+//
+// Persistent blocks of 256 threads, blockIdx.y = right-hand side.  An item
+// is R rows of 32 columns over all levels (R * nch <= 8: warp w takes row
+// w / nch, chunk w % nch).  One thread streams the items' r and q tiles
+// ([LEV][R][32], LEV = nch * LZ) into two shared-memory stages by bulk
+// tensor copies, each stage on its own mbarrier, so the copies of the next
+// item are in flight while an item is solved.  The threads write r and z.
+// ---------------------------------------------------------------------------
+template <int LZ>
+struct PrecTmaTile {
+    static constexpr int VN = 8 * LZ * 32;                 // floats of one vector in one stage (R * LEV <= 8 LZ)
+    static constexpr size_t SMEM = 4 * (size_t)VN * 4 + 16 + 128;   // 2 stages x (r, q), 2 mbarriers, alignment
+};
+
+template <int LZ>
+__global__ __launch_bounds__(256, 2) void k_sweep_prec_tma(
+    OpView<float> op, const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_q,
+    float* __restrict__ r, const float* __restrict__ q, float* __restrict__ z, SolveState* __restrict__ states,
+    double* __restrict__ partials, unsigned* __restrict__ counters, int R, int nch, int gx, int nitems) {
+    using TT = PrecTmaTile<LZ>;
+    __shared__ float sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* sbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 4 * TT::VN);
+    const int rhs = blockIdx.y;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const float alpha = (float)st->alpha;
+    const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
+    const int row = w / nch, ch = w - row * nch;
+    const uint32_t bytes = 2u * 32u * (uint32_t)R * (uint32_t)(nch * LZ) * 4u;
+    const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
+    if (tid == 0) {
+        mbar_init(bar0);
+        mbar_init(bar1);
+    }
+    __syncthreads();
+    const int lev0 = rhs * op.nz;
+    auto issue = [&](int item, int stage) {
+        const uint32_t bar = stage ? bar1 : bar0;
+        float* rs = sbase + stage * 2 * TT::VN;
+        mbar_expect(bar, bytes);
+        tma_load_3d(smem_u32(rs), &tm_r, (item % gx) * 32, (item / gx) * R, lev0, bar);
+        tma_load_3d(smem_u32(rs + TT::VN), &tm_q, (item % gx) * 32, (item / gx) * R, lev0, bar);
+    };
+    if (tid == 0) {
+        if ((int)blockIdx.x < nitems) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < nitems) issue(blockIdx.x + gridDim.x, 1);
+    }
+    const long long vb = (long long)rhs * op.vol;
+    Acc<float> acc[2];
+    uint32_t par0 = 0, par1 = 0;
+    bool ok = true;                 // false once a stage failed to land in time: nothing more is computed
+    int n = 0;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++n) {
+        const int stage = n & 1;
+        bool landed = false;
+        if (ok) landed = mbar_wait(stage ? bar1 : bar0, stage ? par1 : par0, 1 << 22);
+        landed = __syncthreads_and(landed ? 1 : 0) != 0;
+        if (landed) {
+            if (stage) par1 ^= 1u; else par0 ^= 1u;
+        }
+        if (ok && !landed) {
+            if (tid == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT
+            ok = false;
+        }
+        const int j = (ok && row < R) ? (item / gx) * R + row : op.ny;   // op.ny: no column (barriers only)
+        const Col<float> col = make_col(op, (item % gx) * 32 + lane, j);
+        const float* rs = sbase + stage * 2 * TT::VN + ((ch * LZ) * R + row) * 32 + lane;
+        prec_chunked_body<float, LZ>(op, col, lane, ch, nch, row * nch, r + vb, q + vb, z + vb, alpha, acc, sh_y,
+                                     sh_c, sh_z, sh_d, rs, rs + TT::VN, R * 32);
+        __syncthreads();            // the stage has been read: refill it
+        if (tid == 0 && ok && item + 2 * (int)gridDim.x < nitems) issue(item + 2 * gridDim.x, stage);
+    }
+    if (!ok) {
+        // copies still in flight (the pending phase of each stage) land before
+        // the block's shared memory is released
+        mbar_wait(bar0, par0, 1 << 22);
+        mbar_wait(bar1, par1, 1 << 22);
+    }
+    double v[2];
+    if (grid_sum_acc<2>(acc, partials + (long long)rhs * gridDim.x * 2, counters + rhs, gridDim.x, blockIdx.x, v))
+        prec_epilogue(st, v[0], v[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Served batch: persistent sweeps over work lists of (request slot, item).
 //
 // Every admitted request owns a slot with its own tables, vectors, partials,
 // arrival counter and scalar state.  One launch of each kernel walks all
-// items of all requests (grid-stride, one 32 x 4-column tile per item, the
-// column loop above), so many small solves fill the GPU together; the last
-// tile of a request to finish forms that request's scalars exactly as the
-// per-solve kernels do, so a request's arithmetic does not depend on which
-// other requests share the launch.
+// items of all requests in the inner phase (grid-stride), so many small
+// solves fill the GPU together; the last item of a request to finish forms
+// that request's scalars exactly as the per-solve kernels do, so a request's
+// arithmetic does not depend on which other requests share the launch.
+//   k_serve_prec: 256-thread blocks; an item is `rows` rows of 32 columns,
+//     each column split into nch chunks of 16 levels (one warp per chunk,
+//     prec_chunked_body); columns of more than 128 levels take one thread
+//     per column (8 rows per item, prec_column).
+//   k_serve_spmv: 256-thread blocks; an item is a 32 x 8-column tile of one
+//     16-level chunk, staged in shared memory by bulk tensor copies (tensor
+//     maps of the request in device memory) or, when the request's rows are
+//     not 16-byte multiples, by the threads; then spmv_tile_compute.
 // ---------------------------------------------------------------------------
+constexpr int SERVE_LZ = 16, SERVE_BY = 8;
+
 struct ServeSlot {
     OpView<float> op;           // FP32 tables of the request
     float *u, *r, *z, *p, *q;   // inner FP32 vectors
     SolveState* st;             // inner state
-    double* partials;           // [ntiles][4]
+    double* partials;           // [max(nprec, nspmv)][4]
     unsigned* counter;
-    int gx, ntiles;             // tiles per row (ceil(nx/32)) and in total
+    int gx;                     // tiles of 32 columns per row
+    int nch;                    // chunks of 16 levels per column
+    int rows;                   // preconditioner: rows per item
+    int colmode;                // preconditioner: 1 = one thread per column (n_z > 128)
+    int nprec;                  // preconditioner items
+    int nspmv;                  // SpMV items: gx * ceil(n_y / 8) * nch
+    const CUtensorMap* tmaps;   // [4] u, p, q, z (boxes as k_sweep_spmv_tma), or null
 };
 
-__global__ __launch_bounds__(NT) void k_serve_prec(const ServeSlot* __restrict__ slots, const int2* __restrict__ items,
-                                                   const int* __restrict__ n_items) {
+template <int MINB>
+__global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __restrict__ slots,
+                                                         const int2* __restrict__ items,
+                                                         const int* __restrict__ n_items) {
+    __shared__ float sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
     const int n = *n_items;
+    const int lane = threadIdx.x, w = threadIdx.y;
     for (int it = blockIdx.x; it < n; it += gridDim.x) {
-        const int2 w = items[it];
-        const ServeSlot& s = slots[w.x];
+        const int2 wk = items[it];
+        const ServeSlot& s = slots[wk.x];
         SolveState* st = s.st;
         if (!st->done) {
             const float alpha = (float)st->alpha;
-            const int bx = w.y % s.gx, by = w.y / s.gx;
-            const Col<float> col = make_col(s.op, bx * BX + threadIdx.x, by * BY + threadIdx.y);
+            const int bx = wk.y % s.gx, jb = wk.y / s.gx;
             Acc<float> acc[2];
-            if (col.valid) prec_column<float>(s.op, col, s.r + col.c, s.q + col.c, s.z + col.c, alpha, acc[0], acc[1]);
+            if (s.colmode) {
+                const Col<float> col = make_col(s.op, bx * 32 + lane, jb * 8 + w);
+                if (col.valid) prec_column<float>(s.op, col, s.r + col.c, s.q + col.c, s.z + col.c, alpha, acc[0], acc[1]);
+            } else {
+                // warp w: row w / nch of the item, chunk w % nch; warps past
+                // rows * nch only take part in the barriers
+                const int row = w / s.nch, ch = w - row * s.nch;
+                const int j = row < s.rows ? jb * s.rows + row : s.op.ny;
+                const Col<float> col = make_col(s.op, bx * 32 + lane, j);
+                prec_chunked_body<float, SERVE_LZ>(s.op, col, lane, ch, s.nch, row * s.nch, s.r, s.q, s.z, alpha, acc,
+                                                   sh_y, sh_c, sh_z, sh_d);
+            }
             double v[2];
-            if (grid_sum_acc<2>(acc, s.partials, s.counter, s.ntiles, w.y, v)) prec_epilogue(st, v[0], v[1]);
+            if (grid_sum_acc<2>(acc, s.partials, s.counter, s.nprec, wk.y, v)) prec_epilogue(st, v[0], v[1]);
         }
         __syncthreads();
     }
 }
 
-__global__ __launch_bounds__(NT) void k_serve_spmv(const ServeSlot* __restrict__ slots, const int2* __restrict__ items,
-                                                   const int* __restrict__ n_items) {
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(reinterpret_cast<uint64_t>(m)) : "memory");
+}
+
+__global__ __launch_bounds__(256) void k_serve_spmv(const ServeSlot* __restrict__ slots, const int2* __restrict__ items,
+                                                    const int* __restrict__ n_items) {
+    using TT = SpmvTmaTile<SERVE_LZ, SERVE_BY>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* zs = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float* us = zs + TT::ZN;
+    float* ps = us + TT::VN;
+    float* qs = ps + TT::VN;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(qs + TT::VN);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const uint32_t b = smem_u32(bar);
+    if (tid == 0) mbar_init(b);
+    __syncthreads();
+    uint32_t parity = 0;
+    bool broken = false;        // a staged copy timed out: this block computes nothing more
+    int last_slot = -1;         // slot whose tensor maps thread 0 acquired last
     const int n = *n_items;
     for (int it = blockIdx.x; it < n; it += gridDim.x) {
-        const int2 w = items[it];
-        const ServeSlot& s = slots[w.x];
+        const int2 wk = items[it];
+        const ServeSlot& s = slots[wk.x];
         SolveState* st = s.st;
         if (!st->done) {
-            const float alpha = (float)st->alpha;
-            const float beta = (float)st->beta;
-            const int bx = w.y % s.gx, by = w.y / s.gx;
-            const Col<float> col = make_col(s.op, bx * BX + threadIdx.x, by * BY + threadIdx.y);
+            const OpView<float>& op = s.op;
+            const int ch = wk.y % s.nch, tile = wk.y / s.nch;
+            const int i0 = (tile % s.gx) * BX, j0 = (tile / s.gx) * SERVE_BY, k0 = ch * SERVE_LZ;
+            const int kn = min(SERVE_LZ, op.nz - k0);
+            bool landed = !broken;
+            if (broken) {
+                if (tid == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT: this item is not computed
+            } else if (s.tmaps) {
+                if (tid == 0) {
+                    if (wk.x != last_slot) {
+                        for (int m = 0; m < 4; ++m) tmap_acquire(s.tmaps + m);
+                        last_slot = wk.x;
+                    }
+                    // earlier items may have written the tiles through the generic proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect(b, TT::BYTES);
+                    tma_load_3d(smem_u32(zs), s.tmaps + 3, i0 - TMA_HALO_X, j0 - 1, k0 - 1, b);
+                    tma_load_3d(smem_u32(us), s.tmaps + 0, i0, j0, k0, b);
+                    tma_load_3d(smem_u32(ps), s.tmaps + 1, i0, j0, k0, b);
+                    tma_load_3d(smem_u32(qs), s.tmaps + 2, i0, j0, k0, b);
+                }
+                // one verdict for the whole block
+                landed = __syncthreads_and(mbar_wait(b, parity, 1 << 22) ? 1 : 0) != 0;
+                if (!landed) {
+                    if (tid == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT
+                    mbar_wait(b, parity, 1 << 22);
+                    broken = true;
+                }
+                parity ^= 1u;
+            } else {
+                // staged by the threads, cells outside the grid as zeros
+                for (int e = tid; e < TT::ZN; e += 256) {
+                    const int xx = e % TT::ZX, yy = (e / TT::ZX) % TT::ZY, zz = e / (TT::ZX * TT::ZY);
+                    const int gi = i0 - TMA_HALO_X + xx, gj = j0 - 1 + yy, gk = k0 - 1 + zz;
+                    const bool in = gi >= 0 && gi < op.nx && gj >= 0 && gj < op.ny && gk >= 0 && gk < op.nz;
+                    zs[e] = in ? ldro(s.z + (long long)gk * op.plane + (long long)gj * op.nx + gi) : 0.f;
+                }
+                for (int e = tid; e < TT::VN; e += 256) {
+                    const int xx = e % BX, yy = (e / BX) % SERVE_BY, zz = e / (BX * SERVE_BY);
+                    const int gi = i0 + xx, gj = j0 + yy, gk = k0 + zz;
+                    const bool in = gi < op.nx && gj < op.ny && gk < op.nz;
+                    const long long o = (long long)gk * op.plane + (long long)gj * op.nx + gi;
+                    us[e] = in ? s.u[o] : 0.f;
+                    ps[e] = in ? s.p[o] : 0.f;
+                    qs[e] = in ? s.q[o] : 0.f;
+                }
+                __syncthreads();
+            }
             Acc<float> sig[1];
-            if (col.valid) spmv_column<float>(s.op, col, s.u + col.c, s.p + col.c, s.q + col.c, s.z, alpha, beta, sig[0]);
+            const Col<float> col = make_col(op, i0 + tx, j0 + ty);
+            if (landed && col.valid && kn > 0) {
+                const bool in_e = col.ce == col.c + 1, in_w = col.cw == col.c - 1;
+                const bool in_n = col.cn == col.c + op.nx, in_s = col.cs == col.c - op.nx;
+                spmv_tile_compute<SERVE_LZ, SERVE_BY>(op, col, tx, ty, k0, kn, zs, us, ps, qs, s.z, s.u, s.p, s.q,
+                                                      (float)st->alpha, (float)st->beta, in_e, in_w, in_n, in_s,
+                                                      sig[0]);
+            }
             double v[1];
-            if (grid_sum_acc<1>(sig, s.partials, s.counter, s.ntiles, w.y, v)) spmv_epilogue(st, v[0]);
+            if (grid_sum_acc<1>(sig, s.partials, s.counter, s.nspmv, wk.y, v)) spmv_epilogue(st, v[0]);
         }
-        __syncthreads();
+        __syncthreads();    // the tiles are refilled by the next item
     }
 }
 

@@ -7,6 +7,7 @@
 // the iteration live on the device; the host only polls the per-rhs `done`
 // flags between graph launches (two launches are kept in flight so the GPU
 // never waits for the poll).
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +42,8 @@ struct DevTables {
     void* fg = nullptr;
     void* fe = nullptr;
     void* fc = nullptr;
+    void* amass = nullptr;      // FP64 only: [rows][nz] area-folded level tables, or null
+    void* awv = nullptr;
 };
 
 }  // namespace
@@ -63,6 +66,16 @@ struct pcg_ctx {
     // workspace
     double *u64 = nullptr, *r64 = nullptr, *z64 = nullptr, *p64 = nullptr, *q64 = nullptr;
     float *u32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    // tensor maps of the FP32 u, p, q (own tile) and z (tile with halo) for the TMA SpMV sweep
+    CUtensorMap tm_u, tm_p, tm_q, tm_z;
+    bool tma_ready = false;
+    // ... and of r, q for the TMA preconditioner sweep (box 32 x prec_R x nch * lz_a)
+    CUtensorMap tm_pr, tm_pq;
+    int prec32 = 0;                       // FP32 preconditioner sweep: 0 column/chunked, 2 TMA pipeline
+    bool prec_tma_ready = false;
+    int prec_R = 1, prec_gx = 1, prec_items = 0, prec_G = 1;
+    dim3 grid_t, block_t;
+    int nblk_t = 0;
     double *hb = nullptr, *hx = nullptr;  // device staging for pcg_solve_host
     SolveState* st = nullptr;              // [nrhs] outer / FP64 state
     SolveState* st_in = nullptr;           // [nrhs] inner FP32 state
@@ -74,7 +87,7 @@ struct pcg_ctx {
     dim3 grid, block;
     // chunked sweeps (levels split across threads): launch shapes
     int chunked32 = 0, chunked64 = 0, lz_a = 16, lz_b = 16, nch_b = 1;
-    int spmv32 = 0, spmv64 = 0;          // SpMV sweep variant: 0 per column, 1 chunked, 2 chunked + smem tile
+    int spmv32 = 0, spmv64 = 0;          // SpMV sweep variant: 0 per column, 1 chunked, 2 chunked + smem tile, 3 TMA
     // minimum resident blocks asked of the compiler for the chunked FP32 sweeps;
     // 3 for the preconditioner sweep (85-register cap, no spills) measured
     // 9-13 % faster than the uncapped 108 registers at 256^2, 1024^2 and the shell
@@ -116,6 +129,9 @@ struct pcg_ctx {
         v.cls_mode = cls_mode;
         v.ncls = ncls;
         v.area_percol = geometry == PCG_GEOM_CUBED_PANEL ? 1 : 0;
+        v.amass = (const T*)t.amass;
+        v.awv = (const T*)t.awv;
+        v.arow_step = geometry == PCG_GEOM_LATLON ? 1 : 0;
         return v;
     }
 };
@@ -272,7 +288,10 @@ int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables
 
 int upload_tables(pcg_t h, const HostTables& t) {
     const size_t nz = h->nz, ny = t.area.size(), nxy = (size_t)h->nx * h->ny, nf = (size_t)nz * h->ncls;
-    const size_t n64 = 3 * nz + ny + 2 * nxy + 3 * nf;
+    // area-folded level tables for the FP64 SpMV sweep: one row (box), one per
+    // latitude row (latlon), none when the area varies per column (panel)
+    const size_t frows = h->geometry == PCG_GEOM_BOX ? 1 : (h->geometry == PCG_GEOM_LATLON ? (size_t)h->ny : 0);
+    const size_t n64 = 3 * nz + ny + 2 * nxy + 3 * nf + 2 * frows * nz;
     double* b64 = nullptr;
     float* b32 = nullptr;
     int rc = dmalloc(h, &b64, n64);
@@ -296,6 +315,11 @@ int upload_tables(pcg_t h, const HostTables& t) {
     carve(nf, h->t64.fg, h->t32.fg);
     carve(nf, h->t64.fe, h->t32.fe);
     carve(nf, h->t64.fc, h->t32.fc);
+    void *am32 = nullptr, *aw32 = nullptr;
+    if (frows) {
+        carve(frows * nz, h->t64.amass, am32);
+        carve(frows * nz, h->t64.awv, aw32);
+    }
     cudaStream_t s = h->stream;
     PCG_CK(h, cudaMemcpyAsync(h->t64.mass, t.mass.data(), nz * 8, cudaMemcpyHostToDevice, s));
     PCG_CK(h, cudaMemcpyAsync(h->t64.wv, t.wv.data(), nz * 8, cudaMemcpyHostToDevice, s));
@@ -303,6 +327,16 @@ int upload_tables(pcg_t h, const HostTables& t) {
     PCG_CK(h, cudaMemcpyAsync(h->t64.area, t.area.data(), ny * 8, cudaMemcpyHostToDevice, s));
     PCG_CK(h, cudaMemcpyAsync(h->t64.mue, t.mue.data(), nxy * 8, cudaMemcpyHostToDevice, s));
     PCG_CK(h, cudaMemcpyAsync(h->t64.mun, t.mun.data(), nxy * 8, cudaMemcpyHostToDevice, s));
+    if (frows) {
+        std::vector<double> fold(2 * frows * nz);
+        for (size_t j = 0; j < frows; ++j)
+            for (size_t k = 0; k < nz; ++k) {
+                fold[j * nz + k] = t.area[j] * t.mass[k];
+                fold[(frows + j) * nz + k] = t.area[j] * t.wv[k];
+            }
+        // pageable source: the copy has consumed it when the call returns
+        PCG_CK(h, cudaMemcpyAsync(h->t64.amass, fold.data(), 2 * frows * nz * 8, cudaMemcpyHostToDevice, s));
+    }
     // Thomas factors of every class, in FP64 on the device
     const OpView<double> v = h->view64();
     pcg::k_factors<<<(h->ncls + 127) / 128, 128, 0, s>>>(v, (double*)h->t64.fg, (double*)h->t64.fe,
@@ -323,11 +357,81 @@ int ensure_ws64(pcg_t h) {
     return PCG_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    return fn;
+}
+
+// Tensor map of an FP32 array [nlev][ny][nx] with box bx x by x bz (rows of
+// a multiple of 16 bytes: nx % 4 == 0).
+bool encode_map_dims(CUtensorMap* m, float* base, long long nx, long long ny, long long nlev, unsigned bx,
+                     unsigned by, unsigned bz) {
+    auto enc = tensor_map_encoder();
+    if (!enc || nx % 4 != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nlev};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
+    const cuuint32_t box[3] = {bx, by, bz};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ... of a handle's FP32 vector [nrhs * n_z][n_y][n_x]
+bool encode_map(pcg_t h, CUtensorMap* m, float* base, unsigned bx, unsigned by, unsigned bz) {
+    return encode_map_dims(m, base, h->nx, h->ny, (long long)h->nz * h->nrhs, bx, by, bz);
+}
+
+constexpr int TMA_LZ = 16, TMA_BY = 8;
+using SpmvTile = pcg::SpmvTmaTile<TMA_LZ, TMA_BY>;
+
 int ensure_ws32(pcg_t h) {
     if (h->u32) return PCG_OK;
     int rc;
     for (float** p : {&h->u32, &h->r32, &h->z32, &h->p32, &h->q32})
         if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
+    if (h->spmv32 == 3) {
+        // the TMA SpMV sweep: maps of the workspace vectors; fall back to the
+        // chunked sweep when the driver cannot encode them
+        const unsigned zx = BX + 2 * pcg::TMA_HALO_X;
+        h->tma_ready = encode_map(h, &h->tm_u, h->u32, BX, TMA_BY, TMA_LZ) &&
+                       encode_map(h, &h->tm_p, h->p32, BX, TMA_BY, TMA_LZ) &&
+                       encode_map(h, &h->tm_q, h->q32, BX, TMA_BY, TMA_LZ) &&
+                       encode_map(h, &h->tm_z, h->z32, zx, TMA_BY + 2, TMA_LZ + 2) &&
+                       cudaFuncSetAttribute(pcg::k_sweep_spmv_tma<TMA_LZ, TMA_BY>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)SpmvTile::SMEM) == cudaSuccess;
+        if (!h->tma_ready) h->spmv32 = (h->chunked32 && h->plane * (long long)h->nrhs < (1LL << 19)) ? 1 : 0;
+    }
+    if (h->prec32 == 2) {
+        const unsigned lev = (unsigned)(((h->nz + h->lz_a - 1) / h->lz_a) * h->lz_a);
+        int occ = 0;
+        cudaError_t ea = cudaFuncSetAttribute(pcg::k_sweep_prec_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)pcg::PrecTmaTile<16>::SMEM);
+        if (ea == cudaSuccess)
+            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg::k_sweep_prec_tma<16>, 256,
+                                                               pcg::PrecTmaTile<16>::SMEM);
+        int dev = 0, sms = 1;
+        if (ea == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        h->prec_tma_ready = ea == cudaSuccess && occ >= 1 &&
+                            encode_map(h, &h->tm_pr, h->r32, BX, (unsigned)h->prec_R, lev) &&
+                            encode_map(h, &h->tm_pq, h->q32, BX, (unsigned)h->prec_R, lev);
+        // persistent grid: the resident blocks of every SM, shared by the right-hand sides
+        h->prec_G = std::max(1, std::min(h->prec_items, sms * std::max(occ, 1) / std::max(1, h->nrhs)));
+        if (!h->prec_tma_ready) h->prec32 = 0;
+    }
     return PCG_OK;
 }
 
@@ -338,6 +442,16 @@ bool use_chunked(pcg_t h) { return sizeof(T) == 4 ? h->chunked32 != 0 : h->chunk
 template <typename T>
 void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, SolveState* st) {
     const bool chunked = use_chunked<T>(h);
+    if constexpr (sizeof(T) == 4) {
+        if (h->prec32 == 2 && h->prec_tma_ready && r == h->r32 && q == h->q32 && z == h->z32) {
+            const dim3 grid(h->prec_G, h->nrhs, 1), block(BX, 8, 1);
+            const int nch = (h->nz + h->lz_a - 1) / h->lz_a;
+            pcg::k_sweep_prec_tma<16><<<grid, block, pcg::PrecTmaTile<16>::SMEM, s>>>(
+                v, h->tm_pr, h->tm_pq, r, q, z, st, h->partials, h->counters, h->prec_R, nch, h->prec_gx,
+                h->prec_items);
+            return;
+        }
+    }
 #define PCG_PREC_CH(LZ, MB)                                                                                  \
     pcg::k_sweep_prec_chunked<T, LZ, MB><<<h->grid_a, h->block_a, 0, s>>>(v, r, q, z, st, h->partials, h->counters, \
                                                                           h->nblk_a)
@@ -359,12 +473,19 @@ void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, 
 #define PCG_SPMV_CH(LZ, TILE, MB)                                                                            \
     pcg::k_sweep_spmv_chunked<T, LZ, TILE, MB><<<h->grid_b, h->block_b, 0, s>>>(v, u, p, q, z, st, h->partials,  \
                                                                                 h->counters, h->nblk_b, h->nch_b)
+    if constexpr (sizeof(T) == 4) {
+        if (mode == 3 && h->tma_ready && u == h->u32 && p == h->p32 && q == h->q32 && z == h->z32) {
+            pcg::k_sweep_spmv_tma<TMA_LZ, TMA_BY><<<h->grid_t, h->block_t, SpmvTile::SMEM, s>>>(
+                v, h->tm_u, h->tm_p, h->tm_q, h->tm_z, u, p, q, z, st, h->partials, h->counters, h->nblk_t, h->nch_b);
+            return;
+        }
+    }
     if (mode == 2) {
         PCG_SPMV_CH(16, true, 1);
-    } else if (mode == 1 && h->lz_b == 8) {
+    } else if ((mode == 1 || mode == 3) && h->lz_b == 8) {
         if (h->spmv_minb == 8) PCG_SPMV_CH(8, false, 8);
         else PCG_SPMV_CH(8, false, 1);
-    } else if (mode == 1) {
+    } else if (mode == 1 || mode == 3) {
         if (h->spmv_minb == 6) PCG_SPMV_CH(16, false, 6);
         else PCG_SPMV_CH(16, false, 1);
     } else {
@@ -554,7 +675,8 @@ int solve_mixed(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_
             if (!active[r]) continue;
             sweeps[r] += 1;
             inner_it[r] += std::max(0, h->h_st[nr + r].pass - 1);
-            if (h->h_st[nr + r].status == PCG_BREAKDOWN) { done[r] = 1; status[r] = PCG_BREAKDOWN; }
+            const int is = h->h_st[nr + r].status;
+            if (is == PCG_BREAKDOWN || is == PCG_TIMEOUT) { done[r] = 1; status[r] = is; }
         }
     }
     int worst = PCG_OK;
@@ -691,16 +813,44 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->grid_b = dim3((h->nx + BX - 1) / BX, (h->ny + BY - 1) / BY, h->nrhs * h->nch_b);
     h->nblk_b = (int)(h->grid_b.x * h->grid_b.y) * h->nch_b;
     if ((long long)h->nrhs * h->nch_b > 65535 || h->grid_a.y > 65535) h->chunked32 = h->chunked64 = 0;
-    // FP32 SpMV sweep: chunked while the grid has few columns (65536 columns:
-    // 76 us vs 124 us per sweep at 128 levels); one thread per column once there
-    // are enough columns to hide latency (2^20 columns: 902 us vs 1062 us).
-    // A shared-memory z tile with halo measured slower than both at both
-    // sizes and is kept only as an experiment (PCG_SPMV=tile).
+    // FP32 SpMV sweep without TMA: chunked while the grid has few columns
+    // (65536 columns: 93 us vs 123 us per sweep at 128 levels); one thread per
+    // column once there are enough columns to hide latency (2^20 columns:
+    // 966 us vs 1300 us).  A shared-memory z tile loaded by the threads
+    // measured slower than both and is kept only as an experiment (PCG_SPMV=tile).
     h->spmv32 = (h->chunked32 && h->plane * (long long)h->nrhs < (1LL << 19)) ? 1 : 0;
     h->spmv64 = h->chunked64 ? 1 : 0;
-    if (const char* sv = std::getenv("PCG_SPMV")) {            // experiments: column|chunked|tile
-        const int m = !std::strcmp(sv, "tile") ? 2 : (!std::strcmp(sv, "chunked") ? 1 : 0);
-        if (h->nz <= 256 && (long long)h->nrhs * h->nch_b <= 65535) h->spmv32 = h->spmv64 = m;
+    // TMA-staged FP32 SpMV sweep (k_sweep_spmv_tma): tiles of 32 x 8 columns x
+    // 16 levels; the tensor maps need rows of a multiple of 16 bytes (n_x % 4 == 0)
+    h->block_t = dim3(BX, TMA_BY, 1);
+    h->grid_t = dim3((h->nx + BX - 1) / BX, (h->ny + TMA_BY - 1) / TMA_BY, h->nrhs * h->nch_b);
+    h->nblk_t = (int)(h->grid_t.x * h->grid_t.y) * h->nch_b;
+    const bool tma_ok = h->lz_b == TMA_LZ && h->nx % 4 == 0 && (long long)h->nrhs * h->nch_b <= 65535 &&
+                        (long long)h->nz * h->nrhs < (1LL << 31);
+    // the TMA sweep wherever it applies: 65536 columns 72 us, 2^20 columns
+    // 923 us per sweep at 128 levels (3.3 and 4.1 TB/s)
+    if (tma_ok) h->spmv32 = 3;
+    // TMA-pipelined FP32 preconditioner sweep: items of prec_R rows of 32
+    // columns (prec_R x chunks <= 8 warps), same eligibility plus the chunked form
+    {
+        const int nch_p = (h->nz + h->lz_a - 1) / h->lz_a;
+        h->prec_R = std::max(1, 8 / nch_p);
+        h->prec_gx = (h->nx + BX - 1) / BX;
+        h->prec_items = h->prec_gx * ((h->ny + h->prec_R - 1) / h->prec_R);
+        const bool ptma_ok = h->chunked32 && h->lz_a == 16 && nch_p <= 8 && h->nx % 4 == 0 && h->nrhs <= 65535 &&
+                             (long long)h->nz * h->nrhs < (1LL << 31);
+        h->prec32 = 0;                                             // TMA pipeline: opt-in until measured
+        if (const char* pv = std::getenv("PCG_PREC")) {            // experiments: chunked|tma
+            if (!std::strcmp(pv, "chunked")) h->prec32 = 0;
+            if (!std::strcmp(pv, "tma")) h->prec32 = ptma_ok ? 2 : 0;
+        }
+    }
+    if (const char* sv = std::getenv("PCG_SPMV")) {            // experiments: column|chunked|tile|tma
+        const int m = !std::strcmp(sv, "tile") ? 2 : (!std::strcmp(sv, "chunked") ? 1 : (!std::strcmp(sv, "tma") ? 3 : 0));
+        if (h->nz <= 256 && (long long)h->nrhs * h->nch_b <= 65535) {
+            h->spmv32 = (m == 3 && !tma_ok) ? 1 : m;
+            if (m != 3) h->spmv64 = m;
+        }
     }
 
     auto bail = [&](int rc) {
@@ -720,7 +870,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if ((rc = dmalloc(h, &h->st, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->st_in, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->d_active, h->nrhs))) return bail(rc);
-    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(std::max(h->nblocks, h->nblk_c), std::max(h->nblk_a, h->nblk_b)) * 4))) return bail(rc);
+    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(std::max(std::max(h->nblocks, h->nblk_c), h->prec_items), std::max(std::max(h->nblk_a, h->nblk_b), h->nblk_t)) * 4))) return bail(rc);
     if ((rc = dmalloc(h, &h->counters, h->nrhs))) return bail(rc);
     e = cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * h->nrhs, h->stream);
     if (e != cudaSuccess) { h->err = std::string("cudaMemset: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
@@ -1026,6 +1176,9 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
     v.cls_mode = cls_mode;
     v.ncls = (int)ncls;
     v.area_percol = 0;
+    v.amass = nullptr;
+    v.awv = nullptr;
+    v.arow_step = 0;
     // the factors are rewritten in full by every call, so nothing left by an
     // earlier call is read
     pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, s>>>(v, fg, fe, fc);

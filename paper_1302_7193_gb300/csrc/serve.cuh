@@ -9,8 +9,10 @@
 // (Algorithm 1), FP64 update.  The inner iterations of all requests that are
 // in their inner phase advance together: one CUDA graph holds
 // `epochs_per_launch` epochs, an epoch being one launch of k_serve_prec and
-// one of k_serve_spmv, persistent kernels that walk the work list of
-// (slot, tile) items of every such request.  Between graph launches the host
+// one of k_serve_spmv, persistent kernels that walk the work lists of
+// (slot, item) pairs of every such request (preconditioner items: rows of
+// 32 columns split into 16-level chunks; SpMV items: 32 x 8-column tiles of
+// one 16-level chunk, staged by bulk tensor copies).  Between graph launches the host
 // runs the FP64 refinement steps of requests whose inner solve finished,
 // retires requests that converged (their x is copied out and their memory
 // returned) and admits waiting requests into the freed slots, so new
@@ -41,7 +43,9 @@ struct ServeReq {
     double* partials = nullptr;
     unsigned* counter = nullptr;
     double total_mass = 0.0;
-    int gx = 0, gy = 0, ntiles = 0;
+    int gx = 0, gy = 0, ntiles = 0;          // 32 x 4 tiles (residual kernels)
+    int nch = 1, rows = 1, colmode = 0, nprec = 0, nspmv = 0;   // served sweep items
+    CUtensorMap* tmaps = nullptr;            // device copies of the u, p, q, z maps, or null
     std::vector<double> hist;
     double bb = 0.0, last_rr = 0.0, floor_rel = 0.0;
     int sweeps = 0, inner_its = 0, status = PCG_NOT_CONVERGED, stag = 0;
@@ -49,6 +53,8 @@ struct ServeReq {
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+using ServeSpmvTile = pcg::SpmvTmaTile<pcg::SERVE_LZ, pcg::SERVE_BY>;
 
 }  // namespace
 
@@ -67,15 +73,17 @@ struct pcg_server {
     std::vector<pcg::ServeSlot> h_slots;
     SolveState* d_states = nullptr;     // [max_slots][2]: inner, outer
     SolveState* h_states = nullptr;     // pinned mirror
-    int2* d_items = nullptr;
-    int* d_nitems = nullptr;
-    int2* h_items = nullptr;            // pinned
-    int* h_nitems = nullptr;            // pinned
+    int2* d_items = nullptr;            // [2][items_cap]: preconditioner items, then SpMV items
+    int* d_nitems = nullptr;            // [2]
+    int2* h_items = nullptr;            // pinned mirror
+    int* h_nitems = nullptr;            // pinned [2]
     int* d_one = nullptr;
     int items_cap = 0;
     bool items_dirty = true;
     cudaGraphExec_t graph = nullptr;
-    int persistent_blocks = 152 * 8;
+    int blocks_prec = 152 * 3, blocks_spmv = 152 * 2;   // persistent grids (resident blocks on every SM)
+    int no_tma = 0;                     // PCG_SERVE_TMA=0: stage the SpMV tiles by the threads
+    int prec_minb = 2;                  // PCG_SERVE_PREC_MINB=3: preconditioner kernel with 3 blocks per SM
     long long epochs = 0, launches = 0, retired = 0;
     int trace = 0;                      // PCG_TRACE=1: refinement history per request on stderr
     std::string err = "no error";
@@ -107,13 +115,31 @@ size_t area_count(const pcg_grid_t& g) {
     return g.geometry == PCG_GEOM_CUBED_PANEL ? (size_t)g.n_x * g.n_y : (size_t)g.n_y;
 }
 
+// Work items of a request in the served sweeps (see k_serve_prec / k_serve_spmv).
+struct ServeItems {
+    int gx, nch, rows, colmode, nprec, nspmv;
+};
+
+ServeItems serve_items(const pcg_grid_t& g) {
+    ServeItems it;
+    it.gx = (g.n_x + BX - 1) / BX;
+    it.nch = (g.n_z + pcg::SERVE_LZ - 1) / pcg::SERVE_LZ;
+    it.colmode = it.nch > 8 ? 1 : 0;
+    it.rows = it.colmode ? 8 : 8 / it.nch;
+    it.nprec = it.gx * ((g.n_y + it.rows - 1) / it.rows);
+    it.nspmv = it.gx * ((g.n_y + pcg::SERVE_BY - 1) / pcg::SERVE_BY) * it.nch;
+    return it;
+}
+
 size_t request_bytes(const pcg_grid_t& g, int cls_mode) {
     const size_t nx = g.n_x, ny = g.n_y, nz = g.n_z, nxy = nx * ny, vol = nxy * nz;
     const size_t ncls = cls_mode == 0 ? 1 : (cls_mode == 1 ? ny : nxy);
     const size_t ntab = 3 * nz + area_count(g) + 2 * nxy + 2 * nz * ncls;
     const size_t ntiles = ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY);
+    const ServeItems it = serve_items(g);
+    const size_t nparts = std::max(ntiles, (size_t)std::max(it.nprec, it.nspmv));
     return align_up(ntab * 8) + align_up(ntab * 4) + 2 * align_up(vol * 8) + 5 * align_up(vol * 4) +
-           align_up(ntiles * 4 * 8) + 256;
+           align_up(nparts * 4 * 8) + align_up(4 * sizeof(CUtensorMap)) + 256;
 }
 
 int admit(pcg_server_t s, ServeReq* q) {
@@ -152,8 +178,12 @@ int admit(pcg_server_t s, ServeReq* q) {
         *v = (float*)m;
         m += align_up(vol * 4);
     }
+    const ServeItems its = serve_items(g);
+    q->nch = its.nch; q->rows = its.rows; q->colmode = its.colmode; q->nprec = its.nprec; q->nspmv = its.nspmv;
     q->partials = (double*)m;
-    m += align_up((size_t)q->ntiles * 4 * 8);
+    m += align_up((size_t)std::max(q->ntiles, std::max(q->nprec, q->nspmv)) * 4 * 8);
+    q->tmaps = (CUtensorMap*)m;             // 256-byte aligned like every carved region
+    m += align_up(4 * sizeof(CUtensorMap));
     q->counter = (unsigned*)m;
     // tables: same carving as a solver handle
     auto carve = [&](auto& op, auto* base) {
@@ -168,6 +198,7 @@ int admit(pcg_server_t s, ServeReq* q) {
         op.periodic_y = g.geometry == PCG_GEOM_LATLON ? 0 : 1;
         op.cls_mode = cls_mode; op.ncls = (int)ncls;
         op.area_percol = g.geometry == PCG_GEOM_CUBED_PANEL ? 1 : 0;
+        op.amass = nullptr; op.awv = nullptr; op.arow_step = 0;
     };
     carve(q->op64, t64);
     carve(q->op32, t32);
@@ -184,6 +215,22 @@ int admit(pcg_server_t s, ServeReq* q) {
     SRV_CK(s, cudaMemcpyAsync(q->bd, q->b.data(), vol * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemsetAsync(q->xd, 0, vol * 8, st));
     SRV_CK(s, cudaMemsetAsync(q->counter, 0, sizeof(unsigned), st));
+    {
+        // tensor maps of the SpMV sweep's staged tiles (boxes as k_sweep_spmv_tma);
+        // without them the tiles are staged by the threads
+        CUtensorMap hm[4];
+        const unsigned zx = BX + 2 * pcg::TMA_HALO_X;
+        const bool ok = encode_map_dims(&hm[0], q->u, nx, ny, nz, BX, pcg::SERVE_BY, pcg::SERVE_LZ) &&
+                        encode_map_dims(&hm[1], q->p, nx, ny, nz, BX, pcg::SERVE_BY, pcg::SERVE_LZ) &&
+                        encode_map_dims(&hm[2], q->q, nx, ny, nz, BX, pcg::SERVE_BY, pcg::SERVE_LZ) &&
+                        encode_map_dims(&hm[3], q->z, nx, ny, nz, zx, pcg::SERVE_BY + 2, pcg::SERVE_LZ + 2);
+        if (ok && !s->no_tma) {
+            // pageable source: the call returns once the maps have been staged
+            SRV_CK(s, cudaMemcpyAsync(q->tmaps, hm, sizeof(hm), cudaMemcpyHostToDevice, st));
+        } else {
+            q->tmaps = nullptr;
+        }
+    }
     SRV_CK(s, cudaGetLastError());
     s->launches += 2;
     // slot
@@ -199,7 +246,12 @@ int admit(pcg_server_t s, ServeReq* q) {
     hs.partials = q->partials;
     hs.counter = q->counter;
     hs.gx = q->gx;
-    hs.ntiles = q->ntiles;
+    hs.nch = q->nch;
+    hs.rows = q->rows;
+    hs.colmode = q->colmode;
+    hs.nprec = q->nprec;
+    hs.nspmv = q->nspmv;
+    hs.tmaps = q->tmaps;
     SRV_CK(s, cudaMemcpyAsync(s->d_slots + slot, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
     pcg::k_init_state<<<1, 32, 0, st>>>(s->d_states + 2 * slot, 2, 0.0, 0, nullptr);
     s->launches += 1;
@@ -298,19 +350,25 @@ int measure_and_decide(pcg_server_t s) {
 }
 
 int rebuild_items(pcg_server_t s) {
-    long long n = 0;
+    long long na = 0, nb = 0;
     for (ServeReq* q : s->slot_req)
-        if (q && q->phase == RQ_INNER) n += q->ntiles;
-    if (n > s->items_cap) return sfail(s, PCG_ERR_OOM, "work list capacity exceeded");
-    int k = 0;
+        if (q && q->phase == RQ_INNER) { na += q->nprec; nb += q->nspmv; }
+    if (na > s->items_cap || nb > s->items_cap) return sfail(s, PCG_ERR_OOM, "work list capacity exceeded");
+    int2* ha = s->h_items;
+    int2* hb = s->h_items + s->items_cap;
+    int ka = 0, kb = 0;
     for (ServeReq* q : s->slot_req) {
         if (!q || q->phase != RQ_INNER) continue;
-        for (int t = 0; t < q->ntiles; ++t) s->h_items[k++] = make_int2(q->slot, t);
+        for (int t = 0; t < q->nprec; ++t) ha[ka++] = make_int2(q->slot, t);
+        for (int t = 0; t < q->nspmv; ++t) hb[kb++] = make_int2(q->slot, t);
     }
-    *s->h_nitems = (int)n;
-    SRV_CK(s, cudaMemcpyAsync(s->d_items, s->h_items, sizeof(int2) * (size_t)std::max<long long>(n, 1),
+    s->h_nitems[0] = (int)na;
+    s->h_nitems[1] = (int)nb;
+    SRV_CK(s, cudaMemcpyAsync(s->d_items, ha, sizeof(int2) * (size_t)std::max<long long>(na, 1),
                               cudaMemcpyHostToDevice, s->stream));
-    SRV_CK(s, cudaMemcpyAsync(s->d_nitems, s->h_nitems, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    SRV_CK(s, cudaMemcpyAsync(s->d_items + s->items_cap, hb, sizeof(int2) * (size_t)std::max<long long>(nb, 1),
+                              cudaMemcpyHostToDevice, s->stream));
+    SRV_CK(s, cudaMemcpyAsync(s->d_nitems, s->h_nitems, 2 * sizeof(int), cudaMemcpyHostToDevice, s->stream));
     s->items_dirty = false;
     return PCG_OK;
 }
@@ -319,8 +377,12 @@ int capture_epochs(pcg_server_t s) {
     cudaGraph_t g = nullptr;
     SRV_CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int e = 0; e < s->epochs_per_launch; ++e) {
-        pcg::k_serve_prec<<<s->persistent_blocks, dim3(BX, BY, 1), 0, s->cap_stream>>>(s->d_slots, s->d_items, s->d_nitems);
-        pcg::k_serve_spmv<<<s->persistent_blocks, dim3(BX, BY, 1), 0, s->cap_stream>>>(s->d_slots, s->d_items, s->d_nitems);
+        if (s->prec_minb == 3)
+            pcg::k_serve_prec<3><<<s->blocks_prec, dim3(BX, 8, 1), 0, s->cap_stream>>>(s->d_slots, s->d_items, s->d_nitems);
+        else
+            pcg::k_serve_prec<2><<<s->blocks_prec, dim3(BX, 8, 1), 0, s->cap_stream>>>(s->d_slots, s->d_items, s->d_nitems);
+        pcg::k_serve_spmv<<<s->blocks_spmv, dim3(BX, pcg::SERVE_BY, 1), ServeSpmvTile::SMEM, s->cap_stream>>>(
+            s->d_slots, s->d_items + s->items_cap, s->d_nitems + 1);
     }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
     if (e != cudaSuccess) return sfail(s, PCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -370,28 +432,45 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
     struct { void** p; size_t b; } dev_allocs[] = {
         {(void**)&s->d_slots, sizeof(pcg::ServeSlot) * max_slots},
         {(void**)&s->d_states, sizeof(SolveState) * 2 * max_slots},
-        {(void**)&s->d_items, sizeof(int2) * (size_t)s->items_cap},
-        {(void**)&s->d_nitems, sizeof(int)},
+        {(void**)&s->d_items, 2 * sizeof(int2) * (size_t)s->items_cap},
+        {(void**)&s->d_nitems, 2 * sizeof(int)},
         {(void**)&s->d_one, sizeof(int)},
     };
     for (auto& a : dev_allocs)
         if ((e = cudaMalloc(a.p, a.b)) != cudaSuccess) { *a.p = nullptr; s->err = "cudaMalloc failed"; return bail(PCG_ERR_OOM); }
     if ((e = cudaMallocHost((void**)&s->h_states, sizeof(SolveState) * 2 * max_slots)) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&s->h_items, sizeof(int2) * (size_t)s->items_cap)) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&s->h_nitems, sizeof(int))) != cudaSuccess) {
+        (e = cudaMallocHost((void**)&s->h_items, 2 * sizeof(int2) * (size_t)s->items_cap)) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&s->h_nitems, 2 * sizeof(int))) != cudaSuccess) {
         s->err = "cudaMallocHost failed";
         return bail(PCG_ERR_OOM);
     }
     const int one = 1;
     if ((e = cudaMemcpy(s->d_one, &one, sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(s->d_nitems, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(s->d_nitems, 0, 2 * sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(s->d_slots, 0, sizeof(pcg::ServeSlot) * max_slots)) != cudaSuccess) {
         s->err = cudaGetErrorString(e);
         return bail(PCG_ERR_CUDA);
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    s->persistent_blocks = sms * 8;
+    if (const char* e2 = std::getenv("PCG_SERVE_TMA")) s->no_tma = std::atoi(e2) == 0 ? 1 : 0;
+    // persistent grids: as many blocks as are resident on every SM at once
+    if ((e = cudaFuncSetAttribute(pcg::k_serve_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ServeSpmvTile::SMEM)) != cudaSuccess) {
+        s->err = cudaGetErrorString(e);
+        return bail(PCG_ERR_CUDA);
+    }
+    if (const char* e3 = std::getenv("PCG_SERVE_PREC_MINB")) s->prec_minb = std::atoi(e3) == 3 ? 3 : 2;
+    int occ_a = 0, occ_b = 0;
+    cudaError_t eo = s->prec_minb == 3
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<3>, BX * 8, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<2>, BX * 8, 0);
+    if (eo != cudaSuccess || occ_a < 1) occ_a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, pcg::k_serve_spmv, BX * pcg::SERVE_BY,
+                                                      ServeSpmvTile::SMEM) != cudaSuccess || occ_b < 1)
+        occ_b = 1;
+    s->blocks_prec = sms * occ_a;
+    s->blocks_spmv = sms * occ_b;
     *out = s;
     return PCG_OK;
 }
@@ -481,8 +560,8 @@ int pcg_serve_step(pcg_server_t s, int max_epochs, int* n_active, int* n_pending
             if (!si.done) continue;
             q->sweeps += 1;
             q->inner_its += std::max(0, si.pass - 1);
-            if (si.status == PCG_BREAKDOWN) {
-                q->status = PCG_BREAKDOWN;
+            if (si.status == PCG_BREAKDOWN || si.status == PCG_TIMEOUT) {
+                q->status = si.status;
                 rc = retire(s, q);
                 if (rc) return rc;
                 s->items_dirty = true;
