@@ -84,6 +84,8 @@ struct pcg_server {
     int blocks_prec = 152 * 3, blocks_spmv = 152 * 2;   // persistent grids (resident blocks on every SM)
     int no_tma = 0;                     // PCG_SERVE_TMA=0: stage the SpMV tiles by the threads
     int prec_minb = 2;                  // PCG_SERVE_PREC_MINB=3: preconditioner kernel with 3 blocks per SM
+    long long active_cap = 0;           // PCG_SERVE_ACTIVE: admit while the admitted unknowns stay below this (0: no cap)
+    long long active_unknowns = 0;      // unknowns of the admitted requests
     long long epochs = 0, launches = 0, retired = 0;
     int trace = 0;                      // PCG_TRACE=1: refinement history per request on stderr
     std::string err = "no error";
@@ -256,6 +258,7 @@ int admit(pcg_server_t s, ServeReq* q) {
     pcg::k_init_state<<<1, 32, 0, st>>>(s->d_states + 2 * slot, 2, 0.0, 0, nullptr);
     s->launches += 1;
     s->used += q->bytes;
+    s->active_unknowns += (long long)vol;
     q->phase = RQ_MEASURE;
     q->t_admit = now_ms();
     q->b.clear();
@@ -269,6 +272,7 @@ int retire(pcg_server_t s, ServeReq* q) {
     SRV_CK(s, cudaFreeAsync(q->dmem, s->stream));
     SRV_CK(s, cudaStreamSynchronize(s->stream));
     s->used -= q->bytes;
+    s->active_unknowns -= (long long)q->grid.n_x * q->grid.n_y * q->grid.n_z;
     q->dmem = nullptr;
     s->slot_req[q->slot] = nullptr;
     q->slot = -1;
@@ -461,6 +465,7 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
         return bail(PCG_ERR_CUDA);
     }
     if (const char* e3 = std::getenv("PCG_SERVE_PREC_MINB")) s->prec_minb = std::atoi(e3) == 3 ? 3 : 2;
+    if (const char* e4 = std::getenv("PCG_SERVE_ACTIVE")) s->active_cap = std::atoll(e4);
     int occ_a = 0, occ_b = 0;
     cudaError_t eo = s->prec_minb == 3
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<3>, BX * 8, 0)
@@ -529,6 +534,9 @@ int pcg_serve_step(pcg_server_t s, int max_epochs, int* n_active, int* n_pending
             for (ServeReq* r : s->slot_req) if (!r) { free_slot = true; break; }
             const int cls_mode = serve_cls_mode(q->grid, !q->alpha_e.empty() || !q->alpha_n.empty());
             if (!free_slot || s->used + request_bytes(q->grid, cls_mode) > s->budget) break;
+            // optional cap on the unknowns in flight (the first request always fits)
+            const long long qn = (long long)q->grid.n_x * q->grid.n_y * q->grid.n_z;
+            if (s->active_cap > 0 && s->active_unknowns > 0 && s->active_unknowns + qn > s->active_cap) break;
             s->pending.pop_front();
             int rc = admit(s, q);
             if (rc) return rc;
