@@ -216,7 +216,15 @@ def run_serve(args, dev, pkg, W, torch):
     request is submitted at its arrival time; latency = submission to
     retirement.  Right-hand sides are generated before the clock starts."""
     import numpy as np
-    reqs = W.request_stream(duration_s=args.serve_seconds, rate_hz=200.0, seed=1)
+    scale = 1.0
+    if args.serve_mix == "small":
+        # the same stream restricted to requests of at most 128 x 128 x 64
+        # (each too small to fill the GPU alone), arrivals 10x denser
+        reqs = [r for r in W.request_stream(duration_s=10.0 * args.serve_seconds, rate_hz=200.0, seed=1)
+                if r.problem.n_x <= 128 and r.problem.n_y <= 128 and r.problem.n_z <= 64]
+        scale = 0.1
+    else:
+        reqs = W.request_stream(duration_s=args.serve_seconds, rate_hz=200.0, seed=1)
     rhs = [W.rhs_for(r.problem, seed=r.rhs_seed) for r in reqs]
     rhs_keep = list(rhs) if args.serve_compare else None
     stream = torch.cuda.current_stream(dev)
@@ -232,12 +240,12 @@ def run_serve(args, dev, pkg, W, torch):
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         while i < len(reqs) or live:
             now = time.perf_counter() - t0
-            while i < len(reqs) and reqs[i].arrival_s <= now:
+            while i < len(reqs) and reqs[i].arrival_s * scale <= now:
                 live[srv.submit(reqs[i].problem, rhs[i], tol=reqs[i].tol)] = reqs[i]
                 rhs[i] = None
                 i += 1
             if not live:
-                time.sleep(max(0.0, reqs[i].arrival_s - (time.perf_counter() - t0)))
+                time.sleep(max(0.0, reqs[i].arrival_s * scale - (time.perf_counter() - t0)))
                 continue
             srv.step(8)
             for rid in list(live):
@@ -254,7 +262,8 @@ def run_serve(args, dev, pkg, W, torch):
     unknowns = sum(r.problem.n_cells for r, _ in done)
     line = {"metric": "PCG solves/s", "value": len(done) / elapsed, "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic", "workload": "serve",
-            "config": {"arrivals": "Poisson 200/s, seed 1", "seconds_of_arrivals": args.serve_seconds,
+            "config": {"arrivals": "Poisson 200/s, seed 1" if scale == 1.0 else "Poisson 2000/s, seed 1",
+                       "mix": args.serve_mix, "seconds_of_arrivals": args.serve_seconds,
                        "requests": len(reqs), "budget_gb": 60, "max_slots": 256, "tol": 1e-8,
                        "mean_unknowns": unknowns / max(1, len(done))},
             "completed": len(done), "converged": ok, "elapsed_s": elapsed,
@@ -266,23 +275,34 @@ def run_serve(args, dev, pkg, W, torch):
                                     if st.relres_true < r.tol or st.relres_true <= 2.0 * st.relres_floor),
             "clocks": clocks}
     if args.serve_compare:
-        # the same requests one at a time, FP64 and mixed solver handles (creation included)
-        for prec in ("fp64", "mixed"):
+        # the same requests one at a time through pcg_solve_host (each request's
+        # b from host memory and x back to it, like a served request; solver
+        # creation included), FP64 and mixed; and mixed with b already on the device
+        arms = [("fp64", "host"), ("mixed", "host"), ("mixed", "device")]
+        for prec, where in arms:
             t = 0.0
             its = 0
             for r, bnp in zip(reqs, rhs_keep):
-                bt = torch.from_numpy(bnp.ravel()).to(dev)
-                x = torch.zeros_like(bt)
-                torch.cuda.synchronize(dev)
-                t1 = time.perf_counter()
-                with pkg.Solver(r.problem, precision=prec, stream=stream.cuda_stream) as s1:
-                    st = s1.solve(bt, x, tol=r.tol, maxit=200000)
-                torch.cuda.synchronize(dev)
-                t += time.perf_counter() - t1
+                if where == "host":
+                    bh = np.ascontiguousarray(bnp.ravel())
+                    xh = np.zeros_like(bh)
+                    t1 = time.perf_counter()
+                    with pkg.Solver(r.problem, precision=prec, stream=stream.cuda_stream) as s1:
+                        st = s1.solve_host(bh, xh, tol=r.tol, maxit=200000)
+                    t += time.perf_counter() - t1
+                else:
+                    bt = torch.from_numpy(bnp.ravel()).to(dev)
+                    x = torch.zeros_like(bt)
+                    torch.cuda.synchronize(dev)
+                    t1 = time.perf_counter()
+                    with pkg.Solver(r.problem, precision=prec, stream=stream.cuda_stream) as s1:
+                        st = s1.solve(bt, x, tol=r.tol, maxit=200000)
+                    torch.cuda.synchronize(dev)
+                    t += time.perf_counter() - t1
                 its += st.iterations
-            line[f"sequential_{prec}"] = {"solves_per_s": len(reqs) / t, "seconds": t, "iterations": its}
-        line["served_speedup_vs_sequential_fp64"] = line["value"] / line["sequential_fp64"]["solves_per_s"]
-        line["served_speedup_vs_sequential_mixed"] = line["value"] / line["sequential_mixed"]["solves_per_s"]
+            line[f"sequential_{prec}_{where}"] = {"solves_per_s": len(reqs) / t, "seconds": t, "iterations": its}
+        line["served_speedup_vs_sequential_fp64_host"] = line["value"] / line["sequential_fp64_host"]["solves_per_s"]
+        line["served_speedup_vs_sequential_mixed_host"] = line["value"] / line["sequential_mixed_host"]["solves_per_s"]
     print(json.dumps(line), flush=True)
 
 
@@ -389,6 +409,8 @@ def main():
                          "serve: Poisson request stream through the served batch; paper-panel: the paper's own "
                          "cubed-sphere panel problem, 256x256x128, residual reduced by 1e5")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: seconds of arrivals (200 req/s)")
+    ap.add_argument("--serve-mix", choices=["paper", "small"], default="paper",
+                    help="serve: the full request mix, or only requests of at most 128 x 128 x 64 at 10x the rate")
     ap.add_argument("--serve-compare", action="store_true",
                     help="serve: also solve the same requests one at a time with the FP64 and mixed solvers")
     ap.add_argument("--profile-sweeps", choices=["fp64", "mixed"], default=None,

@@ -18,7 +18,8 @@ discretisation  explicit CSR matrix of the finite-volume operator
                 in flux form (FluxOperator), which the solvers use.
 linesolve       vertical-line preconditioner M = block-diag(A) (Section 4.1),
                 solved with LAPACK's tridiagonal LU (GTTRF/GTTRS), the routines
-                of the paper's CPU code (Section 6.2).
+                of the paper's CPU code (Section 6.2); on the whole grid, or on
+                selected columns for sampled checks of very large grids.
 pcg             textbook left-preconditioned CG (Section 4.1) and the
                 interleaved loop of Algorithm 1 (Section 4.3).
 
@@ -28,11 +29,11 @@ dense direct solves, manufactured-solution convergence).
 """
 from .discretisation import (OperatorTerms, operator_terms, assemble_csr, apply_rows,
                              column_blocks, cell_volumes, FluxOperator)
-from .linesolve import LinePreconditioner
+from .linesolve import LinePreconditioner, apply_columns, solve_columns
 from .pcg import pcg_textbook, pcg_interleaved, PCGResult, rounding_floor
 
 __all__ = [
     "OperatorTerms", "operator_terms", "assemble_csr", "apply_rows", "column_blocks", "cell_volumes",
     "FluxOperator",
-    "LinePreconditioner", "pcg_textbook", "pcg_interleaved", "PCGResult", "rounding_floor",
+    "LinePreconditioner", "solve_columns", "apply_columns", "pcg_textbook", "pcg_interleaved", "PCGResult", "rounding_floor",
 ]

@@ -103,3 +103,87 @@ class LinePreconditioner:
 
     def __call__(self, r):
         return self.solve(r)
+
+
+def _column_flux(p: Problem, t, j: int, i: int):
+    """Flux form of column (j, i)'s block of A: s_k (zero-order term plus the
+    couplings to other columns) and W_k (coupling of level k to k+1, 0 at
+    the top), from the operator's rows restricted to the column."""
+    nx, ny, nz = p.n_x, p.n_y, p.n_z
+    k = np.arange(nz)
+    cl, vals = _row_entries(p, t, k, np.full(nz, j), np.full(nz, i))
+    own = j * nx + i
+    s = t.area[j, i] * t.mass
+    for f in range(1, 5):                           # horizontal neighbours in other columns
+        s = s + np.where((cl[f] % (nx * ny)) != own, -vals[f], 0.0)
+    return s, -vals[5]
+
+
+def _flux_apply(s, w, z):
+    f = w[:-1] * (z[:-1] - z[1:])
+    y = s * z
+    y[:-1] += f
+    y[1:] -= f
+    return y
+
+
+def solve_columns(p: Problem, r_cols: np.ndarray, cols) -> np.ndarray:
+    """z = M^{-1} r on selected columns only (Section 4.1: each column's
+    tridiagonal block A_T solved on its own), for sampled checks of very
+    large grids.
+
+    ``cols`` is a (2, m) array of (j, i); ``r_cols`` (m, n_z) holds r on
+    those columns.  Each block is taken in flux form (``_column_flux``),
+    factored with LAPACK's GTTRF and applied with GTTRS, plus one refinement
+    step with the flux-form residual, exactly as ``LinePreconditioner`` does
+    for the whole grid.
+    """
+    t = operator_terms(p)
+    nz = p.n_z
+    jj, ii = (np.asarray(c, dtype=np.int64) for c in cols)
+    r_cols = np.asarray(r_cols, dtype=np.float64).reshape(len(jj), nz)
+    out = np.empty_like(r_cols)
+    for c in range(len(jj)):
+        s, w = _column_flux(p, t, int(jj[c]), int(ii[c]))
+        wd = np.concatenate([[0.0], w[:-1]])        # coupling k -> k-1
+        main = s + w + wd
+        rc = r_cols[c]
+        if nz == 1:
+            out[c] = rc / main
+            continue
+        off = -w[:-1]
+        dl, d, du, du2, ipiv, info = lapack.dgttrf(off.copy(), main.copy(), off.copy())
+        if info != 0:
+            raise np.linalg.LinAlgError(f"dgttrf failed, info={info}")
+
+        def lu_solve(b):
+            x, inf = lapack.dgttrs(dl, d, du, du2, ipiv, b)
+            if inf != 0:
+                raise np.linalg.LinAlgError(f"dgttrs failed, info={inf}")
+            return x
+
+        x = lu_solve(rc)
+        x = x + lu_solve(rc - _flux_apply(s, w, x))
+        out[c] = x
+    return out
+
+
+def apply_columns(p: Problem, z_cols: np.ndarray, cols):
+    """M z on selected columns, in flux form, and the scale sum |terms| of
+    every row (for backward-error bounds): two (m, n_z) arrays."""
+    t = operator_terms(p)
+    nz = p.n_z
+    jj, ii = (np.asarray(c, dtype=np.int64) for c in cols)
+    z_cols = np.asarray(z_cols, dtype=np.float64).reshape(len(jj), nz)
+    mz = np.empty_like(z_cols)
+    scale = np.empty_like(z_cols)
+    for c in range(len(jj)):
+        s, w = _column_flux(p, t, int(jj[c]), int(ii[c]))
+        z = z_cols[c]
+        mz[c] = _flux_apply(s, w, z)
+        af = np.abs(w[:-1] * (z[:-1] - z[1:]))
+        sc = np.abs(s * z)
+        sc[:-1] += af
+        sc[1:] += af
+        scale[c] = sc
+    return mz, scale

@@ -95,6 +95,7 @@ template <typename T> struct Acc;
 template <> struct Acc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ void add(double a) { s += a; }
     __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct Acc<float> {
@@ -107,6 +108,13 @@ template <> struct Acc<float> {
         float e = (s - (t - bp)) + (p - bp);
         s = t;
         c += e + pe;
+    }
+    // add an exact-enough partial sum (TwoSum, error kept in c)
+    __device__ __forceinline__ void add(float a) {
+        const float t = s + a;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (a - bp);
+        s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
@@ -435,7 +443,7 @@ __global__ __launch_bounds__(NT) void k_precond(OpView<T> op, const T* __restric
 // ---------------------------------------------------------------------------
 // One column of the preconditioner sweep; r, q, z point at the column's
 // level-0 entry.
-template <typename T>
+template <typename T, bool PIPE = false>
 __device__ __forceinline__ void prec_column(const OpView<T>& op, const Col<T>& col, T* __restrict__ rb,
                                             const T* __restrict__ qb, T* __restrict__ zb, T alpha, Acc<T>& rr,
                                             Acc<T>& kap) {
@@ -449,26 +457,96 @@ __device__ __forceinline__ void prec_column(const OpView<T>& op, const Col<T>& c
         // c_k is one rounding of the exact ratio, so the excess 1 - c_k keeps a
         // relative accuracy of 2^-53 / (1 - c_k), ample in FP64 (the FP32
         // sweeps below cannot afford it and carry E_k instead).
-        const T* fc = op.fc + col.cls;
-        T y = T(0), cprev = T(0);
-#pragma unroll 4
-        for (int k = 0; k < op.nz; ++k) {
-            const long long o = (long long)k * op.plane;
-            const T rn = fma(-alpha, qb[o], rb[o]);
-            rb[o] = rn;
-            rr.add_prod(rn, rn);
-            y = fma(cprev, y, rn);
-            const T t = ldro(fg + k * fs) * y;
-            kap.add_prod(t, y);
-            zb[o] = t;
-            cprev = ldro(fc + k * fs);
-        }
-        T zn = T(0);
-#pragma unroll 4
-        for (int k = op.nz - 1; k >= 0; --k) {
-            const long long o = (long long)k * op.plane;
-            zn = fma(ldro(fc + k * fs), zn, zb[o]);
-            zb[o] = zn;
+        if constexpr (!PIPE) {
+            const T* fc = op.fc + col.cls;
+            T y = T(0), cprev = T(0);
+    #pragma unroll 4
+            for (int k = 0; k < op.nz; ++k) {
+                const long long o = (long long)k * op.plane;
+                const T rn = fma(-alpha, qb[o], rb[o]);
+                rb[o] = rn;
+                rr.add_prod(rn, rn);
+                y = fma(cprev, y, rn);
+                const T t = ldro(fg + k * fs) * y;
+                kap.add_prod(t, y);
+                zb[o] = t;
+                cprev = ldro(fc + k * fs);
+            }
+            T zn = T(0);
+    #pragma unroll 4
+            for (int k = op.nz - 1; k >= 0; --k) {
+                const long long o = (long long)k * op.plane;
+                zn = fma(ldro(fc + k * fs), zn, zb[o]);
+                zb[o] = zn;
+            }
+        } else {
+            // The loads of the next PB levels are issued before the current PB
+            // levels are computed and stored (the stores go to the same arrays,
+            // so the compiler cannot hoist the loads over them by itself).
+            constexpr int PB = 8;
+            const T* fc = op.fc + col.cls;
+            const long long pl = op.plane;
+            const int nz = op.nz;
+            T y = T(0), cprev = T(0);
+            T ra[PB], qa[PB];
+    #pragma unroll
+            for (int t = 0; t < PB; ++t) {
+                ra[t] = t < nz ? rb[t * pl] : T(0);
+                qa[t] = t < nz ? qb[t * pl] : T(0);
+            }
+            for (int k0 = 0; k0 < nz; k0 += PB) {
+                T rn_[PB], qn_[PB];
+    #pragma unroll
+                for (int t = 0; t < PB; ++t) {
+                    const int k = k0 + PB + t;
+                    rn_[t] = k < nz ? rb[k * pl] : T(0);
+                    qn_[t] = k < nz ? qb[k * pl] : T(0);
+                }
+    #pragma unroll
+                for (int t = 0; t < PB; ++t) {
+                    const int k = k0 + t;
+                    if (k < nz) {
+                        const T rn = fma(-alpha, qa[t], ra[t]);
+                        rb[k * pl] = rn;
+                        rr.add_prod(rn, rn);
+                        y = fma(cprev, y, rn);
+                        const T tk = ldro(fg + k * fs) * y;
+                        kap.add_prod(tk, y);
+                        zb[k * pl] = tk;
+                        cprev = ldro(fc + k * fs);
+                    }
+                }
+    #pragma unroll
+                for (int t = 0; t < PB; ++t) {
+                    ra[t] = rn_[t];
+                    qa[t] = qn_[t];
+                }
+            }
+            // backward: z_k = t_k + c_k z_{k+1}, with the t of the next PB levels
+            // (below) loaded before the current ones are overwritten
+            T zn = T(0);
+            T ta[PB];
+            const int kt = nz - 1;
+    #pragma unroll
+            for (int t = 0; t < PB; ++t) ta[t] = kt - t >= 0 ? zb[(kt - t) * pl] : T(0);
+            for (int k0 = kt; k0 >= 0; k0 -= PB) {
+                T tn[PB];
+    #pragma unroll
+                for (int t = 0; t < PB; ++t) {
+                    const int k = k0 - PB - t;
+                    tn[t] = k >= 0 ? zb[k * pl] : T(0);
+                }
+    #pragma unroll
+                for (int t = 0; t < PB; ++t) {
+                    const int k = k0 - t;
+                    if (k >= 0) {
+                        zn = fma(ldro(fc + k * fs), zn, ta[t]);
+                        zb[k * pl] = zn;
+                    }
+                }
+    #pragma unroll
+                for (int t = 0; t < PB; ++t) ta[t] = tn[t];
+            }
         }
     } else {
         const T* fe = op.fe + col.cls;
@@ -495,7 +573,9 @@ __device__ __forceinline__ void prec_column(const OpView<T>& op, const Col<T>& c
     }
 }
 
-template <typename T>
+// PIPE: FP64 Thomas with the next levels' loads issued ahead (for grids with
+// few columns, where occupancy cannot hide the load latency)
+template <typename T, bool PIPE = false>
 __global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__ r, const T* __restrict__ q,
                                                    T* __restrict__ z, SolveState* __restrict__ states,
                                                    double* __restrict__ partials, unsigned* __restrict__ counters,
@@ -508,7 +588,7 @@ __global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__
     Acc<T> acc[2];
     if (col.valid) {
         const long long base = (long long)rhs * op.vol + col.c;
-        prec_column<T>(op, col, r + base, q + base, z + base, alpha, acc[0], acc[1]);
+        prec_column<T, PIPE>(op, col, r + base, q + base, z + base, alpha, acc[0], acc[1]);
     }
     double v[2];
     if (grid_sum_acc<2>(acc, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
@@ -522,24 +602,25 @@ __global__ __launch_bounds__(NT) void k_sweep_prec(OpView<T> op, T* __restrict__
 // One column of the SpMV sweep; u, p, q point at the column's level-0
 // entry, zb at level 0 of the right-hand side's z (the stencil reads
 // neighbouring columns).
-template <typename T, bool FOLD = false>
+template <typename T, bool FOLD = false, bool PIPE = false>
 __device__ __forceinline__ void spmv_column(const OpView<T>& op, const Col<T>& col, T* __restrict__ ub,
                                             T* __restrict__ pb, T* __restrict__ qb, const T* __restrict__ zb,
-                                            T alpha, T beta, Acc<T>& sig) {
+                                            T alpha, T beta, Acc<T>& sig, int k0 = 0, int k1 = -1) {
     // FOLD: the area is folded into the level tables (|T| a_k, |T| w_k per
-    // row), one multiplication fewer per unknown for uniform or per-row areas
+    // row), one multiplication fewer per unknown for uniform or per-row areas.
+    // Levels k0 .. k1-1 (default all); the flux into level k0 from below is
+    // recomputed from z at k0-1.
+    if (k1 < 0) k1 = op.nz;
     const T* am = FOLD ? op.amass + (op.arow_step ? (long long)col.j * op.nz : 0LL) : op.mass;
     const T* aw = FOLD ? op.awv + (op.arow_step ? (long long)col.j * op.nz : 0LL) : op.wv;
-    T zc = zb[col.c];
-    T fprev = T(0);
-#pragma unroll 4
-    for (int k = 0; k < op.nz; ++k) {
+    T zc = zb[(long long)k0 * op.plane + col.c];
+    T fprev = k0 > 0 ? ldro(aw + k0 - 1) * (zb[(long long)(k0 - 1) * op.plane + col.c] - zc) : T(0);
+    // one level: uk, pk, qk are the loaded u, p, q at level k
+    auto level = [&](int k, T uk, T pk, T qk) {
         const long long o = (long long)k * op.plane;
         const T* zl = zb + o;
         const T zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
-        const T pk = pb[o];
-        const T qk = qb[o];
-        ub[o] = fma(alpha, pk, ub[o]);
+        ub[o] = fma(alpha, pk, uk);
         const T pn = fma(beta, pk, zc);
         pb[o] = pn;
         const T f = ldro(aw + k) * (zc - zu);
@@ -551,15 +632,59 @@ __device__ __forceinline__ void spmv_column(const OpView<T>& op, const Col<T>& c
         sig.add_prod(pn, qn);
         fprev = f;
         zc = zu;
+    };
+    if constexpr (!PIPE) {
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            const long long o = (long long)k * op.plane;
+            level(k, ub[o], pb[o], qb[o]);
+        }
+    } else {
+        // u, p, q of the next PB levels are loaded before the current PB levels
+        // are stored (same arrays: the compiler cannot reorder them itself)
+        constexpr int PB = 4;
+        const long long pl = op.plane;
+        T ua[PB], pa[PB], qa[PB];
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            const int k = k0 + t;
+            ua[t] = k < k1 ? ub[k * pl] : T(0);
+            pa[t] = k < k1 ? pb[k * pl] : T(0);
+            qa[t] = k < k1 ? qb[k * pl] : T(0);
+        }
+        for (int kb = k0; kb < k1; kb += PB) {
+            T un[PB], pn[PB], qn[PB];
+#pragma unroll
+            for (int t = 0; t < PB; ++t) {
+                const int k = kb + PB + t;
+                un[t] = k < k1 ? ub[k * pl] : T(0);
+                pn[t] = k < k1 ? pb[k * pl] : T(0);
+                qn[t] = k < k1 ? qb[k * pl] : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < PB; ++t)
+                if (kb + t < k1) level(kb + t, ua[t], pa[t], qa[t]);
+#pragma unroll
+            for (int t = 0; t < PB; ++t) {
+                ua[t] = un[t];
+                pa[t] = pn[t];
+                qa[t] = qn[t];
+            }
+        }
     }
 }
 
-template <typename T>
+// blockIdx.z = rhs * ksplit + part: part takes levels [part n_z / ksplit,
+// (part + 1) n_z / ksplit) of every column of the tile (more, shorter threads
+// that spread evenly over the SMs).
+template <typename T, bool PIPE = false>
 __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__ u, T* __restrict__ p,
                                                    T* __restrict__ q, const T* __restrict__ z,
                                                    SolveState* __restrict__ states, double* __restrict__ partials,
-                                                   unsigned* __restrict__ counters, int nblocks) {
-    const int rhs = blockIdx.z;
+                                                   unsigned* __restrict__ counters, int nblocks, int ksplit = 1) {
+    const int rhs = blockIdx.z / ksplit;
+    const int part = blockIdx.z - rhs * ksplit;
+    const int k0 = (int)((long long)part * op.nz / ksplit), k1 = (int)((long long)(part + 1) * op.nz / ksplit);
     SolveState* st = states + rhs;
     if (st->done) return;
     const T alpha = (T)st->alpha;
@@ -569,14 +694,15 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
     if (col.valid) {
         const long long base = (long long)rhs * op.vol;
         if (sizeof(T) == 8 && op.amass)
-            spmv_column<T, true>(op, col, u + base + col.c, p + base + col.c, q + base + col.c, z + base, alpha, beta,
-                                 sig[0]);
+            spmv_column<T, true, PIPE>(op, col, u + base + col.c, p + base + col.c, q + base + col.c, z + base, alpha,
+                                       beta, sig[0], k0, k1);
         else
-            spmv_column<T, false>(op, col, u + base + col.c, p + base + col.c, q + base + col.c, z + base, alpha, beta,
-                                  sig[0]);
+            spmv_column<T, false, PIPE>(op, col, u + base + col.c, p + base + col.c, q + base + col.c, z + base, alpha,
+                                        beta, sig[0], k0, k1);
     }
     double v[1];
-    if (grid_sum_acc<1>(sig, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
+    const int bid = (part * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (grid_sum_acc<1>(sig, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid, v))
         spmv_epilogue(st, v[0]);
 }
 
@@ -655,22 +781,27 @@ __device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col
         }
     }
     const T e_in = (act && k0 > 0) ? ldro(fe - fs) * ldro(fg - fs) : T(0);
-    // updated residual, ||r||^2, local forward sweep with zero carry-in
+    // updated residual, ||r||^2, local forward sweep with zero carry-in.
+    // ||r||^2 and kappa are sums of non-negative terms: each chunk sums its
+    // LZ terms directly (relative error <= (LZ - 1) u) and adds the chunk sum
+    // to the compensated accumulator once.
     T yl = T(0), cp = T(0);
     if (act) {
         T ep = e_in;
+        T rr_chunk = T(0);
 #pragma unroll
         for (int t = 0; t < LZ; ++t) {
             if (t < kn) {
                 const T rn = yv[t];
                 rb[t * pl] = rn;
-                acc[0].add_prod(rn, rn);
+                rr_chunk = fma(rn, rn, rr_chunk);
                 yl = fma(-ep, yl, rn) + yl;
                 cp = (t == 0) ? ep : fma(ep, T(1) - cp, cp);
                 yv[t] = yl;
                 ep = ev[t] * gv[t];
             }
         }
+        acc[0].add(rr_chunk);
     }
     sh_y[w0 + ch][lane] = yl;
     sh_c[w0 + ch][lane] = cp;
@@ -682,16 +813,18 @@ __device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col
     if (act) {
         T ep = e_in;
         cp = T(0);
+        T kap_chunk = T(0);
 #pragma unroll
         for (int t = 0; t < LZ; ++t) {
             if (t < kn) {
                 cp = (t == 0) ? ep : fma(ep, T(1) - cp, cp);
                 const T y = fma(-cp, Y, yv[t]) + Y;
                 yv[t] = y;
-                acc[1].add_prod(gv[t] * y, y);
+                kap_chunk = fma(gv[t] * y, y, kap_chunk);
                 ep = ev[t] * gv[t];
             }
         }
+        acc[1].add(kap_chunk);
         bool first = true;
 #pragma unroll
         for (int t = LZ - 1; t >= 0; --t) {
@@ -1044,6 +1177,97 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma(
 }
 
 // ---------------------------------------------------------------------------
+// The same SpMV sweep as a persistent two-stage pipeline: blockIdx.y = right-
+// hand side; a block walks the (tile, chunk) items i = blockIdx.x, +gridDim.x,
+// ... and keeps the copies of its next item in flight (second stage, second
+// mbarrier) while it computes the current one.
+// ---------------------------------------------------------------------------
+template <int LZ, int BYT>
+__global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
+    OpView<float> op, const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
+    const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_z, float* __restrict__ u,
+    float* __restrict__ p, float* __restrict__ q, const float* __restrict__ z, SolveState* __restrict__ states,
+    double* __restrict__ partials, unsigned* __restrict__ counters, int gx, int gy, int nchunks) {
+    using TT = SpmvTmaTile<LZ, BYT>;
+    constexpr int STAGE = TT::ZN + 3 * TT::VN;          // floats per stage (a multiple of 32)
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* sbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 2 * STAGE);
+    const int rhs = blockIdx.y;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int nitems = gx * gy * nchunks;
+    const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
+    if (tid == 0) {
+        mbar_init(bar0);
+        mbar_init(bar1);
+    }
+    __syncthreads();
+    auto issue = [&](int item, int stage) {
+        const int ch = item % nchunks, tile = item / nchunks;
+        const int i0 = (tile % gx) * BX, j0 = (tile / gx) * BYT, lev0 = rhs * op.nz + ch * LZ;
+        float* zs = sbase + stage * STAGE;
+        const uint32_t bar = stage ? bar1 : bar0;
+        mbar_expect(bar, TT::BYTES);
+        tma_load_3d(smem_u32(zs), &tm_z, i0 - TMA_HALO_X, j0 - 1, lev0 - 1, bar);
+        tma_load_3d(smem_u32(zs + TT::ZN), &tm_u, i0, j0, lev0, bar);
+        tma_load_3d(smem_u32(zs + TT::ZN + TT::VN), &tm_p, i0, j0, lev0, bar);
+        tma_load_3d(smem_u32(zs + TT::ZN + 2 * TT::VN), &tm_q, i0, j0, lev0, bar);
+    };
+    if (tid == 0) {
+        if ((int)blockIdx.x < nitems) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < nitems) issue(blockIdx.x + gridDim.x, 1);
+    }
+    const float alpha = (float)st->alpha;
+    const float beta = (float)st->beta;
+    const long long base = (long long)rhs * op.vol;
+    Acc<float> sig[1];
+    uint32_t par0 = 0, par1 = 0;
+    bool ok = true;                 // false once a stage failed to land in time
+    int n = 0;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++n) {
+        const int stage = n & 1;
+        bool landed = false;
+        if (ok) landed = mbar_wait(stage ? bar1 : bar0, stage ? par1 : par0, 1 << 22);
+        landed = __syncthreads_and(landed ? 1 : 0) != 0;
+        if (landed) {
+            if (stage) par1 ^= 1u; else par0 ^= 1u;
+        }
+        if (ok && !landed) {
+            if (tid == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT
+            ok = false;
+        }
+        if (ok) {
+            const int ch = item % nchunks, tile = item / nchunks;
+            const int i0 = (tile % gx) * BX, j0 = (tile / gx) * BYT, k0 = ch * LZ;
+            const int kn = min(LZ, op.nz - k0);
+            const Col<float> col = make_col(op, i0 + tx, j0 + ty);
+            if (col.valid && kn > 0) {
+                const bool in_e = col.ce == col.c + 1, in_w = col.cw == col.c - 1;
+                const bool in_n = col.cn == col.c + op.nx, in_s = col.cs == col.c - op.nx;
+                const float* zs = sbase + stage * STAGE;
+                spmv_tile_compute<LZ, BYT>(op, col, tx, ty, k0, kn, zs, zs + TT::ZN, zs + TT::ZN + TT::VN,
+                                           zs + TT::ZN + 2 * TT::VN, z + base, u + base, p + base, q + base, alpha,
+                                           beta, in_e, in_w, in_n, in_s, sig[0]);
+            }
+        }
+        __syncthreads();            // the stage has been read: refill it
+        if (tid == 0 && ok && item + 2 * (int)gridDim.x < nitems) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(item + 2 * gridDim.x, stage);
+        }
+    }
+    if (!ok) {
+        mbar_wait(bar0, par0, 1 << 22);
+        mbar_wait(bar1, par1, 1 << 22);
+    }
+    double v[1];
+    if (grid_sum_acc<1>(sig, partials + (long long)rhs * gridDim.x * 2, counters + rhs, gridDim.x, blockIdx.x, v))
+        spmv_epilogue(st, v[0]);
+}
+
+// ---------------------------------------------------------------------------
 // FP32 preconditioner sweep on a TMA pipeline: the chunked solve of
 // prec_chunked_body on tiles staged in shared memory.
 //
@@ -1144,12 +1368,12 @@ __global__ __launch_bounds__(256, 2) void k_sweep_prec_tma(
 //     each column split into nch chunks of 16 levels (one warp per chunk,
 //     prec_chunked_body); columns of more than 128 levels take one thread
 //     per column (8 rows per item, prec_column).
-//   k_serve_spmv: 256-thread blocks; an item is a 32 x 8-column tile of one
+//   k_serve_spmv: 128-thread blocks; an item is a 32 x 4-column tile of one
 //     16-level chunk, staged in shared memory by bulk tensor copies (tensor
 //     maps of the request in device memory) or, when the request's rows are
 //     not 16-byte multiples, by the threads; then spmv_tile_compute.
 // ---------------------------------------------------------------------------
-constexpr int SERVE_LZ = 16, SERVE_BY = 8;
+constexpr int SERVE_LZ = 16, SERVE_BY = 4;
 
 struct ServeSlot {
     OpView<float> op;           // FP32 tables of the request
@@ -1204,7 +1428,8 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
-__global__ __launch_bounds__(256) void k_serve_spmv(const ServeSlot* __restrict__ slots, const int2* __restrict__ items,
+__global__ __launch_bounds__(BX * SERVE_BY) void k_serve_spmv(const ServeSlot* __restrict__ slots,
+                                                             const int2* __restrict__ items,
                                                     const int* __restrict__ n_items) {
     using TT = SpmvTmaTile<SERVE_LZ, SERVE_BY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1257,13 +1482,14 @@ __global__ __launch_bounds__(256) void k_serve_spmv(const ServeSlot* __restrict_
                 parity ^= 1u;
             } else {
                 // staged by the threads, cells outside the grid as zeros
-                for (int e = tid; e < TT::ZN; e += 256) {
+                constexpr int NTH = BX * SERVE_BY;
+                for (int e = tid; e < TT::ZN; e += NTH) {
                     const int xx = e % TT::ZX, yy = (e / TT::ZX) % TT::ZY, zz = e / (TT::ZX * TT::ZY);
                     const int gi = i0 - TMA_HALO_X + xx, gj = j0 - 1 + yy, gk = k0 - 1 + zz;
                     const bool in = gi >= 0 && gi < op.nx && gj >= 0 && gj < op.ny && gk >= 0 && gk < op.nz;
                     zs[e] = in ? ldro(s.z + (long long)gk * op.plane + (long long)gj * op.nx + gi) : 0.f;
                 }
-                for (int e = tid; e < TT::VN; e += 256) {
+                for (int e = tid; e < TT::VN; e += NTH) {
                     const int xx = e % BX, yy = (e / BX) % SERVE_BY, zz = e / (BX * SERVE_BY);
                     const int gi = i0 + xx, gj = j0 + yy, gk = k0 + zz;
                     const bool in = gi < op.nx && gj < op.ny && gk < op.nz;

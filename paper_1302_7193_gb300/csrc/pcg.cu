@@ -69,8 +69,13 @@ struct pcg_ctx {
     // tensor maps of the FP32 u, p, q (own tile) and z (tile with halo) for the TMA SpMV sweep
     CUtensorMap tm_u, tm_p, tm_q, tm_z;
     bool tma_ready = false;
+    int tma_by = 4;                       // rows of the TMA SpMV tile (4; PCG_TMA_BY=8 for 8)
     // ... and of r, q for the TMA preconditioner sweep (box 32 x prec_R x nch * lz_a)
     CUtensorMap tm_pr, tm_pq;
+    // ... and of u, p, q, z for the pipelined TMA SpMV sweep (8-level chunks)
+    CUtensorMap tm2_u, tm2_p, tm2_q, tm2_z;
+    bool tma2_ready = false;
+    int spmv2_G = 1, spmv2_nch = 1;
     int prec32 = 0;                       // FP32 preconditioner sweep: 0 column/chunked, 2 TMA pipeline
     bool prec_tma_ready = false;
     int prec_R = 1, prec_gx = 1, prec_items = 0, prec_G = 1;
@@ -96,6 +101,8 @@ struct pcg_ctx {
     int nblk_a = 0, nblk_b = 0;
     dim3 grid_c, block_c;                 // one-thread-per-column sweeps: 32 x by column tiles
     int nblk_c = 0;
+    int ksplit = 1;                       // one-thread-per-column SpMV sweep: parts of each column
+    int spmv_pipe = 1;                    // FP64 SpMV sweep with u, p, q loads issued ahead (PCG_SPMV_PIPE=0: plain)
 
     cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -395,6 +402,9 @@ bool encode_map(pcg_t h, CUtensorMap* m, float* base, unsigned bx, unsigned by, 
 
 constexpr int TMA_LZ = 16, TMA_BY = 8;
 using SpmvTile = pcg::SpmvTmaTile<TMA_LZ, TMA_BY>;
+constexpr int TMA2_LZ = 8;
+using SpmvTile2 = pcg::SpmvTmaTile<TMA2_LZ, TMA_BY>;
+constexpr size_t SPMV2_SMEM = 2 * ((size_t)SpmvTile2::ZN + 3 * SpmvTile2::VN) * 4 + 16 + 128;
 
 int ensure_ws32(pcg_t h) {
     if (h->u32) return PCG_OK;
@@ -405,14 +415,39 @@ int ensure_ws32(pcg_t h) {
         // the TMA SpMV sweep: maps of the workspace vectors; fall back to the
         // chunked sweep when the driver cannot encode them
         const unsigned zx = BX + 2 * pcg::TMA_HALO_X;
-        h->tma_ready = encode_map(h, &h->tm_u, h->u32, BX, TMA_BY, TMA_LZ) &&
-                       encode_map(h, &h->tm_p, h->p32, BX, TMA_BY, TMA_LZ) &&
-                       encode_map(h, &h->tm_q, h->q32, BX, TMA_BY, TMA_LZ) &&
-                       encode_map(h, &h->tm_z, h->z32, zx, TMA_BY + 2, TMA_LZ + 2) &&
-                       cudaFuncSetAttribute(pcg::k_sweep_spmv_tma<TMA_LZ, TMA_BY>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)SpmvTile::SMEM) == cudaSuccess;
+        const unsigned by = (unsigned)h->tma_by;
+        h->tma_ready = encode_map(h, &h->tm_u, h->u32, BX, by, TMA_LZ) &&
+                       encode_map(h, &h->tm_p, h->p32, BX, by, TMA_LZ) &&
+                       encode_map(h, &h->tm_q, h->q32, BX, by, TMA_LZ) &&
+                       encode_map(h, &h->tm_z, h->z32, zx, by + 2, TMA_LZ + 2) &&
+                       (h->tma_by == 4
+                            ? cudaFuncSetAttribute(pcg::k_sweep_spmv_tma<TMA_LZ, 4>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)pcg::SpmvTmaTile<TMA_LZ, 4>::SMEM)
+                            : cudaFuncSetAttribute(pcg::k_sweep_spmv_tma<TMA_LZ, TMA_BY>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)SpmvTile::SMEM)) == cudaSuccess;
         if (!h->tma_ready) h->spmv32 = (h->chunked32 && h->plane * (long long)h->nrhs < (1LL << 19)) ? 1 : 0;
+    }
+    if (h->spmv32 == 4) {
+        const unsigned zx = BX + 2 * pcg::TMA_HALO_X;
+        int occ = 0, dev = 0, sms = 1;
+        cudaError_t ea = cudaFuncSetAttribute(pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA_BY>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPMV2_SMEM);
+        if (ea == cudaSuccess)
+            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA_BY>,
+                                                               BX * TMA_BY, SPMV2_SMEM);
+        if (ea == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        h->spmv2_nch = (h->nz + TMA2_LZ - 1) / TMA2_LZ;
+        const int nitems = h->grid_t.x * h->grid_t.y * h->spmv2_nch;
+        h->spmv2_G = std::max(1, std::min(nitems, sms * std::max(occ, 1)));
+        h->tma2_ready = ea == cudaSuccess && occ >= 1 && h->tma_by == TMA_BY &&
+                        encode_map(h, &h->tm2_u, h->u32, BX, TMA_BY, TMA2_LZ) &&
+                        encode_map(h, &h->tm2_p, h->p32, BX, TMA_BY, TMA2_LZ) &&
+                        encode_map(h, &h->tm2_q, h->q32, BX, TMA_BY, TMA2_LZ) &&
+                        encode_map(h, &h->tm2_z, h->z32, zx, TMA_BY + 2, TMA2_LZ + 2);
+        if (!h->tma2_ready) h->spmv32 = (h->chunked32 && h->plane * (long long)h->nrhs < (1LL << 19)) ? 1 : 0;
     }
     if (h->prec32 == 2) {
         const unsigned lev = (unsigned)(((h->nz + h->lz_a - 1) / h->lz_a) * h->lz_a);
@@ -464,7 +499,15 @@ void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, 
     } else if (chunked) {
         PCG_PREC_CH(32, 1);
     } else {
-        pcg::k_sweep_prec<T><<<h->grid_c, h->block_c, 0, s>>>(v, r, q, z, st, h->partials, h->counters, h->nblk_c);
+        // loads issued ahead while the grid has few columns (65536 columns:
+        // 155 -> 113 us per sweep); plain loop beyond (2^20 columns: 1505 vs
+        // 1634 us, where the extra registers cost more occupancy than they gain)
+        if (sizeof(T) == 8 && h->plane * (long long)h->nrhs < (1LL << 19))
+            pcg::k_sweep_prec<T, true><<<h->grid_c, h->block_c, 0, s>>>(v, r, q, z, st, h->partials, h->counters,
+                                                                         h->nblk_c);
+        else
+            pcg::k_sweep_prec<T, false><<<h->grid_c, h->block_c, 0, s>>>(v, r, q, z, st, h->partials, h->counters,
+                                                                          h->nblk_c);
     }
 #undef PCG_PREC_CH
 }
@@ -476,22 +519,40 @@ void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, 
     pcg::k_sweep_spmv_chunked<T, LZ, TILE, MB><<<h->grid_b, h->block_b, 0, s>>>(v, u, p, q, z, st, h->partials,  \
                                                                                 h->counters, h->nblk_b, h->nch_b)
     if constexpr (sizeof(T) == 4) {
+        if (mode == 4 && h->tma2_ready && u == h->u32 && p == h->p32 && q == h->q32 && z == h->z32) {
+            pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA_BY><<<dim3(h->spmv2_G, h->nrhs, 1), h->block_t, SPMV2_SMEM, s>>>(
+                v, h->tm2_u, h->tm2_p, h->tm2_q, h->tm2_z, u, p, q, z, st, h->partials, h->counters, h->grid_t.x,
+                h->grid_t.y, h->spmv2_nch);
+            return;
+        }
         if (mode == 3 && h->tma_ready && u == h->u32 && p == h->p32 && q == h->q32 && z == h->z32) {
-            pcg::k_sweep_spmv_tma<TMA_LZ, TMA_BY><<<h->grid_t, h->block_t, SpmvTile::SMEM, s>>>(
-                v, h->tm_u, h->tm_p, h->tm_q, h->tm_z, u, p, q, z, st, h->partials, h->counters, h->nblk_t, h->nch_b);
+            if (h->tma_by == 4)
+                pcg::k_sweep_spmv_tma<TMA_LZ, 4><<<h->grid_t, h->block_t, pcg::SpmvTmaTile<TMA_LZ, 4>::SMEM, s>>>(
+                    v, h->tm_u, h->tm_p, h->tm_q, h->tm_z, u, p, q, z, st, h->partials, h->counters, h->nblk_t,
+                    h->nch_b);
+            else
+                pcg::k_sweep_spmv_tma<TMA_LZ, TMA_BY><<<h->grid_t, h->block_t, SpmvTile::SMEM, s>>>(
+                    v, h->tm_u, h->tm_p, h->tm_q, h->tm_z, u, p, q, z, st, h->partials, h->counters, h->nblk_t,
+                    h->nch_b);
             return;
         }
     }
     if (mode == 2) {
         PCG_SPMV_CH(16, true, 1);
-    } else if ((mode == 1 || mode == 3) && h->lz_b == 8) {
+    } else if ((mode == 1 || mode >= 3) && h->lz_b == 8) {
         if (h->spmv_minb == 8) PCG_SPMV_CH(8, false, 8);
         else PCG_SPMV_CH(8, false, 1);
-    } else if (mode == 1 || mode == 3) {
+    } else if (mode == 1 || mode >= 3) {
         if (h->spmv_minb == 6) PCG_SPMV_CH(16, false, 6);
         else PCG_SPMV_CH(16, false, 1);
     } else {
-        pcg::k_sweep_spmv<T><<<h->grid_c, h->block_c, 0, s>>>(v, u, p, q, z, st, h->partials, h->counters, h->nblk_c);
+        const dim3 g(h->grid_c.x, h->grid_c.y, h->grid_c.z * h->ksplit);
+        if (sizeof(T) == 8 && h->spmv_pipe)
+            pcg::k_sweep_spmv<T, true><<<g, h->block_c, 0, s>>>(v, u, p, q, z, st, h->partials, h->counters,
+                                                                h->nblk_c * h->ksplit, h->ksplit);
+        else
+            pcg::k_sweep_spmv<T, false><<<g, h->block_c, 0, s>>>(v, u, p, q, z, st, h->partials, h->counters,
+                                                                 h->nblk_c * h->ksplit, h->ksplit);
     }
 #undef PCG_SPMV_CH
 }
@@ -787,6 +848,17 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
             if (v == 1 || v == 2 || v == 4) by = v;
         }
         h->block_c = dim3(BX, by, 1);
+        // PCG_SPMV_KSPLIT=2 splits every column of the SpMV sweep in two parts
+        // (twice the threads); measured 5 % slower at 256^2 x 128 and no faster
+        // elsewhere, so one part is the default.
+        h->ksplit = 1;
+        // u, p, q of the next 4 levels loaded before the current ones are stored:
+        // 295.6 -> 288.9 us at 256^2 x 128, 4231 -> 4058 us at 1024^2 x 128
+        if (const char* e = std::getenv("PCG_SPMV_PIPE")) h->spmv_pipe = std::atoi(e) ? 1 : 0;   // experiments
+        if (const char* e = std::getenv("PCG_SPMV_KSPLIT")) {  // experiments: 1 or 2
+            const int v = std::atoi(e);
+            if (v == 1 || (v == 2 && h->nz >= 2 && (long long)h->nrhs * 2 <= 65535)) h->ksplit = v;
+        }
         h->grid_c = dim3((h->nx + BX - 1) / BX, (h->ny + by - 1) / by, h->nrhs);
         h->nblk_c = (int)(h->grid_c.x * h->grid_c.y);
     }
@@ -824,8 +896,12 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->spmv64 = h->chunked64 ? 1 : 0;
     // TMA-staged FP32 SpMV sweep (k_sweep_spmv_tma): tiles of 32 x 8 columns x
     // 16 levels; the tensor maps need rows of a multiple of 16 bytes (n_x % 4 == 0)
-    h->block_t = dim3(BX, TMA_BY, 1);
-    h->grid_t = dim3((h->nx + BX - 1) / BX, (h->ny + TMA_BY - 1) / TMA_BY, h->nrhs * h->nch_b);
+    // TMA SpMV tiles of 32 x 4 columns (5 blocks of 42 KB per SM): 65.3 us at
+    // 256^2 x 128 and 848 us at 1024^2 x 128, against 71.4 and 908 us for
+    // 32 x 8 tiles (2 blocks of 78 KB per SM)
+    if (const char* e = std::getenv("PCG_TMA_BY")) h->tma_by = std::atoi(e) == 8 ? 8 : 4;   // experiments
+    h->block_t = dim3(BX, h->tma_by, 1);
+    h->grid_t = dim3((h->nx + BX - 1) / BX, (h->ny + h->tma_by - 1) / h->tma_by, h->nrhs * h->nch_b);
     h->nblk_t = (int)(h->grid_t.x * h->grid_t.y) * h->nch_b;
     const bool tma_ok = h->lz_b == TMA_LZ && h->nx % 4 == 0 && (long long)h->nrhs * h->nch_b <= 65535 &&
                         (long long)h->nz * h->nrhs < (1LL << 31);
@@ -847,11 +923,14 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
             if (!std::strcmp(pv, "tma")) h->prec32 = ptma_ok ? 2 : 0;
         }
     }
-    if (const char* sv = std::getenv("PCG_SPMV")) {            // experiments: column|chunked|tile|tma
-        const int m = !std::strcmp(sv, "tile") ? 2 : (!std::strcmp(sv, "chunked") ? 1 : (!std::strcmp(sv, "tma") ? 3 : 0));
+    // PCG_SPMV=tma2 (persistent two-stage pipeline, 8-level chunks) measured
+    // 2-4 % slower than the single-stage sweep at every size and is opt-in only.
+    if (const char* sv = std::getenv("PCG_SPMV")) {            // experiments: column|chunked|tile|tma|tma2
+        const int m = !std::strcmp(sv, "tile") ? 2 : (!std::strcmp(sv, "chunked") ? 1 :
+                      (!std::strcmp(sv, "tma") ? 3 : (!std::strcmp(sv, "tma2") ? 4 : 0)));
         if (h->nz <= 256 && (long long)h->nrhs * h->nch_b <= 65535) {
-            h->spmv32 = (m == 3 && !tma_ok) ? 1 : m;
-            if (m != 3) h->spmv64 = m;
+            h->spmv32 = (m >= 3 && !tma_ok) ? 1 : m;
+            if (m < 3) h->spmv64 = m;
         }
     }
 
@@ -872,7 +951,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if ((rc = dmalloc(h, &h->st, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->st_in, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->d_active, h->nrhs))) return bail(rc);
-    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(std::max(std::max(h->nblocks, h->nblk_c), h->prec_items), std::max(std::max(h->nblk_a, h->nblk_b), h->nblk_t)) * 4))) return bail(rc);
+    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(std::max(std::max(h->nblocks, 2 * h->nblk_c), h->prec_items), std::max(std::max(h->nblk_a, h->nblk_b), 2 * h->nblk_t)) * 4))) return bail(rc);
     if ((rc = dmalloc(h, &h->counters, h->nrhs))) return bail(rc);
     e = cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * h->nrhs, h->stream);
     if (e != cudaSuccess) { h->err = std::string("cudaMemset: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }

@@ -1,0 +1,106 @@
+"""The two large configurations at full size, in the launch configuration
+bench.py times, checked where the oracle cannot run whole:
+
+* sampled outputs, each computed by the oracle on its own: operator rows
+  (``apply_rows``) and column solves of the preconditioner
+  (``solve_columns``, ``apply_columns`` for the backward error);
+* properties that hold at any size: the mixed-precision solve and the FP64
+  solve of the same system agree, and both reach the stopping test or the
+  rounding floor.
+
+Box: 1024 x 1024 x 128 with alpha = 1 + 0.5 sin(2 pi x) sin(2 pi y).
+Band: 1440 x 640 x 64 latitude-longitude band of the shell r in [1, 1.002],
+two right-hand sides solved together.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import apply_columns, apply_rows, solve_columns
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs cuda:0"
+    return torch
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a).ravel().copy()).cuda()
+
+
+def _sampled_checks(torch, s, p, seed):
+    """Operator rows and column solves at sampled places of a full-size grid."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, p.shape)
+    cells = np.stack([rng.integers(0, n, 3000) for n in p.shape])
+    y = torch.empty(p.n_cells, dtype=torch.float64, device="cuda")
+    s.apply_A(_dev(torch, x), y)
+    yg = y.cpu().numpy().reshape(p.shape)[tuple(cells)]
+    yo = apply_rows(p, x, cells)
+    assert np.allclose(yg, yo, rtol=1e-12, atol=1e-12 * np.abs(yo).max())
+    # preconditioner: 48 sampled columns
+    r = rng.uniform(-1, 1, p.shape)
+    z = torch.empty(p.n_cells, dtype=torch.float64, device="cuda")
+    s.precond(_dev(torch, r), z)
+    zg = z.cpu().numpy().reshape(p.shape)
+    cols = np.stack([rng.integers(0, p.n_y, 48), rng.integers(0, p.n_x, 48)])
+    r_cols = np.stack([r[:, j, i] for j, i in cols.T])
+    z_cols = np.stack([zg[:, j, i] for j, i in cols.T])
+    mz, scale = apply_columns(p, z_cols, cols)
+    assert (np.abs(mz - r_cols) <= 16 * p.n_z * EPS64 * scale).all()        # backward error
+    zo = solve_columns(p, r_cols, cols)
+    assert np.linalg.norm(z_cols - zo) / np.linalg.norm(zo) < 1e-10          # forward, vs oracle
+
+
+def _reached(st, tol):
+    return st.status == 0 and (st.relres_true < tol or st.relres_true <= 2.0 * st.relres_floor)
+
+
+def test_large_box_full_size(torch_cuda):
+    import paper_1302_7193_gb300 as pkg
+    torch = torch_cuda
+    p = W.large_box()
+    b = W.rhs_for(p, seed=0)
+    with pkg.Solver(p) as s:
+        _sampled_checks(torch, s, p, seed=21)
+        xf = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        stf = s.solve(_dev(torch, b), xf, tol=1e-8, maxit=100000)
+    with pkg.Solver(p, precision="mixed") as s:
+        xm = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        stm = s.solve(_dev(torch, b), xm, tol=1e-8, maxit=100000)
+    # FP64 stops on the updated residual (Algorithm 1); its true residual sits
+    # a little above it at this grading
+    assert stf.status == 0 and stf.relres_recursive < 1e-8 and stf.relres_true < 1e-7, stf
+    assert _reached(stm, 1e-8), stm
+    rel = (torch.linalg.norm(xm - xf) / torch.linalg.norm(xf)).item()
+    assert rel < 1e-7, rel
+
+
+def test_shell_band_full_size(torch_cuda):
+    import paper_1302_7193_gb300 as pkg
+    torch = torch_cuda
+    p = W.latlon_problem(1440, 640, 64)
+    bs = W.batched_rhs(p, [0, 1])
+    with pkg.Solver(p) as s:
+        _sampled_checks(torch, s, p, seed=22)
+    with pkg.Solver(p, nrhs=2, precision="mixed") as s:
+        xm = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
+        s.solve(_dev(torch, bs), xm, tol=1e-8, maxit=100000)
+        stm = [s.pcg_rhs_stats(r) for r in range(2)]
+    with pkg.Solver(p, nrhs=2) as s:
+        xf = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
+        s.solve(_dev(torch, bs), xf, tol=1e-8, maxit=100000)
+        stf = [s.pcg_rhs_stats(r) for r in range(2)]
+    n = p.n_cells
+    for r in range(2):
+        assert _reached(stm[r], 1e-8), stm[r]
+        assert stf[r].status == 0 and stf[r].relres_recursive < 1e-8 and stf[r].relres_true < 1e-7, stf[r]
+        d = (torch.linalg.norm(xm[r * n:(r + 1) * n] - xf[r * n:(r + 1) * n]) /
+             torch.linalg.norm(xf[r * n:(r + 1) * n])).item()
+        assert d < 1e-7, (r, d)

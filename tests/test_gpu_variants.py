@@ -29,6 +29,8 @@ FP64_VARIANTS = {
     "column-by4": {"PCG_COL_BY": "4"},
     "column-by1": {"PCG_COL_BY": "1"},
     "chunked": {"PCG_KERNELS": "chunked"},
+    "spmv-split": {"PCG_SPMV_KSPLIT": "2"},
+    "spmv-plain-loop": {"PCG_SPMV_PIPE": "0"},
 }
 
 FP32_VARIANTS = {
@@ -36,6 +38,8 @@ FP32_VARIANTS = {
     "spmv-column": {"PCG_SPMV": "column"},
     "spmv-chunked": {"PCG_SPMV": "chunked"},
     "spmv-tile": {"PCG_SPMV": "tile"},
+    "spmv-tma2": {"PCG_SPMV": "tma2"},
+    "spmv-tma-8rows": {"PCG_TMA_BY": "8"},
     "prec-chunked": {"PCG_PREC": "chunked"},
     "all-column": {"PCG_KERNELS": "column"},
 }
@@ -53,7 +57,7 @@ def _oracle(p, b, **kw):
 
 
 def _set(monkeypatch, env):
-    for k in ("PCG_COL_BY", "PCG_KERNELS", "PCG_SPMV", "PCG_PREC"):
+    for k in ("PCG_COL_BY", "PCG_KERNELS", "PCG_SPMV", "PCG_PREC", "PCG_SPMV_KSPLIT", "PCG_TMA_BY", "PCG_SPMV_PIPE"):
         monkeypatch.delenv(k, raising=False)
     for k, v in env.items():
         monkeypatch.setenv(k, v)

@@ -1,7 +1,9 @@
 """Pins of the oracle's line preconditioner and PCG loops.
 
 * M = block-diag(A) (Section 4.1): the LAPACK tridiagonal solve of every
-  column equals a dense LU solve of the block cut out of the assembled A.
+  column equals a dense LU solve of the block cut out of the assembled A;
+  the column-by-column solve used for sampled checks of large grids equals
+  it too.
 * With a single column (no horizontal coupling survives) M = A, so one
   preconditioner application is the exact solution and PCG stops after one
   iteration.
@@ -16,7 +18,7 @@ import scipy.linalg as sla
 
 import workloads as W
 from oracle import (FluxOperator, LinePreconditioner, assemble_csr, column_blocks, pcg_interleaved,
-                    pcg_textbook, rounding_floor)
+                    pcg_textbook, rounding_floor, solve_columns, apply_columns)
 
 
 def _problems():
@@ -45,6 +47,32 @@ def test_line_solve_equals_dense_block_lu(p):
         bound = 10 * p.n_z * np.linalg.cond(block) * np.finfo(float).eps
         err = np.linalg.norm(z.ravel()[idx] - zc) / np.linalg.norm(zc)
         assert err <= max(bound, 1e-14), (col, err, bound)
+
+
+@pytest.mark.parametrize("p", _problems() + [W.panel_problem(6, 5, 7, thickness=0.05, name="panel"),
+                                             W.box_problem(1, 3, 4, 0.01, name="box-1x3")],
+                         ids=lambda p: p.name)
+def test_column_solve_equals_dense_block_lu(p):
+    a = assemble_csr(p)
+    dense = a.toarray()
+    plane = p.n_x * p.n_y
+    rng = np.random.default_rng(11)
+    r = rng.uniform(-1, 1, p.shape)
+    cols = np.array([[c // p.n_x for c in range(plane)], [c % p.n_x for c in range(plane)]])
+    r_cols = np.stack([r[:, j, i] for j, i in cols.T])
+    z = solve_columns(p, r_cols, cols)
+    for c, (j, i) in enumerate(cols.T):
+        idx = (j * p.n_x + i) + plane * np.arange(p.n_z)
+        block = dense[np.ix_(idx, idx)]
+        zc = sla.lu_solve(sla.lu_factor(block), r_cols[c])
+        bound = 10 * p.n_z * np.linalg.cond(block) * np.finfo(float).eps
+        err = np.linalg.norm(z[c] - zc) / np.linalg.norm(zc)
+        assert err <= max(bound, 1e-14), (c, err, bound)
+        # the flux-form product of the column block is the block times z, to
+        # the rounding of the assembled product (the flux form is the exact one)
+        mz, scale = apply_columns(p, z[c:c + 1], cols[:, c:c + 1])
+        tol = 64 * np.finfo(float).eps * (np.abs(block) @ np.abs(z[c]) + scale[0])
+        assert (np.abs(mz[0] - block @ z[c]) <= tol).all()
 
 
 @pytest.mark.parametrize("p", _problems(), ids=lambda p: p.name)
