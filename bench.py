@@ -394,6 +394,60 @@ def run_other_workload(args, dev, pkg, W, torch):
     print(json.dumps(out), flush=True)
 
 
+def run_multigrid(args, dev, pkg, W, torch):
+    """FP64 solves preconditioned by one multigrid V-cycle (PCG_PREC_MULTIGRID,
+    the solver the paper names as its next step, Section 8) next to the
+    vertical-line preconditioner, on the benchmark grids: solves/s to 1e-8,
+    iterations, and the distance between the two solutions."""
+    import numpy as np
+    cases = [("box256x256x128", W.medium_box(), lambda p: W.medium_box_rhs(p)),
+             ("box1024x1024x128_sin", W.large_box(), lambda p: W.rhs_for(p, seed=0)),
+             ("paper-panel256x256x128", W.panel_problem(256, 256, 128), lambda p: W.rhs_for(p, seed=0))]
+    stream = torch.cuda.current_stream(dev)
+    out = {"metric": "PCG solves/s", "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic", "workload": "multigrid", "dtype": "f64", "tol": TOL, "cases": {}}
+    for name, p, rhs in cases:
+        b = torch.from_numpy(np.ascontiguousarray(rhs(p)).ravel()).to(dev)
+        res, xs = {}, {}
+        for pc in ("line", "multigrid"):
+            with pkg.Solver(p, preconditioner=pc, stream=stream.cuda_stream) as s:
+                x = torch.zeros_like(b)
+                s.solve(b, x, tol=TOL, maxit=200000)           # warm-up (graph capture)
+                times = []
+                for _ in range(max(1, min(args.steps, 3))):
+                    x.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st = s.solve(b, x, tol=TOL, maxit=200000)
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = statistics.mean(times)
+                entry = {"solves_per_s": 1000.0 / ms, "ms": ms, "iterations": st.iterations,
+                         "ms_per_iteration": ms / max(1, st.iterations), "relres_recursive": st.relres_recursive,
+                         "relres_true": st.relres_true, "status": st.status_name}
+                if pc == "multigrid":
+                    z = torch.empty_like(b)
+                    s.precond(b, z)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(10):
+                        s.precond(b, z)
+                    e1.record(stream)
+                    e1.synchronize()
+                    entry["vcycle_ms"] = e0.elapsed_time(e1) / 10
+                res[pc] = entry
+                xs[pc] = x.clone()
+        res["multigrid_speedup"] = res["multigrid"]["solves_per_s"] / res["line"]["solves_per_s"]
+        res["relative_distance_of_solutions"] = float((xs["multigrid"] - xs["line"]).norm() / xs["line"].norm())
+        out["cases"][name] = res
+        del b, xs
+    out["value"] = out["cases"]["box256x256x128"]["multigrid"]["solves_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,12 +456,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", choices=["box256", "box1024", "shell-batch", "serve", "paper-panel"],
+    ap.add_argument("--workload", choices=["box256", "box1024", "shell-batch", "serve", "paper-panel", "multigrid"],
                     default="box256",
                     help="box256: the benchmark (default); box1024: 1024x1024x128 box with variable alpha, "
                          "FP64 and mixed; shell-batch: 1440x640x64 lat-lon band, 16 right-hand sides, FP64 and mixed; "
                          "serve: Poisson request stream through the served batch; paper-panel: the paper's own "
-                         "cubed-sphere panel problem, 256x256x128, residual reduced by 1e5")
+                         "cubed-sphere panel problem, 256x256x128, residual reduced by 1e5; multigrid: FP64 solves "
+                         "with the multigrid V-cycle preconditioner next to the line preconditioner")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: seconds of arrivals (200 req/s)")
     ap.add_argument("--serve-mix", choices=["paper", "small"], default="paper",
                     help="serve: the full request mix, or only requests of at most 128 x 128 x 64 at 10x the rate")
@@ -434,6 +489,9 @@ def main():
         return
     if args.workload == "paper-panel":
         run_paper_panel(args, dev, pkg, W, torch)
+        return
+    if args.workload == "multigrid":
+        run_multigrid(args, dev, pkg, W, torch)
         return
     if args.workload != "box256":
         run_other_workload(args, dev, pkg, W, torch)

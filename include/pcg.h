@@ -67,6 +67,18 @@ enum pcg_precision {
     PCG_FP64 = 0,              /* FP64 storage and arithmetic throughout          */
     PCG_MIXED = 1              /* FP32 inner PCG inside FP64 iterative refinement */
 };
+enum pcg_preconditioner {
+    PCG_PREC_LINE = 0,         /* vertical-line preconditioner M = block-diag(A) (Section 4.1) */
+    PCG_PREC_MULTIGRID = 1     /* one V-cycle of geometric multigrid with vertical line smoothing (the
+                                  solver Section 8 names as the next step): n_x, n_y halved per level
+                                  while both are even, the vertical grid kept; each level the same
+                                  discretisation (alpha on a coarse face = mean of its two fine faces);
+                                  restriction = sum of the four fine cells, prolongation = its
+                                  transpose; one damped (omega = 0.8) block-Jacobi sweep before and
+                                  after the coarse correction; coarsest level: its column block
+                                  (with one refinement step) if it is one column, else 8 smoothing
+                                  sweeps.  PCG_FP64 only. */
+};
 
 typedef struct pcg_ctx* pcg_t;
 typedef struct pcg_server* pcg_server_t;
@@ -100,6 +112,7 @@ typedef struct {
     int max_outer;             /* PCG_MIXED: refinement sweeps cap; 0 selects 16   */
     int passes_per_launch;     /* PCG passes per CUDA-graph launch between convergence polls; 0 selects 16 */
     void* stream;              /* cudaStream_t for all work; NULL = default stream */
+    int preconditioner;        /* pcg_preconditioner (PCG_PREC_LINE when opts is NULL) */
 } pcg_opts_t;
 
 /* Per-solve statistics.  For nrhs > 1 the scalar fields report the worst
@@ -148,7 +161,8 @@ int pcg_apply_A(pcg_t h, const double* x, double* y);
 
 /* z = M^{-1} r, M = block-diag(A) (Section 4.1; one Thomas solve per
  * column), FP64 device pointers, nrhs vectors; r and z must not overlap.
- * Asynchronous on the handle's stream. */
+ * For a handle created with PCG_PREC_MULTIGRID, z = B r: one V-cycle from a
+ * zero guess.  Asynchronous on the handle's stream. */
 int pcg_precond(pcg_t h, const double* r, double* z);
 
 /* FP32 versions of the two operators (the kernels of the FP32 inner solve

@@ -15,10 +15,14 @@ At strong anisotropy a row's diagonal is the sum of two large vertical
 couplings and a much smaller remainder s (the zero-order term plus the
 horizontal couplings); stored in FP64 the diagonal keeps s only to a
 relative accuracy of about eps * W / s, and the LU inherits that error.  The
-solve therefore takes one step of classical iterative refinement with the
-residual r - M z evaluated in flux form,
+solve therefore refines the LU solution with the residual r - M z evaluated
+in flux form,
     (M z)_k = s_k z_k + W_k (z_k - z_{k+1}) + W_{k-1} (z_k - z_{k-1}),
-which is exact to rounding, so the returned z is M^{-1} r to FP64 accuracy.
+which is exact to rounding, until the correction falls below rounding (at
+most ``refine_steps`` steps): one step suffices while a column has
+horizontal couplings; a column block without them (the coarsest level of the
+multigrid hierarchy, condition number ~1e9) needs several.  The returned z is
+M^{-1} r to FP64 accuracy.
 """
 from __future__ import annotations
 
@@ -30,7 +34,7 @@ from .discretisation import _row_entries, column_blocks, operator_terms
 
 
 class LinePreconditioner:
-    def __init__(self, a, p: Problem, refine_steps: int = 1):
+    def __init__(self, a, p: Problem, refine_steps: int = 20):
         self.p = p
         self.refine_steps = refine_steps
         lower, main, upper = column_blocks(a, p)
@@ -97,8 +101,12 @@ class LinePreconditioner:
         shape = np.shape(r)
         rc = self._to_columns(r)
         x = self._lu_solve(rc)
+        eps = np.finfo(np.float64).eps
         for _ in range(self.refine_steps):
-            x = x + self._lu_solve(rc - self.apply_flux(x))
+            d = self._lu_solve(rc - self.apply_flux(x))
+            x = x + d
+            if np.linalg.norm(d) <= 4 * eps * np.linalg.norm(x):
+                break
         return self._from_columns(x).reshape(shape)
 
     def __call__(self, r):
@@ -134,9 +142,9 @@ def solve_columns(p: Problem, r_cols: np.ndarray, cols) -> np.ndarray:
 
     ``cols`` is a (2, m) array of (j, i); ``r_cols`` (m, n_z) holds r on
     those columns.  Each block is taken in flux form (``_column_flux``),
-    factored with LAPACK's GTTRF and applied with GTTRS, plus one refinement
-    step with the flux-form residual, exactly as ``LinePreconditioner`` does
-    for the whole grid.
+    factored with LAPACK's GTTRF and applied with GTTRS, then refined with the
+    flux-form residual until the correction falls below rounding, exactly as
+    ``LinePreconditioner`` does for the whole grid.
     """
     t = operator_terms(p)
     nz = p.n_z
@@ -163,14 +171,20 @@ def solve_columns(p: Problem, r_cols: np.ndarray, cols) -> np.ndarray:
             return x
 
         x = lu_solve(rc)
-        x = x + lu_solve(rc - _flux_apply(s, w, x))
+        eps = np.finfo(np.float64).eps
+        for _ in range(20):
+            dx = lu_solve(rc - _flux_apply(s, w, x))
+            x = x + dx
+            if np.linalg.norm(dx) <= 4 * eps * np.linalg.norm(x):
+                break
         out[c] = x
     return out
 
 
 def apply_columns(p: Problem, z_cols: np.ndarray, cols):
-    """M z on selected columns, in flux form, and the scale sum |terms| of
-    every row (for backward-error bounds): two (m, n_z) arrays."""
+    """M z on selected columns, in flux form, and |M| |z| of every row (the
+    scale of a backward-error bound of a tridiagonal solve): two (m, n_z)
+    arrays."""
     t = operator_terms(p)
     nz = p.n_z
     jj, ii = (np.asarray(c, dtype=np.int64) for c in cols)
@@ -181,9 +195,9 @@ def apply_columns(p: Problem, z_cols: np.ndarray, cols):
         s, w = _column_flux(p, t, int(jj[c]), int(ii[c]))
         z = z_cols[c]
         mz[c] = _flux_apply(s, w, z)
-        af = np.abs(w[:-1] * (z[:-1] - z[1:]))
-        sc = np.abs(s * z)
-        sc[:-1] += af
-        sc[1:] += af
+        wd = np.concatenate([[0.0], w[:-1]])
+        sc = np.abs(s + w + wd) * np.abs(z)
+        sc[:-1] += np.abs(w[:-1] * z[1:])
+        sc[1:] += np.abs(w[:-1] * z[:-1])
         scale[c] = sc
     return mz, scale

@@ -19,8 +19,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpcg.so")
 
 PCG_OK, PCG_ERR_INVALID_ARG, PCG_ERR_OOM, PCG_ERR_CUDA, PCG_NOT_CONVERGED, PCG_BREAKDOWN, PCG_TIMEOUT, PCG_PENDING = range(8)
-PCG_GEOM_BOX, PCG_GEOM_LATLON = 0, 1
+PCG_GEOM_BOX, PCG_GEOM_LATLON, PCG_GEOM_CUBED_PANEL = 0, 1, 2
 PCG_FP64, PCG_MIXED = 0, 1
+PCG_PREC_LINE, PCG_PREC_MULTIGRID = 0, 1
 STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "not_converged", 5: "breakdown", 6: "timeout",
                 7: "pending"}
 
@@ -46,7 +47,8 @@ class pcg_coeffs_t(ctypes.Structure):
 
 class pcg_opts_t(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
-                ("max_outer", ctypes.c_int), ("passes_per_launch", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("max_outer", ctypes.c_int), ("passes_per_launch", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("preconditioner", ctypes.c_int)]
 
 
 class pcg_stats_t(ctypes.Structure):
@@ -167,7 +169,8 @@ def _dbl(a):
 
 
 def pcg_create(problem, nrhs: int = 1, precision: int = PCG_FP64, inner_tol: float = 0.0, inner_maxit: int = 0,
-               max_outer: int = 0, passes_per_launch: int = 0, stream: Optional[int] = None):
+               max_outer: int = 0, passes_per_launch: int = 0, stream: Optional[int] = None,
+               preconditioner: int = PCG_PREC_LINE):
     """Marshal a problem description (any object with the fields of
     ``workloads.Problem``) into pcg_create; returns (handle, keepalive)."""
     lib = load_library()
@@ -186,7 +189,7 @@ def pcg_create(problem, nrhs: int = 1, precision: int = PCG_FP64, inner_tol: flo
         except Exception:
             stream = 0
     o = pcg_opts_t(int(precision), float(inner_tol), int(inner_maxit), int(max_outer), int(passes_per_launch),
-                   ctypes.c_void_p(stream or 0))
+                   ctypes.c_void_p(stream or 0), int(preconditioner))
     h = ctypes.c_void_p()
     rc = lib.pcg_create(ctypes.byref(g), ctypes.byref(c), ctypes.byref(o), ctypes.byref(h))
     if rc != PCG_OK:
@@ -198,14 +201,16 @@ class Solver:
     """One pcg_t handle.  Vectors are torch tensors of nrhs * n_z * n_y * n_x
     elements in the layout [nrhs][n_z][n_y][n_x]."""
 
-    def __init__(self, problem, nrhs: int = 1, precision: str = "fp64", **kw):
+    def __init__(self, problem, nrhs: int = 1, precision: str = "fp64", preconditioner: str = "line", **kw):
         self.lib = load_library()
         self.problem = problem
         self.nrhs = nrhs
         self.n = int(problem.n_x) * int(problem.n_y) * int(problem.n_z) * nrhs
         prec = {"fp64": PCG_FP64, "mixed": PCG_MIXED}[precision]
         self.precision = precision
-        self.h, self._keep = pcg_create(problem, nrhs=nrhs, precision=prec, **kw)
+        self.preconditioner = preconditioner
+        pc = {"line": PCG_PREC_LINE, "multigrid": PCG_PREC_MULTIGRID}[preconditioner]
+        self.h, self._keep = pcg_create(problem, nrhs=nrhs, precision=prec, preconditioner=pc, **kw)
 
     def _check(self, rc: int, allow=(PCG_OK,)):
         if rc not in allow:

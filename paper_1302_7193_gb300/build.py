@@ -16,6 +16,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpcg.so")
 SOURCES = [os.path.join(HERE, "csrc", "pcg.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "kernels.cuh"), os.path.join(HERE, "csrc", "serve.cuh"),
+                  os.path.join(HERE, "csrc", "multigrid.cuh"),
                   os.path.join(ROOT, "include", "pcg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,190 @@
+// Device kernels of the multigrid preconditioner (PCG_PREC_MULTIGRID).
+//
+// A V-cycle on a hierarchy of horizontally coarsened grids (the solver the
+// paper names as the next step, Section 8): damped block-Jacobi smoothing
+// with the column blocks of each level (Thomas recurrences in the excess
+// form of kernels.cuh), residuals in flux form, restriction by summing the four fine
+// cells of a coarse cell and prolongation by its transpose.
+#pragma once
+#include "kernels.cuh"
+
+namespace pcg {
+
+// ---------------------------------------------------------------------------
+// Multigrid V-cycle (FP64) on a hierarchy of horizontally coarsened grids:
+// damped block-Jacobi smoothing with the column blocks, residuals, and the
+// transfers R (sum of the four fine cells of a coarse cell) and P = R^T.
+// Every kernel skips a right-hand side whose solve has stopped (st[rhs].done).
+// ---------------------------------------------------------------------------
+// z = (acc ? z : 0) + omega M^{-1} rin, one thread per column; tmp receives
+// the forward sweep's y_k (tmp may be rin itself).  The Thomas recurrences
+// run in the excess form (g_k = 1/D_k, E_k = D_k - W_k):
+//   y_k = (r_k - e_{k-1} y_{k-1}) + y_{k-1},  e = E g,
+//   z_k = z_{k+1} + g_k (y_k - E_k z_{k+1}),
+// because on coarse levels the vertical couplings grow 4x per level against
+// the horizontal ones, the excess 1 - W/D falls towards 1e-7 and a stored
+// ratio W/D would carry it with a relative error of 2^-53 / (1 - W/D).
+__global__ __launch_bounds__(NT) void k_mg_smooth(OpView<double> op, const double* rin, double* tmp, double* z,
+                                                  double omega, int acc, const SolveState* __restrict__ st) {
+    const int rhs = blockIdx.z;
+    if (st[rhs].done) return;
+    const Col<double> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+    if (!col.valid) return;
+    const long long base = (long long)rhs * op.vol + col.c;
+    const long long pl = op.plane, fs = op.ncls;
+    const double* fg = op.fg + col.cls;
+    const double* fe = op.fe + col.cls;
+    const int nz = op.nz;
+    // the loads of the next PB levels are issued before the current PB levels
+    // are stored (tmp may be rin, and z is read and written)
+    constexpr int PB = 8;
+    double y = 0.0, eprev = 0.0;
+    double ra[PB];
+#pragma unroll
+    for (int t = 0; t < PB; ++t) ra[t] = t < nz ? rin[base + t * pl] : 0.0;
+    for (int k0 = 0; k0 < nz; k0 += PB) {
+        double rn[PB];
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            const int k = k0 + PB + t;
+            rn[t] = k < nz ? rin[base + k * pl] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            const int k = k0 + t;
+            if (k < nz) {
+                y = fma(-eprev, y, ra[t]) + y;
+                tmp[base + k * pl] = y;
+                eprev = ldro(fe + k * fs) * ldro(fg + k * fs);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < PB; ++t) ra[t] = rn[t];
+    }
+    double zn = 0.0;
+    double ya[PB], za[PB];
+    const int kt = nz - 1;
+#pragma unroll
+    for (int t = 0; t < PB; ++t) {
+        const int k = kt - t;
+        ya[t] = k >= 0 ? tmp[base + k * pl] : 0.0;
+        za[t] = (acc && k >= 0) ? z[base + k * pl] : 0.0;
+    }
+    for (int k0 = kt; k0 >= 0; k0 -= PB) {
+        double yn[PB], zn_[PB];
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            const int k = k0 - PB - t;
+            yn[t] = k >= 0 ? tmp[base + k * pl] : 0.0;
+            zn_[t] = (acc && k >= 0) ? z[base + k * pl] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            const int k = k0 - t;
+            if (k >= 0) {
+                zn = fma(ldro(fg + k * fs), fma(-ldro(fe + k * fs), zn, ya[t]), zn);
+                z[base + k * pl] = acc ? fma(omega, zn, za[t]) : omega * zn;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            ya[t] = yn[t];
+            za[t] = zn_[t];
+        }
+    }
+}
+
+// t = r - A z (flux form, as k_apply)
+__global__ __launch_bounds__(NT) void k_mg_resid(OpView<double> op, const double* __restrict__ r,
+                                                 const double* __restrict__ z, double* __restrict__ t,
+                                                 const SolveState* __restrict__ st) {
+    const int rhs = blockIdx.z;
+    if (st[rhs].done) return;
+    const Col<double> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+    if (!col.valid) return;
+    const long long base = (long long)rhs * op.vol;
+    const double* __restrict__ zb = z + base;
+    double zc = zb[col.c];
+    double fprev = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < op.nz; ++k) {
+        const double* zl = zb + (long long)k * op.plane;
+        const double zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
+        const double f = ldro(op.wv + k) * (zc - zu);
+        const double hz = horiz(col, zl, zc);
+        const double az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+        const long long o = base + (long long)k * op.plane + col.c;
+        t[o] = r[o] - az;
+        fprev = f;
+        zc = zu;
+    }
+}
+
+// rc = R tf: every coarse cell (rhs, k, J, I) sums the fine cells
+// (2J, 2I), (2J, 2I+1), (2J+1, 2I), (2J+1, 2I+1) of the same level k.
+__global__ void k_mg_restrict(const double* __restrict__ tf, double* __restrict__ rc, int nxc, int nyc, int nz,
+                              int nrhs, const SolveState* __restrict__ st) {
+    const long long planec = (long long)nxc * nyc, volc = planec * nz, n = volc * nrhs;
+    const long long nxf = 2LL * nxc, planef = 4 * planec;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int rhs = (int)(c / volc);
+        if (st[rhs].done) continue;
+        const long long rem = c - rhs * volc;
+        const long long k = rem / planec, jc = (rem - k * planec) / nxc, ic = rem - k * planec - jc * nxc;
+        const double* f = tf + rhs * (volc * 4) + k * planef + (2 * jc) * nxf + 2 * ic;
+        rc[c] = ((f[0] + f[1]) + f[nxf]) + f[nxf + 1];
+    }
+}
+
+// zf += P zc: every fine cell adds its coarse cell's value.
+__global__ void k_mg_prolong(const double* __restrict__ zc, double* __restrict__ zf, int nxf, int nyf, int nz,
+                             int nrhs, const SolveState* __restrict__ st) {
+    const long long planef = (long long)nxf * nyf, volf = planef * nz, n = volf * nrhs;
+    const int nxc = nxf / 2;
+    const long long planec = planef / 4, volc = planec * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int rhs = (int)(c / volf);
+        if (st[rhs].done) continue;
+        const long long rem = c - rhs * volf;
+        const long long k = rem / planef, j = (rem - k * planef) / nxf, i = rem - k * planef - j * nxf;
+        zf[c] += zc[rhs * volc + k * planec + (j / 2) * nxc + i / 2];
+    }
+}
+
+// r <- r - alpha q (Algorithm 1 line 2, the preconditioner itself applied separately)
+__global__ void k_mg_rupdate(double* __restrict__ r, const double* __restrict__ q, long long vol, int nrhs,
+                             const SolveState* __restrict__ st) {
+    const long long n = vol * nrhs;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int rhs = (int)(c / vol);
+        if (st[rhs].done) continue;
+        r[c] = fma(-st[rhs].alpha, q[c], r[c]);
+    }
+}
+
+// <r, r> and <r, z> of every right-hand side; the last block applies the
+// stopping test and forms beta (Algorithm 1 lines 3-4, as k_sweep_prec).
+__global__ __launch_bounds__(NT) void k_mg_dots(OpView<double> op, const double* __restrict__ r,
+                                                const double* __restrict__ z, SolveState* __restrict__ states,
+                                                double* __restrict__ partials, unsigned* __restrict__ counters,
+                                                int nblocks) {
+    const int rhs = blockIdx.z;
+    SolveState* st = states + rhs;
+    if (st->done) return;
+    const Col<double> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+    Acc<double> acc[2];
+    if (col.valid) {
+        const long long base = (long long)rhs * op.vol + col.c;
+        for (int k = 0; k < op.nz; ++k) {
+            const long long o = base + (long long)k * op.plane;
+            const double rk = r[o];
+            acc[0].add_prod(rk, rk);
+            acc[1].add_prod(rk, z[o]);
+        }
+    }
+    double v[2];
+    if (grid_sum_acc<2>(acc, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
+        prec_epilogue(st, v[0], v[1]);
+}
+
+}  // namespace pcg

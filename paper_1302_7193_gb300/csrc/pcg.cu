@@ -21,6 +21,7 @@
 
 #include "../../include/pcg.h"
 #include "kernels.cuh"
+#include "multigrid.cuh"
 
 using pcg::BX;
 using pcg::BY;
@@ -102,6 +103,18 @@ struct pcg_ctx {
     dim3 grid_c, block_c;                 // one-thread-per-column sweeps: 32 x by column tiles
     int nblk_c = 0;
     int ksplit = 1;                       // one-thread-per-column SpMV sweep: parts of each column
+    // multigrid preconditioner (PCG_PREC_MULTIGRID): coarse levels 1..L-1
+    struct MGLevel {
+        pcg_ctx* h = nullptr;             // the level's own handle (tables, factors, launch shapes)
+        double *r = nullptr, *z = nullptr, *t = nullptr;   // right-hand side, correction, scratch
+    };
+    int precond = PCG_PREC_LINE;
+    std::vector<MGLevel> mg;
+    double* mg_t0 = nullptr;              // scratch of level 0
+    SolveState* mg_free = nullptr;        // all-active states for a V-cycle outside a solve
+    int mg_nu = 1, mg_coarse = 8;
+    double mg_omega = 0.8;
+    int kernels_per_pass = 2;             // kernel launches in one Algorithm-1 pass of the graphs
     int spmv_pipe = 1;                    // FP64 SpMV sweep with u, p, q loads issued ahead (PCG_SPMV_PIPE=0: plain)
 
     cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
@@ -557,12 +570,133 @@ void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, 
 #undef PCG_SPMV_CH
 }
 
+// One V-cycle z0 = B r0 (PCG_PREC_MULTIGRID) on stream s: level 0 is the
+// handle itself (scratch t0), levels 1.. are h->mg.  Returns the number of
+// kernels launched.  st: per-rhs states (a stopped rhs is skipped).
+int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const double* r0, double* z0, double* t0) {
+    const int L = (int)h->mg.size() + 1;
+    auto H = [&](int l) { return l == 0 ? h : h->mg[l - 1].h; };
+    auto R = [&](int l) -> const double* { return l == 0 ? r0 : h->mg[l - 1].r; };
+    auto Z = [&](int l) { return l == 0 ? z0 : h->mg[l - 1].z; };
+    auto T = [&](int l) { return l == 0 ? t0 : h->mg[l - 1].t; };
+    auto elems = [&](long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16); };
+    int n = 0;
+    auto smooth_first = [&](int l, double omega) {       // z = omega M^{-1} r
+        pcg_t hl = H(l);
+        pcg::k_mg_smooth<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), R(l), T(l), Z(l), omega, 0, st);
+        ++n;
+    };
+    auto smooth_more = [&](int l) {                      // z += omega M^{-1} (r - A z)
+        pcg_t hl = H(l);
+        pcg::k_mg_resid<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), R(l), Z(l), T(l), st);
+        pcg::k_mg_smooth<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), T(l), T(l), Z(l), h->mg_omega, 1, st);
+        n += 2;
+    };
+    for (int l = 0; l + 1 < L; ++l) {
+        smooth_first(l, h->mg_omega);
+        for (int k = 1; k < h->mg_nu; ++k) smooth_more(l);
+        pcg_t hl = H(l), hc = H(l + 1);
+        pcg::k_mg_resid<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), R(l), Z(l), T(l), st);
+        pcg::k_mg_restrict<<<elems(hc->ntot), 256, 0, s>>>(T(l), h->mg[l].r, hc->nx, hc->ny, hc->nz, hc->nrhs, st);
+        n += 2;
+    }
+    const int c = L - 1;
+    if (H(c)->plane == 1) {
+        // one column: its block is all of A, solved with one step of
+        // refinement (z += M^{-1} (r - A z)): without horizontal couplings the
+        // block's condition number reaches 1e10 at strong anisotropy
+        pcg_t hl = H(c);
+        smooth_first(c, 1.0);
+        pcg::k_mg_resid<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), R(c), Z(c), T(c), st);
+        pcg::k_mg_smooth<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), T(c), T(c), Z(c), 1.0, 1, st);
+        n += 2;
+    } else {
+        smooth_first(c, h->mg_omega);
+        for (int k = 1; k < h->mg_coarse; ++k) smooth_more(c);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        pcg_t hl = H(l);
+        pcg::k_mg_prolong<<<elems(hl->ntot), 256, 0, s>>>(Z(l + 1), Z(l), hl->nx, hl->ny, hl->nz, hl->nrhs, st);
+        ++n;
+        for (int k = 0; k < h->mg_nu; ++k) smooth_more(l);
+    }
+    return n;
+}
+
+// Levels of the multigrid hierarchy: n_x, n_y halved while both are even
+// (down to one column), each level a handle of its own on the coarser grid
+// with alpha on a coarse face the mean of its two fine faces.
+int build_hierarchy(pcg_t h, const pcg_grid_t* grid, const pcg_coeffs_t* coeffs) {
+    int rc;
+    if ((rc = dmalloc(h, &h->mg_t0, (size_t)h->ntot))) return rc;
+    if ((rc = dmalloc(h, &h->mg_free, h->nrhs))) return rc;
+    PCG_CK(h, cudaMemsetAsync(h->mg_free, 0, sizeof(SolveState) * h->nrhs, h->stream));
+    pcg_grid_t g = *grid;
+    std::vector<double> ae, an;
+    if (coeffs->alpha_e) ae.assign(coeffs->alpha_e, coeffs->alpha_e + (size_t)g.n_x * g.n_y);
+    if (coeffs->alpha_n) an.assign(coeffs->alpha_n, coeffs->alpha_n + (size_t)g.n_x * g.n_y);
+    while (h->mg.size() < 31 && g.n_x % 2 == 0 && g.n_y % 2 == 0 && (long long)g.n_x * g.n_y > 1) {
+        const int nx = g.n_x, nxc = g.n_x / 2, nyc = g.n_y / 2;
+        std::vector<double> aec, anc;
+        if (!ae.empty()) {
+            aec.resize((size_t)nxc * nyc);
+            for (int J = 0; J < nyc; ++J)
+                for (int I = 0; I < nxc; ++I)
+                    aec[(size_t)J * nxc + I] = 0.5 * (ae[(size_t)(2 * J) * nx + 2 * I + 1] + ae[(size_t)(2 * J + 1) * nx + 2 * I + 1]);
+        }
+        if (!an.empty()) {
+            anc.resize((size_t)nxc * nyc);
+            for (int J = 0; J < nyc; ++J)
+                for (int I = 0; I < nxc; ++I)
+                    anc[(size_t)J * nxc + I] = 0.5 * (an[(size_t)(2 * J + 1) * nx + 2 * I] + an[(size_t)(2 * J + 1) * nx + 2 * I + 1]);
+        }
+        g.n_x = nxc;
+        g.n_y = nyc;
+        pcg_coeffs_t c = *coeffs;
+        c.alpha_e = aec.empty() ? nullptr : aec.data();
+        c.alpha_n = anc.empty() ? nullptr : anc.data();
+        pcg_opts_t o{};
+        o.precision = PCG_FP64;
+        o.passes_per_launch = h->ppl;
+        o.stream = (void*)h->stream;
+        o.preconditioner = PCG_PREC_LINE;
+        pcg_t hc = nullptr;
+        rc = pcg_create(&g, &c, &o, &hc);
+        if (rc) return fail(h, rc, "multigrid level " + std::to_string(h->mg.size() + 1) + ": " + g_create_error);
+        h->mg.push_back(pcg_ctx::MGLevel{});
+        h->mg.back().h = hc;
+        for (double** p : {&h->mg.back().r, &h->mg.back().z, &h->mg.back().t})
+            if ((rc = dmalloc(h, p, (size_t)hc->ntot))) return rc;
+        ae.swap(aec);
+        an.swap(anc);
+    }
+    return PCG_OK;
+}
+
+// One Algorithm-1 pass with the V-cycle as preconditioner: r <- r - alpha q;
+// z = B r; <r, r>, <r, z>, stopping test, beta; then the SpMV sweep.
+int launch_mg_pass(pcg_t h, cudaStream_t s) {
+    const unsigned g = (unsigned)std::min<long long>((h->ntot + 255) / 256, 152LL * 16);
+    pcg::k_mg_rupdate<<<g, 256, 0, s>>>(h->r64, h->q64, h->vol, h->nrhs, h->st);
+    int n = 1 + launch_vcycle(h, s, h->st, h->r64, h->z64, h->mg_t0);
+    pcg::k_mg_dots<<<h->grid_c, h->block_c, 0, s>>>(h->view64(), h->r64, h->z64, h->st, h->partials, h->counters,
+                                                    h->nblk_c);
+    launch_spmv<double>(h, s, h->view64(), h->u64, h->p64, h->q64, h->z64, h->st);
+    return n + 2;
+}
+
 // Capture `ppl` passes of Algorithm 1 (preconditioner sweep + SpMV sweep).
 template <typename T>
 int capture_passes(pcg_t h, OpView<T> v, T* u, T* r, T* z, T* p, T* q, SolveState* st, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     PCG_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < h->ppl; ++i) {
+        if constexpr (sizeof(T) == 8) {
+            if (h->precond == PCG_PREC_MULTIGRID) {
+                h->kernels_per_pass = launch_mg_pass(h, h->cap_stream);
+                continue;
+            }
+        }
         launch_prec<T>(h, h->cap_stream, v, r, q, z, st);
         launch_spmv<T>(h, h->cap_stream, v, u, p, q, z, st);
     }
@@ -585,7 +719,7 @@ int run_graph(pcg_t h, cudaGraphExec_t graph, SolveState* st, long long max_laun
         PCG_CK(h, cudaGraphLaunch(graph, h->stream));
         PCG_CK(h, cudaMemcpyAsync(h->h_st + (n & 1) * h->nrhs, st, sb, cudaMemcpyDeviceToHost, h->stream));
         PCG_CK(h, cudaEventRecord(h->ev[n & 1], h->stream));
-        h->launches += 2LL * h->ppl;
+        h->launches += (long long)h->kernels_per_pass * h->ppl;
         return PCG_OK;
     };
     int rc;
@@ -814,10 +948,19 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
         if (opts->max_outer > 0) h->max_outer = opts->max_outer;
         if (opts->passes_per_launch > 0) h->ppl = opts->passes_per_launch;
         h->stream = (cudaStream_t)opts->stream;
+        h->precond = opts->preconditioner;
     }
     if (h->precision != PCG_FP64 && h->precision != PCG_MIXED) {
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG, "unknown precision");
+    }
+    if (h->precond != PCG_PREC_LINE && h->precond != PCG_PREC_MULTIGRID) {
+        delete h;
+        return fail(nullptr, PCG_ERR_INVALID_ARG, "unknown preconditioner");
+    }
+    if (h->precond == PCG_PREC_MULTIGRID && h->precision != PCG_FP64) {
+        delete h;
+        return fail(nullptr, PCG_ERR_INVALID_ARG, "the multigrid preconditioner is available with PCG_FP64 only");
     }
     h->rhs_stats.assign(h->nrhs, pcg_stats_t{});
     if (const char* tr = std::getenv("PCG_TRACE")) h->trace = std::atoi(tr);
@@ -958,6 +1101,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     e = cudaMallocHost((void**)&h->h_st, sizeof(SolveState) * 2 * h->nrhs);
     if (e != cudaSuccess) { h->h_st = nullptr; h->err = "cudaMallocHost failed"; return bail(PCG_ERR_OOM); }
     if ((rc = upload_tables(h, t))) return bail(rc);
+    if (h->precond == PCG_PREC_MULTIGRID && (rc = build_hierarchy(h, grid, coeffs))) return bail(rc);
     *out = h;
     return PCG_OK;
 }
@@ -1012,7 +1156,10 @@ int pcg_apply_A(pcg_t h, const double* x, double* y) {
 int pcg_precond(pcg_t h, const double* r, double* z) {
     if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
     if (!r || !z) return fail(h, PCG_ERR_INVALID_ARG, "r and z are required");
-    pcg::k_precond<double><<<h->grid, h->block, 0, h->stream>>>(h->view64(), r, z);
+    if (h->precond == PCG_PREC_MULTIGRID)
+        launch_vcycle(h, h->stream, h->mg_free, r, z, h->mg_t0);
+    else
+        pcg::k_precond<double><<<h->grid, h->block, 0, h->stream>>>(h->view64(), r, z);
     PCG_CK(h, cudaGetLastError());
     return PCG_OK;
 }
@@ -1103,6 +1250,14 @@ const char* pcg_last_error(pcg_t h) { return h ? h->err.c_str() : g_create_error
 void pcg_destroy(pcg_t h) {
     if (!h) return;
     if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
+    for (auto& l : h->mg) {
+        for (double* p : {l.r, l.z, l.t})
+            if (p) cudaFree(p);
+        pcg_destroy(l.h);
+    }
+    h->mg.clear();
+    if (h->mg_t0) cudaFree(h->mg_t0);
+    if (h->mg_free) cudaFree(h->mg_free);
     if (h->graph64) cudaGraphExecDestroy(h->graph64);
     if (h->graph32) cudaGraphExecDestroy(h->graph32);
     for (void* p : {(void*)h->u64, (void*)h->r64, (void*)h->z64, (void*)h->p64, (void*)h->q64, (void*)h->u32,

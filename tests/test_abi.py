@@ -45,9 +45,9 @@ def _create(p, **over):
     be, bp = pkg._dbl(p.beta_iface)
     g = pkg.pcg_grid_t(p.kind, p.n_x, p.n_y, p.n_z, 1, zp, 1.0, 1.0, p.lat0, p.lat1)
     c = pkg.pcg_coeffs_t(None, None, bp, p.lambda2)
-    for k, v in over.items():
-        setattr(g if hasattr(g, k) else c, k, v)
     o = pkg.pcg_opts_t(0, 0.0, 0, 0, 0, None)
+    for k, v in over.items():
+        setattr(g if hasattr(g, k) else (o if hasattr(o, k) else c), k, v)
     h = ctypes.c_void_p()
     lib = pkg.load_library()
     rc = lib.pcg_create(ctypes.byref(g), ctypes.byref(c), ctypes.byref(o), ctypes.byref(h))
@@ -58,6 +58,14 @@ def _create(p, **over):
                                          ("geometry", 7), ("lambda2", float("nan"))])
 def test_create_rejects_bad_arguments(lib, field, value):
     rc, h, msg, _ = _create(W.small_box(), **{field: value})
+    assert rc == pkg.PCG_ERR_INVALID_ARG and not h.value, (rc, msg)
+    assert msg
+
+
+@pytest.mark.parametrize("over", [{"preconditioner": 5}, {"preconditioner": 1, "precision": 1}, {"precision": 3}])
+def test_create_rejects_bad_options(lib, over):
+    # unknown preconditioner; multigrid is FP64 only; unknown precision
+    rc, h, msg, _ = _create(W.small_box(), **over)
     assert rc == pkg.PCG_ERR_INVALID_ARG and not h.value, (rc, msg)
     assert msg
 
@@ -96,7 +104,31 @@ def test_binding_refuses_missing_library(tmp_path):
         pkg._lib = saved
 
 
-def test_structs_match_header_layout():
-    # field order and sizes of the ctypes mirrors equal the C structs
-    assert ctypes.sizeof(pkg.pcg_stats_t) == 4 * 4 + 4 * 8
-    assert ctypes.sizeof(pkg.pcg_opts_t) == 8 + 8 + 4 + 4 + 4 + 4 + 8
+def test_structs_match_header_layout(tmp_path):
+    # size and field offsets of every ctypes mirror equal the C structs of
+    # include/pcg.h as the C compiler lays them out
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pcg_grid_t": pkg.pcg_grid_t, "pcg_coeffs_t": pkg.pcg_coeffs_t, "pcg_opts_t": pkg.pcg_opts_t,
+               "pcg_stats_t": pkg.pcg_stats_t}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pcg.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
