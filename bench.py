@@ -614,6 +614,29 @@ def main():
                      "fp32_ms_per_iteration": mp + ms, "fp32_iteration_gbs_algorithmic": it_gbs,
                      "fp32_iteration_hbm_frac": it_gbs / hbm_peak}
 
+    # the same FP64 solve with the multigrid V-cycle as preconditioner
+    multigrid = None
+    if not args.no_mixed:
+        with pkg.Solver(p, preconditioner="multigrid", stream=stream.cuda_stream) as sg:
+            for _ in range(2):
+                x.zero_()
+                sg.solve(b, x, tol=TOL, maxit=100000)
+            gt = []
+            for _ in range(max(1, min(args.steps, 3))):
+                flush.fill_(1.0)
+                x.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gst = sg.solve(b, x, tol=TOL, maxit=100000)
+                e1.record(stream)
+                e1.synchronize()
+                gt.append(e0.elapsed_time(e1))
+            multigrid = {"value": 1000.0 / statistics.mean(gt), "unit": "solves/s", "iterations": gst.iterations,
+                         "relres_recursive": gst.relres_recursive, "relres_true": gst.relres_true,
+                         "speedup_vs_line_fp64": (1000.0 / statistics.mean(gt)) / (1000.0 / ms_per_step),
+                         "gpu_launches_per_solve": sg.kernel_launches}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -637,7 +660,7 @@ def main():
                        "relres_true": stats.relres_true, "parallelism": f"replicas{world}",
                        "l2": "256 MB buffer written between timed steps; working set 5 x 67 MB"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
-            "cpu_baseline": cpu, "mixed": mixed,
+            "cpu_baseline": cpu, "mixed": mixed, "multigrid": multigrid,
         }
         print(json.dumps(line), flush=True)
     solver.close()

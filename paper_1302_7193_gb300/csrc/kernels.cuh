@@ -728,10 +728,10 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
 // column are the warps w0 .. w0 + nch - 1 of the block (lane = column);
 // r, q, z point at level 0 of the right-hand side.  The chunk's r and q are
 // read from rsrc / qsrc (level t of the chunk at t * sstride; null: from r
-// and q themselves).  Every thread of the block must call this (it holds two
-// block barriers); threads with col.valid false take part in the barriers
-// only.
-template <typename T, int LZ>
+// and q themselves); STORE_R = false leaves r unwritten.  Every thread of
+// the block must call this (it holds two block barriers); threads with
+// col.valid false take part in the barriers only.
+template <typename T, int LZ, bool STORE_R = true>
 __device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col<T>& col, int lane, int ch, int nch,
                                                   int w0, T* __restrict__ r, const T* __restrict__ q,
                                                   T* __restrict__ z, T alpha, Acc<T> (&acc)[2], T (*sh_y)[32],
@@ -793,7 +793,7 @@ __device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col
         for (int t = 0; t < LZ; ++t) {
             if (t < kn) {
                 const T rn = yv[t];
-                rb[t * pl] = rn;
+                if (STORE_R) rb[t * pl] = rn;
                 rr_chunk = fma(rn, rn, rr_chunk);
                 yl = fma(-ep, yl, rn) + yl;
                 cp = (t == 0) ? ep : fma(ep, T(1) - cp, cp);

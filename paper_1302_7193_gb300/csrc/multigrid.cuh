@@ -94,20 +94,26 @@ __global__ __launch_bounds__(NT) void k_mg_smooth(OpView<double> op, const doubl
     }
 }
 
-// t = r - A z (flux form, as k_apply)
+// t = r - A z (flux form, as k_apply).  blockIdx.z = rhs * ksplit + part:
+// part takes levels [part n_z / ksplit, (part + 1) n_z / ksplit) of every
+// column (small levels of the hierarchy have few columns, and a column's
+// levels are independent here apart from the flux carried from below, which
+// the part recomputes).
 __global__ __launch_bounds__(NT) void k_mg_resid(OpView<double> op, const double* __restrict__ r,
                                                  const double* __restrict__ z, double* __restrict__ t,
-                                                 const SolveState* __restrict__ st) {
-    const int rhs = blockIdx.z;
+                                                 const SolveState* __restrict__ st, int ksplit) {
+    const int rhs = blockIdx.z / ksplit;
+    const int part = blockIdx.z - rhs * ksplit;
     if (st[rhs].done) return;
     const Col<double> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
     if (!col.valid) return;
+    const int k0 = (int)((long long)part * op.nz / ksplit), k1 = (int)((long long)(part + 1) * op.nz / ksplit);
     const long long base = (long long)rhs * op.vol;
     const double* __restrict__ zb = z + base;
-    double zc = zb[col.c];
-    double fprev = 0.0;
+    double zc = zb[(long long)k0 * op.plane + col.c];
+    double fprev = k0 > 0 ? ldro(op.wv + k0 - 1) * (zb[(long long)(k0 - 1) * op.plane + col.c] - zc) : 0.0;
 #pragma unroll 4
-    for (int k = 0; k < op.nz; ++k) {
+    for (int k = k0; k < k1; ++k) {
         const double* zl = zb + (long long)k * op.plane;
         const double zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
         const double f = ldro(op.wv + k) * (zc - zu);
@@ -117,6 +123,35 @@ __global__ __launch_bounds__(NT) void k_mg_resid(OpView<double> op, const double
         t[o] = r[o] - az;
         fprev = f;
         zc = zu;
+    }
+}
+
+// tmp = M^{-1} rin on levels with few columns: the chunked (substructured)
+// Thomas solve of prec_chunked_body in FP64, one warp per 16-level chunk of
+// 32 columns of one row (block (32, n_z/16)), so that a column's work spreads
+// over several warps.  tmp may be rin (every chunk reads its levels first).
+__global__ __launch_bounds__(256) void k_mg_lsolve_chunked(OpView<double> op, const double* rin, double* tmp,
+                                                           const SolveState* __restrict__ st) {
+    __shared__ double sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
+    const int rhs = blockIdx.z;
+    if (st[rhs].done) return;
+    const int lane = threadIdx.x, ch = threadIdx.y, nch = blockDim.y;
+    const Col<double> col = make_col(op, blockIdx.x * 32 + lane, blockIdx.y);
+    const long long rb = (long long)rhs * op.vol;
+    Acc<double> acc[2];
+    // alpha = 0: the chunk's "updated residual" is rin itself, and it is not stored back
+    prec_chunked_body<double, 16, false>(op, col, lane, ch, nch, 0, const_cast<double*>(rin + rb), rin + rb,
+                                         tmp + rb, 0.0, acc, sh_y, sh_c, sh_z, sh_d);
+}
+
+// z = (acc ? z : 0) + omega m, elementwise over all right-hand sides
+__global__ void k_mg_axpy(const double* __restrict__ m, double* __restrict__ z, double omega, int acc, long long vol,
+                          int nrhs, const SolveState* __restrict__ st) {
+    const long long n = vol * nrhs;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int rhs = (int)(c / vol);
+        if (st[rhs].done) continue;
+        z[c] = acc ? fma(omega, m[c], z[c]) : omega * m[c];
     }
 }
 

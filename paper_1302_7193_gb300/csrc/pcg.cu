@@ -581,35 +581,56 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const double* r
     auto T = [&](int l) { return l == 0 ? t0 : h->mg[l - 1].t; };
     auto elems = [&](long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16); };
     int n = 0;
-    auto smooth_first = [&](int l, double omega) {       // z = omega M^{-1} r
+    // Levels with few columns spread each column's work over several threads:
+    // the residual over level chunks, the line solve in its chunked form (one
+    // warp per 16 levels) followed by the damped update.
+    auto few = [&](pcg_t hl) { return hl->plane * (long long)hl->nrhs < 16384 && hl->nz <= 128; };
+    auto ksplit = [&](pcg_t hl) {
+        int ks = 1;
+        while (hl->plane * (long long)hl->nrhs * ks < 32768 && ks < 32 && hl->nz / (2 * ks) >= 4) ks *= 2;
+        return ks;
+    };
+    auto resid = [&](int l) {                            // t = r - A z
         pcg_t hl = H(l);
-        pcg::k_mg_smooth<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), R(l), T(l), Z(l), omega, 0, st);
+        const int ks = ksplit(hl);
+        const dim3 g(hl->grid_c.x, hl->grid_c.y, hl->grid_c.z * ks);
+        pcg::k_mg_resid<<<g, hl->block_c, 0, s>>>(hl->view64(), R(l), Z(l), T(l), st, ks);
         ++n;
     };
-    auto smooth_more = [&](int l) {                      // z += omega M^{-1} (r - A z)
+    auto smooth = [&](int l, const double* rin, double omega, int acc) {   // z = (acc ? z : 0) + omega M^{-1} rin
         pcg_t hl = H(l);
-        pcg::k_mg_resid<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), R(l), Z(l), T(l), st);
-        pcg::k_mg_smooth<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), T(l), T(l), Z(l), h->mg_omega, 1, st);
-        n += 2;
+        if (few(hl)) {
+            const int nch = (hl->nz + 15) / 16;
+            pcg::k_mg_lsolve_chunked<<<dim3((hl->nx + 31) / 32, hl->ny, hl->nrhs), dim3(32, nch, 1), 0, s>>>(
+                hl->view64(), rin, T(l), st);
+            pcg::k_mg_axpy<<<elems(hl->ntot), 256, 0, s>>>(T(l), Z(l), omega, acc, hl->vol, hl->nrhs, st);
+            n += 2;
+        } else {
+            pcg::k_mg_smooth<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), rin, T(l), Z(l), omega, acc, st);
+            ++n;
+        }
+    };
+    auto smooth_first = [&](int l, double omega) { smooth(l, R(l), omega, 0); };   // z = omega M^{-1} r
+    auto smooth_more = [&](int l) {                      // z += omega M^{-1} (r - A z)
+        resid(l);
+        smooth(l, T(l), h->mg_omega, 1);
     };
     for (int l = 0; l + 1 < L; ++l) {
         smooth_first(l, h->mg_omega);
         for (int k = 1; k < h->mg_nu; ++k) smooth_more(l);
-        pcg_t hl = H(l), hc = H(l + 1);
-        pcg::k_mg_resid<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), R(l), Z(l), T(l), st);
+        pcg_t hc = H(l + 1);
+        resid(l);
         pcg::k_mg_restrict<<<elems(hc->ntot), 256, 0, s>>>(T(l), h->mg[l].r, hc->nx, hc->ny, hc->nz, hc->nrhs, st);
-        n += 2;
+        ++n;
     }
     const int c = L - 1;
     if (H(c)->plane == 1) {
         // one column: its block is all of A, solved with one step of
         // refinement (z += M^{-1} (r - A z)): without horizontal couplings the
         // block's condition number reaches 1e10 at strong anisotropy
-        pcg_t hl = H(c);
         smooth_first(c, 1.0);
-        pcg::k_mg_resid<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), R(c), Z(c), T(c), st);
-        pcg::k_mg_smooth<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), T(c), T(c), Z(c), 1.0, 1, st);
-        n += 2;
+        resid(c);
+        smooth(c, T(c), 1.0, 1);
     } else {
         smooth_first(c, h->mg_omega);
         for (int k = 1; k < h->mg_coarse; ++k) smooth_more(c);
