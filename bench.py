@@ -409,7 +409,7 @@ def run_multigrid(args, dev, pkg, W, torch):
     for name, p, rhs in cases:
         b = torch.from_numpy(np.ascontiguousarray(rhs(p)).ravel()).to(dev)
         res, xs = {}, {}
-        for pc in ("line", "multigrid"):
+        for pc in ("line", "multigrid", "multigrid-f32"):
             with pkg.Solver(p, preconditioner=pc, stream=stream.cuda_stream) as s:
                 x = torch.zeros_like(b)
                 s.solve(b, x, tol=TOL, maxit=200000)           # warm-up (graph capture)
@@ -427,7 +427,7 @@ def run_multigrid(args, dev, pkg, W, torch):
                 entry = {"solves_per_s": 1000.0 / ms, "ms": ms, "iterations": st.iterations,
                          "ms_per_iteration": ms / max(1, st.iterations), "relres_recursive": st.relres_recursive,
                          "relres_true": st.relres_true, "status": st.status_name}
-                if pc == "multigrid":
+                if pc != "line":
                     z = torch.empty_like(b)
                     s.precond(b, z)
                     e0 = torch.cuda.Event(enable_timing=True)
@@ -441,7 +441,9 @@ def run_multigrid(args, dev, pkg, W, torch):
                 res[pc] = entry
                 xs[pc] = x.clone()
         res["multigrid_speedup"] = res["multigrid"]["solves_per_s"] / res["line"]["solves_per_s"]
+        res["multigrid_f32_speedup"] = res["multigrid-f32"]["solves_per_s"] / res["line"]["solves_per_s"]
         res["relative_distance_of_solutions"] = float((xs["multigrid"] - xs["line"]).norm() / xs["line"].norm())
+        res["relative_distance_f32_cycle"] = float((xs["multigrid-f32"] - xs["line"]).norm() / xs["line"].norm())
         out["cases"][name] = res
         del b, xs
     out["value"] = out["cases"]["box256x256x128"]["multigrid"]["solves_per_s"]
@@ -614,28 +616,32 @@ def main():
                      "fp32_ms_per_iteration": mp + ms, "fp32_iteration_gbs_algorithmic": it_gbs,
                      "fp32_iteration_hbm_frac": it_gbs / hbm_peak}
 
-    # the same FP64 solve with the multigrid V-cycle as preconditioner
-    multigrid = None
+    # the same FP64 solve with the multigrid V-cycle as preconditioner, in FP64
+    # and in FP32 (the cycle only; the CG stays FP64)
+    multigrid = multigrid_f32 = None
     if not args.no_mixed:
-        with pkg.Solver(p, preconditioner="multigrid", stream=stream.cuda_stream) as sg:
-            for _ in range(2):
-                x.zero_()
-                sg.solve(b, x, tol=TOL, maxit=100000)
-            gt = []
-            for _ in range(max(1, min(args.steps, 3))):
-                flush.fill_(1.0)
-                x.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                gst = sg.solve(b, x, tol=TOL, maxit=100000)
-                e1.record(stream)
-                e1.synchronize()
-                gt.append(e0.elapsed_time(e1))
-            multigrid = {"value": 1000.0 / statistics.mean(gt), "unit": "solves/s", "iterations": gst.iterations,
-                         "relres_recursive": gst.relres_recursive, "relres_true": gst.relres_true,
-                         "speedup_vs_line_fp64": (1000.0 / statistics.mean(gt)) / (1000.0 / ms_per_step),
-                         "gpu_launches_per_solve": sg.kernel_launches}
+        mg = {}
+        for pc in ("multigrid", "multigrid-f32"):
+            with pkg.Solver(p, preconditioner=pc, stream=stream.cuda_stream) as sg:
+                for _ in range(2):
+                    x.zero_()
+                    sg.solve(b, x, tol=TOL, maxit=100000)
+                gt = []
+                for _ in range(max(1, min(args.steps, 3))):
+                    flush.fill_(1.0)
+                    x.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    gst = sg.solve(b, x, tol=TOL, maxit=100000)
+                    e1.record(stream)
+                    e1.synchronize()
+                    gt.append(e0.elapsed_time(e1))
+                mg[pc] = {"value": 1000.0 / statistics.mean(gt), "unit": "solves/s", "iterations": gst.iterations,
+                          "relres_recursive": gst.relres_recursive, "relres_true": gst.relres_true,
+                          "speedup_vs_line_fp64": (1000.0 / statistics.mean(gt)) / (1000.0 / ms_per_step),
+                          "gpu_launches_per_solve": sg.kernel_launches}
+        multigrid, multigrid_f32 = mg["multigrid"], mg["multigrid-f32"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -661,6 +667,7 @@ def main():
                        "l2": "256 MB buffer written between timed steps; working set 5 x 67 MB"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
             "cpu_baseline": cpu, "mixed": mixed, "multigrid": multigrid,
+            "multigrid_f32_cycle": multigrid_f32,
         }
         print(json.dumps(line), flush=True)
     solver.close()

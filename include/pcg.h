@@ -69,7 +69,7 @@ enum pcg_precision {
 };
 enum pcg_preconditioner {
     PCG_PREC_LINE = 0,         /* vertical-line preconditioner M = block-diag(A) (Section 4.1) */
-    PCG_PREC_MULTIGRID = 1     /* one V-cycle of geometric multigrid with vertical line smoothing (the
+    PCG_PREC_MULTIGRID = 1,    /* one V-cycle of geometric multigrid with vertical line smoothing (the
                                   solver Section 8 names as the next step): n_x, n_y halved per level
                                   while both are even, the vertical grid kept; each level the same
                                   discretisation (alpha on a coarse face = mean of its two fine faces);
@@ -78,6 +78,8 @@ enum pcg_preconditioner {
                                   after the coarse correction; coarsest level: its column block
                                   (with one refinement step) if it is one column, else 8 smoothing
                                   sweeps.  PCG_FP64 only. */
+    PCG_PREC_MULTIGRID_F32 = 2 /* the same V-cycle computed in FP32 (r rounded to FP32 on the way in, z
+                                  widened on the way out) inside the FP64 CG.  PCG_FP64 only. */
 };
 
 typedef struct pcg_ctx* pcg_t;

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libpcg.so")
 PCG_OK, PCG_ERR_INVALID_ARG, PCG_ERR_OOM, PCG_ERR_CUDA, PCG_NOT_CONVERGED, PCG_BREAKDOWN, PCG_TIMEOUT, PCG_PENDING = range(8)
 PCG_GEOM_BOX, PCG_GEOM_LATLON, PCG_GEOM_CUBED_PANEL = 0, 1, 2
 PCG_FP64, PCG_MIXED = 0, 1
-PCG_PREC_LINE, PCG_PREC_MULTIGRID = 0, 1
+PCG_PREC_LINE, PCG_PREC_MULTIGRID, PCG_PREC_MULTIGRID_F32 = 0, 1, 2
 STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "not_converged", 5: "breakdown", 6: "timeout",
                 7: "pending"}
 
@@ -209,7 +209,8 @@ class Solver:
         prec = {"fp64": PCG_FP64, "mixed": PCG_MIXED}[precision]
         self.precision = precision
         self.preconditioner = preconditioner
-        pc = {"line": PCG_PREC_LINE, "multigrid": PCG_PREC_MULTIGRID}[preconditioner]
+        pc = {"line": PCG_PREC_LINE, "multigrid": PCG_PREC_MULTIGRID,
+              "multigrid-f32": PCG_PREC_MULTIGRID_F32}[preconditioner]
         self.h, self._keep = pcg_create(problem, nrhs=nrhs, precision=prec, preconditioner=pc, **kw)
 
     def _check(self, rc: int, allow=(PCG_OK,)):

@@ -3,15 +3,18 @@
 // A V-cycle on a hierarchy of horizontally coarsened grids (the solver the
 // paper names as the next step, Section 8): damped block-Jacobi smoothing
 // with the column blocks of each level (Thomas recurrences in the excess
-// form of kernels.cuh), residuals in flux form, restriction by summing the four fine
-// cells of a coarse cell and prolongation by its transpose.
+// form of kernels.cuh), residuals in flux form, restriction by summing the
+// four fine cells of a coarse cell and prolongation by its transpose.  The
+// V-cycle kernels are templated on the precision T of the cycle (FP64, or
+// FP32 inside the FP64 CG of PCG_PREC_MULTIGRID_F32); the CG steps around
+// it are FP64.
 #pragma once
 #include "kernels.cuh"
 
 namespace pcg {
 
 // ---------------------------------------------------------------------------
-// Multigrid V-cycle (FP64) on a hierarchy of horizontally coarsened grids:
+// Multigrid V-cycle on a hierarchy of horizontally coarsened grids:
 // damped block-Jacobi smoothing with the column blocks, residuals, and the
 // transfers R (sum of the four fine cells of a coarse cell) and P = R^T.
 // Every kernel skips a right-hand side whose solve has stopped (st[rhs].done).
@@ -24,30 +27,31 @@ namespace pcg {
 // because on coarse levels the vertical couplings grow 4x per level against
 // the horizontal ones, the excess 1 - W/D falls towards 1e-7 and a stored
 // ratio W/D would carry it with a relative error of 2^-53 / (1 - W/D).
-__global__ __launch_bounds__(NT) void k_mg_smooth(OpView<double> op, const double* rin, double* tmp, double* z,
-                                                  double omega, int acc, const SolveState* __restrict__ st) {
+template <typename T>
+__global__ __launch_bounds__(NT) void k_mg_smooth(OpView<T> op, const T* rin, T* tmp, T* z, T omega, int acc,
+                                                  const SolveState* __restrict__ st) {
     const int rhs = blockIdx.z;
     if (st[rhs].done) return;
-    const Col<double> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
     if (!col.valid) return;
     const long long base = (long long)rhs * op.vol + col.c;
     const long long pl = op.plane, fs = op.ncls;
-    const double* fg = op.fg + col.cls;
-    const double* fe = op.fe + col.cls;
+    const T* fg = op.fg + col.cls;
+    const T* fe = op.fe + col.cls;
     const int nz = op.nz;
     // the loads of the next PB levels are issued before the current PB levels
     // are stored (tmp may be rin, and z is read and written)
     constexpr int PB = 8;
-    double y = 0.0, eprev = 0.0;
-    double ra[PB];
+    T y = T(0), eprev = T(0);
+    T ra[PB];
 #pragma unroll
-    for (int t = 0; t < PB; ++t) ra[t] = t < nz ? rin[base + t * pl] : 0.0;
+    for (int t = 0; t < PB; ++t) ra[t] = t < nz ? rin[base + t * pl] : T(0);
     for (int k0 = 0; k0 < nz; k0 += PB) {
-        double rn[PB];
+        T rn[PB];
 #pragma unroll
         for (int t = 0; t < PB; ++t) {
             const int k = k0 + PB + t;
-            rn[t] = k < nz ? rin[base + k * pl] : 0.0;
+            rn[t] = k < nz ? rin[base + k * pl] : T(0);
         }
 #pragma unroll
         for (int t = 0; t < PB; ++t) {
@@ -61,22 +65,22 @@ __global__ __launch_bounds__(NT) void k_mg_smooth(OpView<double> op, const doubl
 #pragma unroll
         for (int t = 0; t < PB; ++t) ra[t] = rn[t];
     }
-    double zn = 0.0;
-    double ya[PB], za[PB];
+    T zn = T(0);
+    T ya[PB], za[PB];
     const int kt = nz - 1;
 #pragma unroll
     for (int t = 0; t < PB; ++t) {
         const int k = kt - t;
-        ya[t] = k >= 0 ? tmp[base + k * pl] : 0.0;
-        za[t] = (acc && k >= 0) ? z[base + k * pl] : 0.0;
+        ya[t] = k >= 0 ? tmp[base + k * pl] : T(0);
+        za[t] = (acc && k >= 0) ? z[base + k * pl] : T(0);
     }
     for (int k0 = kt; k0 >= 0; k0 -= PB) {
-        double yn[PB], zn_[PB];
+        T yn[PB], zn_[PB];
 #pragma unroll
         for (int t = 0; t < PB; ++t) {
             const int k = k0 - PB - t;
-            yn[t] = k >= 0 ? tmp[base + k * pl] : 0.0;
-            zn_[t] = (acc && k >= 0) ? z[base + k * pl] : 0.0;
+            yn[t] = k >= 0 ? tmp[base + k * pl] : T(0);
+            zn_[t] = (acc && k >= 0) ? z[base + k * pl] : T(0);
         }
 #pragma unroll
         for (int t = 0; t < PB; ++t) {
@@ -99,26 +103,26 @@ __global__ __launch_bounds__(NT) void k_mg_smooth(OpView<double> op, const doubl
 // column (small levels of the hierarchy have few columns, and a column's
 // levels are independent here apart from the flux carried from below, which
 // the part recomputes).
-__global__ __launch_bounds__(NT) void k_mg_resid(OpView<double> op, const double* __restrict__ r,
-                                                 const double* __restrict__ z, double* __restrict__ t,
-                                                 const SolveState* __restrict__ st, int ksplit) {
+template <typename T>
+__global__ __launch_bounds__(NT) void k_mg_resid(OpView<T> op, const T* __restrict__ r, const T* __restrict__ z,
+                                                 T* __restrict__ t, const SolveState* __restrict__ st, int ksplit) {
     const int rhs = blockIdx.z / ksplit;
     const int part = blockIdx.z - rhs * ksplit;
     if (st[rhs].done) return;
-    const Col<double> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+    const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
     if (!col.valid) return;
     const int k0 = (int)((long long)part * op.nz / ksplit), k1 = (int)((long long)(part + 1) * op.nz / ksplit);
     const long long base = (long long)rhs * op.vol;
-    const double* __restrict__ zb = z + base;
-    double zc = zb[(long long)k0 * op.plane + col.c];
-    double fprev = k0 > 0 ? ldro(op.wv + k0 - 1) * (zb[(long long)(k0 - 1) * op.plane + col.c] - zc) : 0.0;
+    const T* __restrict__ zb = z + base;
+    T zc = zb[(long long)k0 * op.plane + col.c];
+    T fprev = k0 > 0 ? ldro(op.wv + k0 - 1) * (zb[(long long)(k0 - 1) * op.plane + col.c] - zc) : T(0);
 #pragma unroll 4
     for (int k = k0; k < k1; ++k) {
-        const double* zl = zb + (long long)k * op.plane;
-        const double zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
-        const double f = ldro(op.wv + k) * (zc - zu);
-        const double hz = horiz(col, zl, zc);
-        const double az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+        const T* zl = zb + (long long)k * op.plane;
+        const T zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
+        const T f = ldro(op.wv + k) * (zc - zu);
+        const T hz = horiz(col, zl, zc);
+        const T az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
         const long long o = base + (long long)k * op.plane + col.c;
         t[o] = r[o] - az;
         fprev = f;
@@ -130,23 +134,25 @@ __global__ __launch_bounds__(NT) void k_mg_resid(OpView<double> op, const double
 // Thomas solve of prec_chunked_body in FP64, one warp per 16-level chunk of
 // 32 columns of one row (block (32, n_z/16)), so that a column's work spreads
 // over several warps.  tmp may be rin (every chunk reads its levels first).
-__global__ __launch_bounds__(256) void k_mg_lsolve_chunked(OpView<double> op, const double* rin, double* tmp,
+template <typename T>
+__global__ __launch_bounds__(256) void k_mg_lsolve_chunked(OpView<T> op, const T* rin, T* tmp,
                                                            const SolveState* __restrict__ st) {
-    __shared__ double sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
+    __shared__ T sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
     const int rhs = blockIdx.z;
     if (st[rhs].done) return;
     const int lane = threadIdx.x, ch = threadIdx.y, nch = blockDim.y;
-    const Col<double> col = make_col(op, blockIdx.x * 32 + lane, blockIdx.y);
+    const Col<T> col = make_col(op, blockIdx.x * 32 + lane, blockIdx.y);
     const long long rb = (long long)rhs * op.vol;
-    Acc<double> acc[2];
+    Acc<T> acc[2];
     // alpha = 0: the chunk's "updated residual" is rin itself, and it is not stored back
-    prec_chunked_body<double, 16, false>(op, col, lane, ch, nch, 0, const_cast<double*>(rin + rb), rin + rb,
-                                         tmp + rb, 0.0, acc, sh_y, sh_c, sh_z, sh_d);
+    prec_chunked_body<T, 16, false>(op, col, lane, ch, nch, 0, const_cast<T*>(rin + rb), rin + rb, tmp + rb, T(0),
+                                    acc, sh_y, sh_c, sh_z, sh_d);
 }
 
 // z = (acc ? z : 0) + omega m, elementwise over all right-hand sides
-__global__ void k_mg_axpy(const double* __restrict__ m, double* __restrict__ z, double omega, int acc, long long vol,
-                          int nrhs, const SolveState* __restrict__ st) {
+template <typename T>
+__global__ void k_mg_axpy(const T* __restrict__ m, T* __restrict__ z, T omega, int acc, long long vol, int nrhs,
+                          const SolveState* __restrict__ st) {
     const long long n = vol * nrhs;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int rhs = (int)(c / vol);
@@ -157,8 +163,9 @@ __global__ void k_mg_axpy(const double* __restrict__ m, double* __restrict__ z, 
 
 // rc = R tf: every coarse cell (rhs, k, J, I) sums the fine cells
 // (2J, 2I), (2J, 2I+1), (2J+1, 2I), (2J+1, 2I+1) of the same level k.
-__global__ void k_mg_restrict(const double* __restrict__ tf, double* __restrict__ rc, int nxc, int nyc, int nz,
-                              int nrhs, const SolveState* __restrict__ st) {
+template <typename T>
+__global__ void k_mg_restrict(const T* __restrict__ tf, T* __restrict__ rc, int nxc, int nyc, int nz, int nrhs,
+                              const SolveState* __restrict__ st) {
     const long long planec = (long long)nxc * nyc, volc = planec * nz, n = volc * nrhs;
     const long long nxf = 2LL * nxc, planef = 4 * planec;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -166,14 +173,15 @@ __global__ void k_mg_restrict(const double* __restrict__ tf, double* __restrict_
         if (st[rhs].done) continue;
         const long long rem = c - rhs * volc;
         const long long k = rem / planec, jc = (rem - k * planec) / nxc, ic = rem - k * planec - jc * nxc;
-        const double* f = tf + rhs * (volc * 4) + k * planef + (2 * jc) * nxf + 2 * ic;
+        const T* f = tf + rhs * (volc * 4) + k * planef + (2 * jc) * nxf + 2 * ic;
         rc[c] = ((f[0] + f[1]) + f[nxf]) + f[nxf + 1];
     }
 }
 
 // zf += P zc: every fine cell adds its coarse cell's value.
-__global__ void k_mg_prolong(const double* __restrict__ zc, double* __restrict__ zf, int nxf, int nyf, int nz,
-                             int nrhs, const SolveState* __restrict__ st) {
+template <typename T>
+__global__ void k_mg_prolong(const T* __restrict__ zc, T* __restrict__ zf, int nxf, int nyf, int nz, int nrhs,
+                             const SolveState* __restrict__ st) {
     const long long planef = (long long)nxf * nyf, volf = planef * nz, n = volf * nrhs;
     const int nxc = nxf / 2;
     const long long planec = planef / 4, volc = planec * nz;
@@ -183,6 +191,18 @@ __global__ void k_mg_prolong(const double* __restrict__ zc, double* __restrict__
         const long long rem = c - rhs * volf;
         const long long k = rem / planef, j = (rem - k * planef) / nxf, i = rem - k * planef - j * nxf;
         zf[c] += zc[rhs * volc + k * planec + (j / 2) * nxc + i / 2];
+    }
+}
+
+// a <-> b between the FP64 CG and an FP32 V-cycle, elementwise over all right-hand sides
+template <typename TA, typename TB>
+__global__ void k_mg_convert(const TA* __restrict__ a, TB* __restrict__ b, long long vol, int nrhs,
+                             const SolveState* __restrict__ st) {
+    const long long n = vol * nrhs;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int rhs = (int)(c / vol);
+        if (st[rhs].done) continue;
+        b[c] = (TB)a[c];
     }
 }
 

@@ -106,11 +106,14 @@ struct pcg_ctx {
     // multigrid preconditioner (PCG_PREC_MULTIGRID): coarse levels 1..L-1
     struct MGLevel {
         pcg_ctx* h = nullptr;             // the level's own handle (tables, factors, launch shapes)
-        double *r = nullptr, *z = nullptr, *t = nullptr;   // right-hand side, correction, scratch
+        double *r = nullptr, *z = nullptr, *t = nullptr;   // right-hand side, correction, scratch (FP64 cycle)
+        float *rf = nullptr, *zf = nullptr, *tf = nullptr; // the same for an FP32 cycle
     };
     int precond = PCG_PREC_LINE;
     std::vector<MGLevel> mg;
     double* mg_t0 = nullptr;              // scratch of level 0
+    float *mg_r0f = nullptr, *mg_z0f = nullptr, *mg_t0f = nullptr;   // level 0 of an FP32 cycle
+    bool mg_f32 = false;                  // PCG_PREC_MULTIGRID_F32: the V-cycle in FP32
     SolveState* mg_free = nullptr;        // all-active states for a V-cycle outside a solve
     int mg_nu = 1, mg_coarse = 8;
     double mg_omega = 0.8;
@@ -570,15 +573,28 @@ void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, 
 #undef PCG_SPMV_CH
 }
 
-// One V-cycle z0 = B r0 (PCG_PREC_MULTIGRID) on stream s: level 0 is the
-// handle itself (scratch t0), levels 1.. are h->mg.  Returns the number of
-// kernels launched.  st: per-rhs states (a stopped rhs is skipped).
-int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const double* r0, double* z0, double* t0) {
+// One V-cycle z0 = B r0 (PCG_PREC_MULTIGRID) on stream s, in precision V:
+// level 0 is the handle itself (scratch t0), levels 1.. are h->mg.  Returns
+// the number of kernels launched.  st: per-rhs states (a stopped rhs is
+// skipped).
+template <typename V>
+OpView<V> level_view(pcg_t hl) {
+    if constexpr (sizeof(V) == 8) return hl->view64();
+    else return hl->view32();
+}
+
+template <typename V>
+int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V* z0, V* t0) {
     const int L = (int)h->mg.size() + 1;
     auto H = [&](int l) { return l == 0 ? h : h->mg[l - 1].h; };
-    auto R = [&](int l) -> const double* { return l == 0 ? r0 : h->mg[l - 1].r; };
-    auto Z = [&](int l) { return l == 0 ? z0 : h->mg[l - 1].z; };
-    auto T = [&](int l) { return l == 0 ? t0 : h->mg[l - 1].t; };
+    auto lv = [&](int l, double* d, float* f) -> V* {
+        (void)d; (void)f;
+        if constexpr (sizeof(V) == 8) return d; else return f;
+    };
+    auto R = [&](int l) -> const V* { return l == 0 ? r0 : lv(l, h->mg[l - 1].r, h->mg[l - 1].rf); };
+    auto Z = [&](int l) -> V* { return l == 0 ? z0 : lv(l, h->mg[l - 1].z, h->mg[l - 1].zf); };
+    auto T = [&](int l) -> V* { return l == 0 ? t0 : lv(l, h->mg[l - 1].t, h->mg[l - 1].tf); };
+    const V omega = (V)h->mg_omega;
     auto elems = [&](long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16); };
     int n = 0;
     // Levels with few columns spread each column's work over several threads:
@@ -594,33 +610,34 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const double* r
         pcg_t hl = H(l);
         const int ks = ksplit(hl);
         const dim3 g(hl->grid_c.x, hl->grid_c.y, hl->grid_c.z * ks);
-        pcg::k_mg_resid<<<g, hl->block_c, 0, s>>>(hl->view64(), R(l), Z(l), T(l), st, ks);
+        pcg::k_mg_resid<V><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
         ++n;
     };
-    auto smooth = [&](int l, const double* rin, double omega, int acc) {   // z = (acc ? z : 0) + omega M^{-1} rin
+    auto smooth = [&](int l, const V* rin, V om, int acc) {   // z = (acc ? z : 0) + omega M^{-1} rin
         pcg_t hl = H(l);
         if (few(hl)) {
             const int nch = (hl->nz + 15) / 16;
-            pcg::k_mg_lsolve_chunked<<<dim3((hl->nx + 31) / 32, hl->ny, hl->nrhs), dim3(32, nch, 1), 0, s>>>(
-                hl->view64(), rin, T(l), st);
-            pcg::k_mg_axpy<<<elems(hl->ntot), 256, 0, s>>>(T(l), Z(l), omega, acc, hl->vol, hl->nrhs, st);
+            pcg::k_mg_lsolve_chunked<V><<<dim3((hl->nx + 31) / 32, hl->ny, hl->nrhs), dim3(32, nch, 1), 0, s>>>(
+                level_view<V>(hl), rin, T(l), st);
+            pcg::k_mg_axpy<V><<<elems(hl->ntot), 256, 0, s>>>(T(l), Z(l), om, acc, hl->vol, hl->nrhs, st);
             n += 2;
         } else {
-            pcg::k_mg_smooth<<<hl->grid_c, hl->block_c, 0, s>>>(hl->view64(), rin, T(l), Z(l), omega, acc, st);
+            pcg::k_mg_smooth<V><<<hl->grid_c, hl->block_c, 0, s>>>(level_view<V>(hl), rin, T(l), Z(l), om, acc, st);
             ++n;
         }
     };
-    auto smooth_first = [&](int l, double omega) { smooth(l, R(l), omega, 0); };   // z = omega M^{-1} r
+    auto smooth_first = [&](int l, V om) { smooth(l, R(l), om, 0); };   // z = omega M^{-1} r
     auto smooth_more = [&](int l) {                      // z += omega M^{-1} (r - A z)
         resid(l);
-        smooth(l, T(l), h->mg_omega, 1);
+        smooth(l, T(l), omega, 1);
     };
     for (int l = 0; l + 1 < L; ++l) {
-        smooth_first(l, h->mg_omega);
+        smooth_first(l, omega);
         for (int k = 1; k < h->mg_nu; ++k) smooth_more(l);
         pcg_t hc = H(l + 1);
         resid(l);
-        pcg::k_mg_restrict<<<elems(hc->ntot), 256, 0, s>>>(T(l), h->mg[l].r, hc->nx, hc->ny, hc->nz, hc->nrhs, st);
+        pcg::k_mg_restrict<V><<<elems(hc->ntot), 256, 0, s>>>(T(l), const_cast<V*>(R(l + 1)), hc->nx, hc->ny, hc->nz,
+                                                             hc->nrhs, st);
         ++n;
     }
     const int c = L - 1;
@@ -628,16 +645,16 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const double* r
         // one column: its block is all of A, solved with one step of
         // refinement (z += M^{-1} (r - A z)): without horizontal couplings the
         // block's condition number reaches 1e10 at strong anisotropy
-        smooth_first(c, 1.0);
+        smooth_first(c, V(1));
         resid(c);
-        smooth(c, T(c), 1.0, 1);
+        smooth(c, T(c), V(1), 1);
     } else {
-        smooth_first(c, h->mg_omega);
+        smooth_first(c, omega);
         for (int k = 1; k < h->mg_coarse; ++k) smooth_more(c);
     }
     for (int l = L - 2; l >= 0; --l) {
         pcg_t hl = H(l);
-        pcg::k_mg_prolong<<<elems(hl->ntot), 256, 0, s>>>(Z(l + 1), Z(l), hl->nx, hl->ny, hl->nz, hl->nrhs, st);
+        pcg::k_mg_prolong<V><<<elems(hl->ntot), 256, 0, s>>>(Z(l + 1), Z(l), hl->nx, hl->ny, hl->nz, hl->nrhs, st);
         ++n;
         for (int k = 0; k < h->mg_nu; ++k) smooth_more(l);
     }
@@ -650,6 +667,9 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const double* r
 int build_hierarchy(pcg_t h, const pcg_grid_t* grid, const pcg_coeffs_t* coeffs) {
     int rc;
     if ((rc = dmalloc(h, &h->mg_t0, (size_t)h->ntot))) return rc;
+    if (h->mg_f32)
+        for (float** p : {&h->mg_r0f, &h->mg_z0f, &h->mg_t0f})
+            if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
     if ((rc = dmalloc(h, &h->mg_free, h->nrhs))) return rc;
     PCG_CK(h, cudaMemsetAsync(h->mg_free, 0, sizeof(SolveState) * h->nrhs, h->stream));
     pcg_grid_t g = *grid;
@@ -686,8 +706,13 @@ int build_hierarchy(pcg_t h, const pcg_grid_t* grid, const pcg_coeffs_t* coeffs)
         if (rc) return fail(h, rc, "multigrid level " + std::to_string(h->mg.size() + 1) + ": " + g_create_error);
         h->mg.push_back(pcg_ctx::MGLevel{});
         h->mg.back().h = hc;
-        for (double** p : {&h->mg.back().r, &h->mg.back().z, &h->mg.back().t})
-            if ((rc = dmalloc(h, p, (size_t)hc->ntot))) return rc;
+        if (h->mg_f32) {
+            for (float** p : {&h->mg.back().rf, &h->mg.back().zf, &h->mg.back().tf})
+                if ((rc = dmalloc(h, p, (size_t)hc->ntot))) return rc;
+        } else {
+            for (double** p : {&h->mg.back().r, &h->mg.back().z, &h->mg.back().t})
+                if ((rc = dmalloc(h, p, (size_t)hc->ntot))) return rc;
+        }
         ae.swap(aec);
         an.swap(anc);
     }
@@ -699,7 +724,14 @@ int build_hierarchy(pcg_t h, const pcg_grid_t* grid, const pcg_coeffs_t* coeffs)
 int launch_mg_pass(pcg_t h, cudaStream_t s) {
     const unsigned g = (unsigned)std::min<long long>((h->ntot + 255) / 256, 152LL * 16);
     pcg::k_mg_rupdate<<<g, 256, 0, s>>>(h->r64, h->q64, h->vol, h->nrhs, h->st);
-    int n = 1 + launch_vcycle(h, s, h->st, h->r64, h->z64, h->mg_t0);
+    int n = 1;
+    if (h->mg_f32) {
+        pcg::k_mg_convert<double, float><<<g, 256, 0, s>>>(h->r64, h->mg_r0f, h->vol, h->nrhs, h->st);
+        n += 2 + launch_vcycle<float>(h, s, h->st, h->mg_r0f, h->mg_z0f, h->mg_t0f);
+        pcg::k_mg_convert<float, double><<<g, 256, 0, s>>>(h->mg_z0f, h->z64, h->vol, h->nrhs, h->st);
+    } else {
+        n += launch_vcycle<double>(h, s, h->st, h->r64, h->z64, h->mg_t0);
+    }
     pcg::k_mg_dots<<<h->grid_c, h->block_c, 0, s>>>(h->view64(), h->r64, h->z64, h->st, h->partials, h->counters,
                                                     h->nblk_c);
     launch_spmv<double>(h, s, h->view64(), h->u64, h->p64, h->q64, h->z64, h->st);
@@ -975,10 +1007,12 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG, "unknown precision");
     }
-    if (h->precond != PCG_PREC_LINE && h->precond != PCG_PREC_MULTIGRID) {
+    if (h->precond != PCG_PREC_LINE && h->precond != PCG_PREC_MULTIGRID && h->precond != PCG_PREC_MULTIGRID_F32) {
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG, "unknown preconditioner");
     }
+    h->mg_f32 = h->precond == PCG_PREC_MULTIGRID_F32;
+    if (h->mg_f32) h->precond = PCG_PREC_MULTIGRID;
     if (h->precond == PCG_PREC_MULTIGRID && h->precision != PCG_FP64) {
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG, "the multigrid preconditioner is available with PCG_FP64 only");
@@ -1177,8 +1211,13 @@ int pcg_apply_A(pcg_t h, const double* x, double* y) {
 int pcg_precond(pcg_t h, const double* r, double* z) {
     if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
     if (!r || !z) return fail(h, PCG_ERR_INVALID_ARG, "r and z are required");
-    if (h->precond == PCG_PREC_MULTIGRID)
-        launch_vcycle(h, h->stream, h->mg_free, r, z, h->mg_t0);
+    if (h->precond == PCG_PREC_MULTIGRID && h->mg_f32) {
+        const unsigned g = (unsigned)std::min<long long>((h->ntot + 255) / 256, 152LL * 16);
+        pcg::k_mg_convert<double, float><<<g, 256, 0, h->stream>>>(r, h->mg_r0f, h->vol, h->nrhs, h->mg_free);
+        launch_vcycle<float>(h, h->stream, h->mg_free, h->mg_r0f, h->mg_z0f, h->mg_t0f);
+        pcg::k_mg_convert<float, double><<<g, 256, 0, h->stream>>>(h->mg_z0f, z, h->vol, h->nrhs, h->mg_free);
+    } else if (h->precond == PCG_PREC_MULTIGRID)
+        launch_vcycle<double>(h, h->stream, h->mg_free, r, z, h->mg_t0);
     else
         pcg::k_precond<double><<<h->grid, h->block, 0, h->stream>>>(h->view64(), r, z);
     PCG_CK(h, cudaGetLastError());
@@ -1272,12 +1311,14 @@ void pcg_destroy(pcg_t h) {
     if (!h) return;
     if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
     for (auto& l : h->mg) {
-        for (double* p : {l.r, l.z, l.t})
+        for (void* p : {(void*)l.r, (void*)l.z, (void*)l.t, (void*)l.rf, (void*)l.zf, (void*)l.tf})
             if (p) cudaFree(p);
         pcg_destroy(l.h);
     }
     h->mg.clear();
     if (h->mg_t0) cudaFree(h->mg_t0);
+    for (void* p : {(void*)h->mg_r0f, (void*)h->mg_z0f, (void*)h->mg_t0f})
+        if (p) cudaFree(p);
     if (h->mg_free) cudaFree(h->mg_free);
     if (h->graph64) cudaGraphExecDestroy(h->graph64);
     if (h->graph32) cudaGraphExecDestroy(h->graph32);
