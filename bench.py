@@ -470,6 +470,9 @@ def main():
                     help="serve: the full request mix, or only requests of at most 128 x 128 x 64 at 10x the rate")
     ap.add_argument("--serve-compare", action="store_true",
                     help="serve: also solve the same requests one at a time with the FP64 and mixed solvers")
+    ap.add_argument("--profile-vcycle", choices=["fp64", "fp32"], default=None,
+                    help="run five multigrid V-cycles (pcg_precond) on the 256x256x128 box and print the mean ms "
+                         "per cycle of the last four (a small case for ncu)")
     ap.add_argument("--profile-sweeps", choices=["fp64", "mixed"], default=None,
                     help="profiling case: 3 passes of the fused sweeps on the benchmark grid, then exit")
     args = ap.parse_args()
@@ -497,6 +500,23 @@ def main():
         return
     if args.workload != "box256":
         run_other_workload(args, dev, pkg, W, torch)
+        return
+    if args.profile_vcycle:
+        p = W.medium_box()
+        rp = torch.from_numpy(W.medium_box_rhs(p).ravel()).to(dev)
+        pc = {"fp64": "multigrid", "fp32": "multigrid-f32"}[args.profile_vcycle]
+        stream = torch.cuda.current_stream(dev)
+        with pkg.Solver(p, preconditioner=pc, stream=stream.cuda_stream) as s:
+            z = torch.empty_like(rp)
+            s.precond(rp, z)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(4):
+                s.precond(rp, z)
+            e1.record(stream)
+            e1.synchronize()
+            print(json.dumps({"vcycle": pc, "ms": e0.elapsed_time(e1) / 4}))
         return
     if args.profile_sweeps:
         p = W.medium_box()

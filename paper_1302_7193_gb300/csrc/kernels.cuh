@@ -731,13 +731,15 @@ __global__ __launch_bounds__(NT) void k_sweep_spmv(OpView<T> op, T* __restrict__
 // and q themselves); STORE_R = false leaves r unwritten.  Every thread of
 // the block must call this (it holds two block barriers); threads with
 // col.valid false take part in the barriers only.
-template <typename T, int LZ, bool STORE_R = true>
+// ZMODE: how the solution m = M^{-1} (r - alpha q) is stored: z = m (0),
+// z = omega m (1) or z += omega m (2, a damped smoothing step).
+template <typename T, int LZ, bool STORE_R = true, int ZMODE = 0>
 __device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col<T>& col, int lane, int ch, int nch,
                                                   int w0, T* __restrict__ r, const T* __restrict__ q,
                                                   T* __restrict__ z, T alpha, Acc<T> (&acc)[2], T (*sh_y)[32],
                                                   T (*sh_c)[32], T (*sh_z)[32], T (*sh_d)[32],
                                                   const T* rsrc = nullptr, const T* qsrc = nullptr,
-                                                  int sstride = 0) {
+                                                  int sstride = 0, T omega = T(1)) {
     const int k0 = ch * LZ;
     const int kn = min(LZ, op.nz - k0);          // levels in this chunk (<= 0: none)
     const bool act = col.valid && kn > 0;
@@ -851,7 +853,10 @@ __device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col
                 const T e = ev[t] * gv[t];
                 dp = first ? e : fma(e, T(1) - dp, dp);
                 first = false;
-                zb[t * pl] = fma(-dp, Z, yv[t]) + Z;
+                const T m = fma(-dp, Z, yv[t]) + Z;
+                if constexpr (ZMODE == 0) zb[t * pl] = m;
+                else if constexpr (ZMODE == 1) zb[t * pl] = omega * m;
+                else zb[t * pl] = fma(omega, m, zb[t * pl]);
             }
         }
     }

@@ -100,10 +100,11 @@ __global__ __launch_bounds__(NT) void k_mg_smooth(OpView<T> op, const T* rin, T*
 
 // t = r - A z (flux form, as k_apply).  blockIdx.z = rhs * ksplit + part:
 // part takes levels [part n_z / ksplit, (part + 1) n_z / ksplit) of every
-// column (small levels of the hierarchy have few columns, and a column's
-// levels are independent here apart from the flux carried from below, which
-// the part recomputes).
-template <typename T>
+// column (a column's levels are independent here apart from the flux carried
+// from below, which the part recomputes), so that enough threads run to keep
+// the loads in flight.  Each thread issues the loads of its next PB levels
+// (the column, its four neighbours, r) before it computes the current PB.
+template <typename T, int PB>
 __global__ __launch_bounds__(NT) void k_mg_resid(OpView<T> op, const T* __restrict__ r, const T* __restrict__ z,
                                                  T* __restrict__ t, const SolveState* __restrict__ st, int ksplit) {
     const int rhs = blockIdx.z / ksplit;
@@ -111,31 +112,68 @@ __global__ __launch_bounds__(NT) void k_mg_resid(OpView<T> op, const T* __restri
     if (st[rhs].done) return;
     const Col<T> col = make_col(op, blockIdx.x * BX + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
     if (!col.valid) return;
-    const int k0 = (int)((long long)part * op.nz / ksplit), k1 = (int)((long long)(part + 1) * op.nz / ksplit);
-    const long long base = (long long)rhs * op.vol;
+    const int nz = op.nz;
+    const int k0 = (int)((long long)part * nz / ksplit), k1 = (int)((long long)(part + 1) * nz / ksplit);
+    const long long pl = op.plane, base = (long long)rhs * op.vol;
     const T* __restrict__ zb = z + base;
-    T zc = zb[(long long)k0 * op.plane + col.c];
-    T fprev = k0 > 0 ? ldro(op.wv + k0 - 1) * (zb[(long long)(k0 - 1) * op.plane + col.c] - zc) : T(0);
-#pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
-        const T* zl = zb + (long long)k * op.plane;
-        const T zu = (k + 1 < op.nz) ? ldro(zl + op.plane + col.c) : zc;
-        const T f = ldro(op.wv + k) * (zc - zu);
-        const T hz = horiz(col, zl, zc);
-        const T az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
-        const long long o = base + (long long)k * op.plane + col.c;
-        t[o] = r[o] - az;
-        fprev = f;
-        zc = zu;
+    const T* __restrict__ rb = r + base + col.c;
+    T* __restrict__ tb = t + base + col.c;
+    T qz[PB], qe[PB], qw[PB], qn[PB], qs[PB], qr[PB];
+    auto fetch = [&](int kb, T(&vz)[PB], T(&ve)[PB], T(&vw)[PB], T(&vn)[PB], T(&vs)[PB], T(&vr)[PB]) {
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            const int k = kb + u;
+            if (k < k1) {
+                const T* zl = zb + (long long)k * pl;
+                vz[u] = ldro(zl + col.c);
+                ve[u] = ldro(zl + col.ce);
+                vw[u] = ldro(zl + col.cw);
+                vn[u] = ldro(zl + col.cn);
+                vs[u] = ldro(zl + col.cs);
+                vr[u] = rb[(long long)k * pl];
+            }
+        }
+    };
+    fetch(k0, qz, qe, qw, qn, qs, qr);
+    const T zend = k1 < nz ? ldro(zb + (long long)k1 * pl + col.c) : T(0);   // the level above the part
+    T fprev = k0 > 0 ? ldro(op.wv + k0 - 1) * (ldro(zb + (long long)(k0 - 1) * pl + col.c) - qz[0]) : T(0);
+    for (int kb = k0; kb < k1; kb += PB) {
+        T xz[PB], xe[PB], xw[PB], xn[PB], xs[PB], xr[PB];
+        fetch(kb + PB, xz, xe, xw, xn, xs, xr);
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            const int k = kb + u;
+            if (k < k1) {
+                const T zc = qz[u];
+                const T zu = (k + 1 < k1) ? (u + 1 < PB ? qz[u + 1] : xz[0]) : (k1 < nz ? zend : zc);
+                const T f = ldro(op.wv + k) * (zc - zu);
+                T h = col.me * (zc - qe[u]);
+                h = fma(col.mw, zc - qw[u], h);
+                h = fma(col.mn, zc - qn[u], h);
+                h = fma(col.ms, zc - qs[u], h);
+                const T az = fma(ldro(op.dk + k), h, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+                tb[(long long)k * pl] = qr[u] - az;
+                fprev = f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            qz[u] = xz[u];
+            qe[u] = xe[u];
+            qw[u] = xw[u];
+            qn[u] = xn[u];
+            qs[u] = xs[u];
+            qr[u] = xr[u];
+        }
     }
 }
 
-// tmp = M^{-1} rin on levels with few columns: the chunked (substructured)
-// Thomas solve of prec_chunked_body in FP64, one warp per 16-level chunk of
-// 32 columns of one row (block (32, n_z/16)), so that a column's work spreads
-// over several warps.  tmp may be rin (every chunk reads its levels first).
+// z = (acc ? z : 0) + omega M^{-1} rin on levels with few columns: the
+// chunked (substructured) Thomas solve of prec_chunked_body, one warp per
+// 16-level chunk of 32 columns of one row (block (32, n_z/16)), so that a
+// column's work spreads over several warps; the damped update is its store.
 template <typename T>
-__global__ __launch_bounds__(256) void k_mg_lsolve_chunked(OpView<T> op, const T* rin, T* tmp,
+__global__ __launch_bounds__(256) void k_mg_lsolve_chunked(OpView<T> op, const T* rin, T* z, T omega, int acc,
                                                            const SolveState* __restrict__ st) {
     __shared__ T sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
     const int rhs = blockIdx.z;
@@ -143,21 +181,43 @@ __global__ __launch_bounds__(256) void k_mg_lsolve_chunked(OpView<T> op, const T
     const int lane = threadIdx.x, ch = threadIdx.y, nch = blockDim.y;
     const Col<T> col = make_col(op, blockIdx.x * 32 + lane, blockIdx.y);
     const long long rb = (long long)rhs * op.vol;
-    Acc<T> acc[2];
+    Acc<T> sums[2];
     // alpha = 0: the chunk's "updated residual" is rin itself, and it is not stored back
-    prec_chunked_body<T, 16, false>(op, col, lane, ch, nch, 0, const_cast<T*>(rin + rb), rin + rb, tmp + rb, T(0),
-                                    acc, sh_y, sh_c, sh_z, sh_d);
+    if (acc)
+        prec_chunked_body<T, 16, false, 2>(op, col, lane, ch, nch, 0, const_cast<T*>(rin + rb), rin + rb, z + rb, T(0),
+                                           sums, sh_y, sh_c, sh_z, sh_d, nullptr, nullptr, 0, omega);
+    else
+        prec_chunked_body<T, 16, false, 1>(op, col, lane, ch, nch, 0, const_cast<T*>(rin + rb), rin + rb, z + rb, T(0),
+                                           sums, sh_y, sh_c, sh_z, sh_d, nullptr, nullptr, 0, omega);
 }
 
-// z = (acc ? z : 0) + omega m, elementwise over all right-hand sides
-template <typename T>
-__global__ void k_mg_axpy(const T* __restrict__ m, T* __restrict__ z, T omega, int acc, long long vol, int nrhs,
-                          const SolveState* __restrict__ st) {
-    const long long n = vol * nrhs;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int rhs = (int)(c / vol);
+// Elementwise kernels run on a 2-D grid (x: cells of one right-hand side,
+// grid-stride; y: right-hand sides), and the transfers on a 3-D grid (x: tiles
+// of blockDim.x x blockDim.y cells of a level, y: levels, z: right-hand
+// sides), so that no thread divides a flat cell index.  Right-hand sides
+// whose solve has stopped are skipped.
+template <class F>
+__device__ __forceinline__ void for_each_elem(long long vol, int nrhs, const SolveState* __restrict__ st, F f) {
+    for (int rhs = blockIdx.y; rhs < nrhs; rhs += gridDim.y) {
         if (st[rhs].done) continue;
-        z[c] = acc ? fma(omega, m[c], z[c]) : omega * m[c];
+        const long long b = (long long)rhs * vol;
+        for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < vol; c += (long long)gridDim.x * blockDim.x)
+            f(b + c, rhs);
+    }
+}
+
+// f(rhs, k, j, i) for every cell of an (nrhs, nz, ny, nx) array; nbi = tiles per row of tiles
+// (a thread takes every gridDim.y-th level: several independent loads in flight)
+template <class F>
+__device__ __forceinline__ void for_each_cell(int nx, int ny, int nz, int nrhs, int nbi,
+                                              const SolveState* __restrict__ st, F f) {
+    const int jb = blockIdx.x / nbi, ib = blockIdx.x - jb * nbi;
+    const int i = ib * blockDim.x + threadIdx.x, j = jb * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    for (int rhs = blockIdx.z; rhs < nrhs; rhs += gridDim.z) {
+        if (st[rhs].done) continue;
+#pragma unroll 4
+        for (int k = blockIdx.y; k < nz; k += gridDim.y) f(rhs, k, j, i);
     }
 }
 
@@ -165,56 +225,39 @@ __global__ void k_mg_axpy(const T* __restrict__ m, T* __restrict__ z, T omega, i
 // (2J, 2I), (2J, 2I+1), (2J+1, 2I), (2J+1, 2I+1) of the same level k.
 template <typename T>
 __global__ void k_mg_restrict(const T* __restrict__ tf, T* __restrict__ rc, int nxc, int nyc, int nz, int nrhs,
-                              const SolveState* __restrict__ st) {
-    const long long planec = (long long)nxc * nyc, volc = planec * nz, n = volc * nrhs;
+                              int nbi, const SolveState* __restrict__ st) {
+    const long long planec = (long long)nxc * nyc, volc = planec * nz;
     const long long nxf = 2LL * nxc, planef = 4 * planec;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int rhs = (int)(c / volc);
-        if (st[rhs].done) continue;
-        const long long rem = c - rhs * volc;
-        const long long k = rem / planec, jc = (rem - k * planec) / nxc, ic = rem - k * planec - jc * nxc;
-        const T* f = tf + rhs * (volc * 4) + k * planef + (2 * jc) * nxf + 2 * ic;
-        rc[c] = ((f[0] + f[1]) + f[nxf]) + f[nxf + 1];
-    }
+    for_each_cell(nxc, nyc, nz, nrhs, nbi, st, [&](int rhs, int k, int jc, int ic) {
+        const T* f = tf + rhs * (volc * 4) + k * planef + (2LL * jc) * nxf + 2 * ic;
+        rc[rhs * volc + k * planec + (long long)jc * nxc + ic] = ((f[0] + f[1]) + f[nxf]) + f[nxf + 1];
+    });
 }
 
 // zf += P zc: every fine cell adds its coarse cell's value.
 template <typename T>
 __global__ void k_mg_prolong(const T* __restrict__ zc, T* __restrict__ zf, int nxf, int nyf, int nz, int nrhs,
-                             const SolveState* __restrict__ st) {
-    const long long planef = (long long)nxf * nyf, volf = planef * nz, n = volf * nrhs;
+                             int nbi, const SolveState* __restrict__ st) {
+    const long long planef = (long long)nxf * nyf, volf = planef * nz;
     const int nxc = nxf / 2;
     const long long planec = planef / 4, volc = planec * nz;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int rhs = (int)(c / volf);
-        if (st[rhs].done) continue;
-        const long long rem = c - rhs * volf;
-        const long long k = rem / planef, j = (rem - k * planef) / nxf, i = rem - k * planef - j * nxf;
-        zf[c] += zc[rhs * volc + k * planec + (j / 2) * nxc + i / 2];
-    }
+    for_each_cell(nxf, nyf, nz, nrhs, nbi, st, [&](int rhs, int k, int j, int i) {
+        zf[rhs * volf + k * planef + (long long)j * nxf + i] +=
+            zc[rhs * volc + k * planec + (long long)(j >> 1) * nxc + (i >> 1)];
+    });
 }
 
-// a <-> b between the FP64 CG and an FP32 V-cycle, elementwise over all right-hand sides
+// a <-> b between the FP64 CG and an FP32 V-cycle
 template <typename TA, typename TB>
 __global__ void k_mg_convert(const TA* __restrict__ a, TB* __restrict__ b, long long vol, int nrhs,
                              const SolveState* __restrict__ st) {
-    const long long n = vol * nrhs;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int rhs = (int)(c / vol);
-        if (st[rhs].done) continue;
-        b[c] = (TB)a[c];
-    }
+    for_each_elem(vol, nrhs, st, [&](long long c, int) { b[c] = (TB)a[c]; });
 }
 
 // r <- r - alpha q (Algorithm 1 line 2, the preconditioner itself applied separately)
 __global__ void k_mg_rupdate(double* __restrict__ r, const double* __restrict__ q, long long vol, int nrhs,
                              const SolveState* __restrict__ st) {
-    const long long n = vol * nrhs;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int rhs = (int)(c / vol);
-        if (st[rhs].done) continue;
-        r[c] = fma(-st[rhs].alpha, q[c], r[c]);
-    }
+    for_each_elem(vol, nrhs, st, [&](long long c, int rhs) { r[c] = fma(-st[rhs].alpha, q[c], r[c]); });
 }
 
 // <r, r> and <r, z> of every right-hand side; the last block applies the

@@ -116,6 +116,9 @@ struct pcg_ctx {
     bool mg_f32 = false;                  // PCG_PREC_MULTIGRID_F32: the V-cycle in FP32
     SolveState* mg_free = nullptr;        // all-active states for a V-cycle outside a solve
     int mg_nu = 1, mg_coarse = 8;
+    long long mg_resid_threads = 524288;  // k_mg_resid splits columns until this many threads run
+    long long mg_few = 0;                 // chunked line solve below this many columns (0: by precision)
+    int mg_resid_pb = 0;                  // k_mg_resid prefetch depth, 1, 2 or 4 levels (0: by precision)
     double mg_omega = 0.8;
     int kernels_per_pass = 2;             // kernel launches in one Algorithm-1 pass of the graphs
     int spmv_pipe = 1;                    // FP64 SpMV sweep with u, p, q loads issued ahead (PCG_SPMV_PIPE=0: plain)
@@ -583,6 +586,26 @@ OpView<V> level_view(pcg_t hl) {
     else return hl->view32();
 }
 
+// Launch shapes of the multigrid's elementwise kernels (x: cells of one
+// right-hand side, y: right-hand sides) and of its transfers (x: tiles of a
+// level, y: levels, z: right-hand sides).
+dim3 elem_grid(long long vol, int nrhs) {
+    return dim3((unsigned)std::min<long long>((vol + 255) / 256, 152LL * 16), (unsigned)std::min(nrhs, 65535));
+}
+
+struct CellLaunch {
+    dim3 g, b;
+    int nbi;
+};
+
+CellLaunch cell_launch(int nx, int ny, int nz, int nrhs) {
+    const int bx = nx >= 128 ? 128 : (nx >= 64 ? 64 : 32), by = 256 / bx;
+    const int nbi = (nx + bx - 1) / bx;
+    const long long gx = (long long)nbi * ((ny + by - 1) / by);
+    const int gy = std::min((nz + 3) / 4, 65535);     // four levels per thread
+    return {dim3((unsigned)gx, (unsigned)gy, (unsigned)std::min(nrhs, 65535)), dim3(bx, by), nbi};
+}
+
 template <typename V>
 int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V* z0, V* t0) {
     const int L = (int)h->mg.size() + 1;
@@ -595,22 +618,31 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
     auto Z = [&](int l) -> V* { return l == 0 ? z0 : lv(l, h->mg[l - 1].z, h->mg[l - 1].zf); };
     auto T = [&](int l) -> V* { return l == 0 ? t0 : lv(l, h->mg[l - 1].t, h->mg[l - 1].tf); };
     const V omega = (V)h->mg_omega;
-    auto elems = [&](long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16); };
     int n = 0;
-    // Levels with few columns spread each column's work over several threads:
-    // the residual over level chunks, the line solve in its chunked form (one
-    // warp per 16 levels) followed by the damped update.
-    auto few = [&](pcg_t hl) { return hl->plane * (long long)hl->nrhs < 16384 && hl->nz <= 128; };
+    // Each column's work is spread over several threads where a level has too
+    // few columns to keep the SMs' loads in flight: the residual over level
+    // chunks (parts of a column), and, below a column count, the line solve in
+    // its chunked form (one warp per 16 levels) with the damped update as its store.
+    const long long few_cols = h->mg_few > 0 ? h->mg_few : (sizeof(V) == 4 ? 32768 : 16384);
+    auto few = [&](pcg_t hl) { return hl->plane * (long long)hl->nrhs < few_cols && hl->nz <= 128; };
     auto ksplit = [&](pcg_t hl) {
         int ks = 1;
-        while (hl->plane * (long long)hl->nrhs * ks < 32768 && ks < 32 && hl->nz / (2 * ks) >= 4) ks *= 2;
+        while (hl->plane * (long long)hl->nrhs * ks < h->mg_resid_threads && ks < 32 && hl->nz / (2 * ks) >= 4 &&
+               (long long)hl->nrhs * ks * 2 <= 65535)
+            ks *= 2;
         return ks;
     };
     auto resid = [&](int l) {                            // t = r - A z
         pcg_t hl = H(l);
         const int ks = ksplit(hl);
         const dim3 g(hl->grid_c.x, hl->grid_c.y, hl->grid_c.z * ks);
-        pcg::k_mg_resid<V><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
+        const int pb = h->mg_resid_pb > 0 ? h->mg_resid_pb : (sizeof(V) == 4 ? 4 : 2);
+        if (pb == 4)
+            pcg::k_mg_resid<V, 4><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
+        else if (pb == 2)
+            pcg::k_mg_resid<V, 2><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
+        else
+            pcg::k_mg_resid<V, 1><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
         ++n;
     };
     auto smooth = [&](int l, const V* rin, V om, int acc) {   // z = (acc ? z : 0) + omega M^{-1} rin
@@ -618,9 +650,8 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
         if (few(hl)) {
             const int nch = (hl->nz + 15) / 16;
             pcg::k_mg_lsolve_chunked<V><<<dim3((hl->nx + 31) / 32, hl->ny, hl->nrhs), dim3(32, nch, 1), 0, s>>>(
-                level_view<V>(hl), rin, T(l), st);
-            pcg::k_mg_axpy<V><<<elems(hl->ntot), 256, 0, s>>>(T(l), Z(l), om, acc, hl->vol, hl->nrhs, st);
-            n += 2;
+                level_view<V>(hl), rin, Z(l), om, acc, st);
+            ++n;
         } else {
             pcg::k_mg_smooth<V><<<hl->grid_c, hl->block_c, 0, s>>>(level_view<V>(hl), rin, T(l), Z(l), om, acc, st);
             ++n;
@@ -636,8 +667,9 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
         for (int k = 1; k < h->mg_nu; ++k) smooth_more(l);
         pcg_t hc = H(l + 1);
         resid(l);
-        pcg::k_mg_restrict<V><<<elems(hc->ntot), 256, 0, s>>>(T(l), const_cast<V*>(R(l + 1)), hc->nx, hc->ny, hc->nz,
-                                                             hc->nrhs, st);
+        const CellLaunch cl = cell_launch(hc->nx, hc->ny, hc->nz, hc->nrhs);
+        pcg::k_mg_restrict<V><<<cl.g, cl.b, 0, s>>>(T(l), const_cast<V*>(R(l + 1)), hc->nx, hc->ny, hc->nz, hc->nrhs,
+                                                    cl.nbi, st);
         ++n;
     }
     const int c = L - 1;
@@ -654,7 +686,8 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
     }
     for (int l = L - 2; l >= 0; --l) {
         pcg_t hl = H(l);
-        pcg::k_mg_prolong<V><<<elems(hl->ntot), 256, 0, s>>>(Z(l + 1), Z(l), hl->nx, hl->ny, hl->nz, hl->nrhs, st);
+        const CellLaunch cl = cell_launch(hl->nx, hl->ny, hl->nz, hl->nrhs);
+        pcg::k_mg_prolong<V><<<cl.g, cl.b, 0, s>>>(Z(l + 1), Z(l), hl->nx, hl->ny, hl->nz, hl->nrhs, cl.nbi, st);
         ++n;
         for (int k = 0; k < h->mg_nu; ++k) smooth_more(l);
     }
@@ -722,7 +755,7 @@ int build_hierarchy(pcg_t h, const pcg_grid_t* grid, const pcg_coeffs_t* coeffs)
 // One Algorithm-1 pass with the V-cycle as preconditioner: r <- r - alpha q;
 // z = B r; <r, r>, <r, z>, stopping test, beta; then the SpMV sweep.
 int launch_mg_pass(pcg_t h, cudaStream_t s) {
-    const unsigned g = (unsigned)std::min<long long>((h->ntot + 255) / 256, 152LL * 16);
+    const dim3 g = elem_grid(h->vol, h->nrhs);
     pcg::k_mg_rupdate<<<g, 256, 0, s>>>(h->r64, h->q64, h->vol, h->nrhs, h->st);
     int n = 1;
     if (h->mg_f32) {
@@ -1017,6 +1050,9 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG, "the multigrid preconditioner is available with PCG_FP64 only");
     }
+    if (const char* e = std::getenv("PCG_MG_RESID_THREADS")) h->mg_resid_threads = std::atoll(e);   // experiments
+    if (const char* e = std::getenv("PCG_MG_FEW")) h->mg_few = std::atoll(e);                        // experiments
+    if (const char* e = std::getenv("PCG_MG_RESID_PB")) h->mg_resid_pb = std::atoi(e);                // experiments
     h->rhs_stats.assign(h->nrhs, pcg_stats_t{});
     if (const char* tr = std::getenv("PCG_TRACE")) h->trace = std::atoi(tr);
     h->block = dim3(BX, BY, 1);
@@ -1212,7 +1248,7 @@ int pcg_precond(pcg_t h, const double* r, double* z) {
     if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
     if (!r || !z) return fail(h, PCG_ERR_INVALID_ARG, "r and z are required");
     if (h->precond == PCG_PREC_MULTIGRID && h->mg_f32) {
-        const unsigned g = (unsigned)std::min<long long>((h->ntot + 255) / 256, 152LL * 16);
+        const dim3 g = elem_grid(h->vol, h->nrhs);
         pcg::k_mg_convert<double, float><<<g, 256, 0, h->stream>>>(r, h->mg_r0f, h->vol, h->nrhs, h->mg_free);
         launch_vcycle<float>(h, h->stream, h->mg_free, h->mg_r0f, h->mg_z0f, h->mg_t0f);
         pcg::k_mg_convert<float, double><<<g, 256, 0, h->stream>>>(h->mg_z0f, z, h->vol, h->nrhs, h->mg_free);
