@@ -30,10 +30,10 @@ dense direct solves, manufactured-solution convergence).
 from .discretisation import (OperatorTerms, operator_terms, assemble_csr, apply_rows,
                              column_blocks, cell_volumes, FluxOperator)
 from .linesolve import LinePreconditioner, apply_columns, solve_columns
-from .pcg import pcg_textbook, pcg_interleaved, PCGResult, rounding_floor
+from .pcg import pcg_textbook, pcg_interleaved, pcg_single_reduction, PCGResult, rounding_floor
 
 __all__ = [
     "OperatorTerms", "operator_terms", "assemble_csr", "apply_rows", "column_blocks", "cell_volumes",
     "FluxOperator",
-    "LinePreconditioner", "solve_columns", "apply_columns", "pcg_textbook", "pcg_interleaved", "PCGResult", "rounding_floor",
+    "LinePreconditioner", "solve_columns", "apply_columns", "pcg_textbook", "pcg_interleaved", "pcg_single_reduction", "PCGResult", "rounding_floor",
 ]

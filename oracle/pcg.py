@@ -1,4 +1,5 @@
-"""Preconditioned conjugate gradients, textbook and interleaved (Algorithm 1).
+"""Preconditioned conjugate gradients: textbook, interleaved (Algorithm 1) and
+single-reduction (Chronopoulos-Gear).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -132,6 +133,73 @@ def pcg_interleaved(A, precond: Callable, b: np.ndarray, u0: Optional[np.ndarray
         alpha = kappa_old / sigma
     u = u + alpha * p
     return PCGResult(u.reshape(shape), passes - 1, converged, hist, _true_relres(A, b, u))
+
+
+def pcg_single_reduction(A, precond: Callable, b: np.ndarray, x0: Optional[np.ndarray] = None,
+                         eps: float = 1e-8, maxiter: int = 10000, tau: float = 0.0) -> PCGResult:
+    """PCG with one reduction phase per iteration (Chronopoulos and Gear, 1989).
+
+    Section 4.2 of the paper points to this rearrangement of CG (fused loops
+    with the inner products gathered in one place).  With u = M^{-1} r,
+    w = A u, gamma = <r, u> and delta = <w, u>, the step lengths come from
+    one reduction:
+      beta  = gamma / gamma_old                                   (0 on the first step),
+      alpha = gamma / (delta - beta gamma / alpha_old)            (gamma / delta on the first step),
+    and the search direction p and s = A p follow by recurrence:
+      p = u + beta p,  s = w + beta s,  x = x + alpha p,  r = r - alpha s.
+    In exact arithmetic the iterates are those of textbook PCG (delta -
+    beta gamma / alpha_old is <p, A p>).
+
+    Written as the passes the one-sweep GPU form takes: every pass applies the
+    previous pass's alpha and beta to p, s, x and r, then forms u = M^{-1} r,
+    w = A u and the three inner products (||r||^2, gamma, delta), and the
+    stopping test on ||r||.  The first pass starts from u = w = p = s = 0 and
+    alpha = beta = 0, so it only forms u, w and the first products.  x is
+    current when the test fires (no fix-up).  Iterations count the updates of
+    x: exiting at the test of pass k counts k - 1.  The stopping reference is
+    ||b|| (as in ``pcg_interleaved``).
+    """
+    shape = b.shape
+    b = np.asarray(b, dtype=np.float64).ravel()
+    x = np.zeros_like(b) if x0 is None else np.asarray(x0, dtype=np.float64).ravel().copy()
+    bnorm = float(np.linalg.norm(b))
+    r = b - A @ x
+    u = np.zeros_like(b)
+    w = np.zeros_like(b)
+    p = np.zeros_like(b)
+    s = np.zeros_like(b)
+    alpha = beta = 0.0
+    gamma_old = 1.0
+    first = True
+    hist: List[float] = []
+    converged = False
+    passes = 0
+    for k in range(1, maxiter + 2):
+        p = u + beta * p
+        s = w + beta * s
+        x = x + alpha * p
+        r = r - alpha * s
+        u = precond(r.reshape(shape)).ravel()
+        w = A @ u
+        rnorm = float(np.sqrt(_dot(r, r)))
+        gamma = _dot(r, u)
+        delta = _dot(w, u)
+        hist.append(rnorm)
+        if rnorm == 0.0 or rnorm < eps * bnorm or rnorm < tau:
+            converged = True
+            passes = k
+            break
+        if k == maxiter + 1:
+            passes = k
+            break
+        if first:
+            beta, alpha = 0.0, gamma / delta
+            first = False
+        else:
+            beta = gamma / gamma_old
+            alpha = gamma / (delta - beta * gamma / alpha)
+        gamma_old = gamma
+    return PCGResult(x.reshape(shape), passes - 1, converged, hist, _true_relres(A, b, x))
 
 
 def rounding_floor(A, x: np.ndarray, b: np.ndarray) -> float:

@@ -10,7 +10,11 @@
 * PCG converges to the dense direct solution; the A-norm of the error never
   increases (a theorem of CG in exact arithmetic, observable here to rounding).
 * Algorithm 1 produces the textbook iterates (Section 4.3: the loop is only
-  a reordering of the same operations).
+  a reordering of the same operations), and so does the single-reduction
+  form (Chronopoulos-Gear, cited in Section 4.2), whose alpha comes from
+  gamma and delta by a recurrence instead of <p, A p>: a wrong recurrence
+  (a dropped beta term, the old gamma in place of the new) changes the
+  iterates from the second step on.
 """
 import numpy as np
 import pytest
@@ -18,7 +22,7 @@ import scipy.linalg as sla
 
 import workloads as W
 from oracle import (FluxOperator, LinePreconditioner, assemble_csr, column_blocks, pcg_interleaved,
-                    pcg_textbook, rounding_floor, solve_columns, apply_columns)
+                    pcg_single_reduction, pcg_textbook, rounding_floor, solve_columns, apply_columns)
 
 
 def _problems():
@@ -111,7 +115,7 @@ def test_pcg_equals_dense_solve(p):
     b = W.rhs_for(p, seed=11)
     xd = np.linalg.solve(a.toarray(), b.ravel())
     op = FluxOperator(p)
-    for fn in (pcg_textbook, pcg_interleaved):
+    for fn in (pcg_textbook, pcg_interleaved, pcg_single_reduction):
         kw = dict(tol=1e-14) if fn is pcg_textbook else dict(eps=1e-14)
         res = fn(op, m, b, maxit=500, **kw) if fn is pcg_textbook else fn(op, m, b, maxiter=500, **kw)
         err = np.linalg.norm(res.x.ravel() - xd) / np.linalg.norm(xd)
@@ -156,6 +160,26 @@ def test_interleaved_equals_textbook(p):
     assert rt.converged and ri.converged
     assert abs(rt.iterations - ri.iterations) <= 1
     assert ri.final_true_relres < 2e-8
+
+
+@pytest.mark.parametrize("p", _problems() + [W.small_box()], ids=lambda p: p.name or "small")
+def test_single_reduction_equals_textbook(p):
+    a = FluxOperator(p)
+    m = LinePreconditioner(assemble_csr(p), p)
+    b = W.rhs_for(p, seed=0)
+    for k in (0, 1, 2, 5, 13):
+        xt = pcg_textbook(a, m, b, tol=0.0, maxit=k)
+        xs = pcg_single_reduction(a, m, b, eps=0.0, maxiter=k)
+        assert xt.iterations == xs.iterations == k
+        scale = max(np.linalg.norm(xt.x), 1e-300)
+        assert np.linalg.norm(xt.x - xs.x) / scale < 1e-11, k
+        r0 = xt.residual_history[0]
+        np.testing.assert_allclose(xs.residual_history, xt.residual_history, rtol=1e-9, atol=1e-12 * r0)
+    rt = pcg_textbook(a, m, b, tol=1e-8, maxit=5000)
+    rs = pcg_single_reduction(a, m, b, eps=1e-8, maxiter=5000)
+    assert rt.converged and rs.converged
+    assert abs(rt.iterations - rs.iterations) <= 1
+    assert rs.final_true_relres < 2e-8
 
 
 def test_zero_rhs_returns_zero():
