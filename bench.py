@@ -394,6 +394,48 @@ def run_other_workload(args, dev, pkg, W, torch):
     print(json.dumps(out), flush=True)
 
 
+def run_single_reduction(args, dev, pkg, W, torch):
+    """FP64 solves to 1e-8 with the single-reduction PCG (one sweep and one
+    reduction per iteration, PCG_ALG_SINGLE_REDUCTION) next to Algorithm 1
+    (two sweeps), on the 32x32x16 box (latency-bound) and the 256x256x128 box:
+    solves/s, ms per iteration, iterations and the distance of the solutions."""
+    import numpy as np
+    cases = [("box32x32x16", W.small_box(), lambda p: W.rhs_for(p, seed=0)),
+             ("box256x256x128", W.medium_box(), lambda p: W.medium_box_rhs(p))]
+    stream = torch.cuda.current_stream(dev)
+    out = {"metric": "PCG solves/s", "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic", "workload": "single-reduction", "dtype": "f64", "tol": TOL, "cases": {}}
+    for name, p, rhs in cases:
+        b = torch.from_numpy(np.ascontiguousarray(rhs(p)).ravel()).to(dev)
+        res, xs = {}, {}
+        for alg in ("interleaved", "single-reduction"):
+            with pkg.Solver(p, algorithm=alg, stream=stream.cuda_stream) as s:
+                x = torch.zeros_like(b)
+                s.solve(b, x, tol=TOL, maxit=100000)           # warm-up (graph capture)
+                times = []
+                for _ in range(max(3, min(args.steps, 10))):
+                    x.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st = s.solve(b, x, tol=TOL, maxit=100000)
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = statistics.median(times)
+                res[alg] = {"solves_per_s": 1000.0 / ms, "ms": ms, "iterations": st.iterations,
+                            "ms_per_iteration": ms / max(1, st.iterations), "relres_true": st.relres_true,
+                            "kernel_launches_per_solve": s.kernel_launches, "status": st.status_name}
+                xs[alg] = x.clone()
+        res["single_reduction_speedup"] = res["single-reduction"]["solves_per_s"] / res["interleaved"]["solves_per_s"]
+        res["relative_distance_of_solutions"] = float((xs["single-reduction"] - xs["interleaved"]).norm()
+                                                      / xs["interleaved"].norm())
+        out["cases"][name] = res
+        del b, xs
+    out["value"] = out["cases"]["box256x256x128"]["single-reduction"]["solves_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def run_multigrid(args, dev, pkg, W, torch):
     """FP64 solves preconditioned by one multigrid V-cycle (PCG_PREC_MULTIGRID,
     the solver the paper names as its next step, Section 8) next to the
@@ -458,13 +500,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", choices=["box256", "box1024", "shell-batch", "serve", "paper-panel", "multigrid"],
+    ap.add_argument("--workload", choices=["box256", "box1024", "shell-batch", "serve", "paper-panel", "multigrid",
+                                           "single-reduction"],
                     default="box256",
                     help="box256: the benchmark (default); box1024: 1024x1024x128 box with variable alpha, "
                          "FP64 and mixed; shell-batch: 1440x640x64 lat-lon band, 16 right-hand sides, FP64 and mixed; "
                          "serve: Poisson request stream through the served batch; paper-panel: the paper's own "
                          "cubed-sphere panel problem, 256x256x128, residual reduced by 1e5; multigrid: FP64 solves "
-                         "with the multigrid V-cycle preconditioner next to the line preconditioner")
+                         "with the multigrid V-cycle preconditioner next to the line preconditioner; "
+                         "single-reduction: FP64 solves with one sweep per iteration next to Algorithm 1")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: seconds of arrivals (200 req/s)")
     ap.add_argument("--serve-mix", choices=["paper", "small"], default="paper",
                     help="serve: the full request mix, or only requests of at most 128 x 128 x 64 at 10x the rate")
@@ -497,6 +541,9 @@ def main():
         return
     if args.workload == "multigrid":
         run_multigrid(args, dev, pkg, W, torch)
+        return
+    if args.workload == "single-reduction":
+        run_single_reduction(args, dev, pkg, W, torch)
         return
     if args.workload != "box256":
         run_other_workload(args, dev, pkg, W, torch)

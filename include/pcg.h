@@ -82,6 +82,17 @@ enum pcg_preconditioner {
                                   widened on the way out) inside the FP64 CG.  PCG_FP64 only. */
 };
 
+/* How an iteration is organised on the device (pcg_opts_t.algorithm). */
+enum pcg_algorithm {
+    PCG_ALG_INTERLEAVED = 0,      /* Algorithm 1 of the paper: a preconditioner sweep and an SpMV sweep per
+                                     iteration, two grid-wide reductions */
+    PCG_ALG_SINGLE_REDUCTION = 1  /* the Chronopoulos-Gear rearrangement cited in Section 4.2: one sweep and one
+                                     reduction per iteration, the line solves of each tile's ring of neighbouring
+                                     columns recomputed by the tile.  PCG_FP64 with PCG_PREC_LINE, n_z <= 256;
+                                     other combinations are rejected with PCG_ERR_INVALID_ARG.  x is current when
+                                     the stopping test fires. */
+};
+
 typedef struct pcg_ctx* pcg_t;
 typedef struct pcg_server* pcg_server_t;
 
@@ -115,6 +126,7 @@ typedef struct {
     int passes_per_launch;     /* PCG passes per CUDA-graph launch between convergence polls; 0 selects 16 */
     void* stream;              /* cudaStream_t for all work; NULL = default stream */
     int preconditioner;        /* pcg_preconditioner (PCG_PREC_LINE when opts is NULL) */
+    int algorithm;             /* pcg_algorithm (PCG_ALG_INTERLEAVED when opts is NULL) */
 } pcg_opts_t;
 
 /* Per-solve statistics.  For nrhs > 1 the scalar fields report the worst

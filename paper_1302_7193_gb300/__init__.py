@@ -22,6 +22,7 @@ PCG_OK, PCG_ERR_INVALID_ARG, PCG_ERR_OOM, PCG_ERR_CUDA, PCG_NOT_CONVERGED, PCG_B
 PCG_GEOM_BOX, PCG_GEOM_LATLON, PCG_GEOM_CUBED_PANEL = 0, 1, 2
 PCG_FP64, PCG_MIXED = 0, 1
 PCG_PREC_LINE, PCG_PREC_MULTIGRID, PCG_PREC_MULTIGRID_F32 = 0, 1, 2
+PCG_ALG_INTERLEAVED, PCG_ALG_SINGLE_REDUCTION = 0, 1
 STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "not_converged", 5: "breakdown", 6: "timeout",
                 7: "pending"}
 
@@ -48,7 +49,8 @@ class pcg_coeffs_t(ctypes.Structure):
 class pcg_opts_t(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("passes_per_launch", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("preconditioner", ctypes.c_int)]
+                ("preconditioner", ctypes.c_int),
+                ("algorithm", ctypes.c_int)]
 
 
 class pcg_stats_t(ctypes.Structure):
@@ -170,7 +172,7 @@ def _dbl(a):
 
 def pcg_create(problem, nrhs: int = 1, precision: int = PCG_FP64, inner_tol: float = 0.0, inner_maxit: int = 0,
                max_outer: int = 0, passes_per_launch: int = 0, stream: Optional[int] = None,
-               preconditioner: int = PCG_PREC_LINE):
+               preconditioner: int = PCG_PREC_LINE, algorithm: int = PCG_ALG_INTERLEAVED):
     """Marshal a problem description (any object with the fields of
     ``workloads.Problem``) into pcg_create; returns (handle, keepalive)."""
     lib = load_library()
@@ -189,7 +191,7 @@ def pcg_create(problem, nrhs: int = 1, precision: int = PCG_FP64, inner_tol: flo
         except Exception:
             stream = 0
     o = pcg_opts_t(int(precision), float(inner_tol), int(inner_maxit), int(max_outer), int(passes_per_launch),
-                   ctypes.c_void_p(stream or 0), int(preconditioner))
+                   ctypes.c_void_p(stream or 0), int(preconditioner), int(algorithm))
     h = ctypes.c_void_p()
     rc = lib.pcg_create(ctypes.byref(g), ctypes.byref(c), ctypes.byref(o), ctypes.byref(h))
     if rc != PCG_OK:
@@ -201,7 +203,8 @@ class Solver:
     """One pcg_t handle.  Vectors are torch tensors of nrhs * n_z * n_y * n_x
     elements in the layout [nrhs][n_z][n_y][n_x]."""
 
-    def __init__(self, problem, nrhs: int = 1, precision: str = "fp64", preconditioner: str = "line", **kw):
+    def __init__(self, problem, nrhs: int = 1, precision: str = "fp64", preconditioner: str = "line",
+                 algorithm: str = "interleaved", **kw):
         self.lib = load_library()
         self.problem = problem
         self.nrhs = nrhs
@@ -211,7 +214,9 @@ class Solver:
         self.preconditioner = preconditioner
         pc = {"line": PCG_PREC_LINE, "multigrid": PCG_PREC_MULTIGRID,
               "multigrid-f32": PCG_PREC_MULTIGRID_F32}[preconditioner]
-        self.h, self._keep = pcg_create(problem, nrhs=nrhs, precision=prec, preconditioner=pc, **kw)
+        self.algorithm = algorithm
+        alg = {"interleaved": PCG_ALG_INTERLEAVED, "single-reduction": PCG_ALG_SINGLE_REDUCTION}[algorithm]
+        self.h, self._keep = pcg_create(problem, nrhs=nrhs, precision=prec, preconditioner=pc, algorithm=alg, **kw)
 
     def _check(self, rc: int, allow=(PCG_OK,)):
         if rc not in allow:

@@ -22,6 +22,7 @@
 #include "../../include/pcg.h"
 #include "kernels.cuh"
 #include "multigrid.cuh"
+#include "single_reduction.cuh"
 
 using pcg::BX;
 using pcg::BY;
@@ -119,6 +120,12 @@ struct pcg_ctx {
     long long mg_resid_threads = 524288;  // k_mg_resid splits columns until this many threads run
     long long mg_few = 0;                 // chunked line solve below this many columns (0: by precision)
     int mg_resid_pb = 0;                  // k_mg_resid prefetch depth, 1, 2 or 4 levels (0: by precision)
+    // PCG_ALG_SINGLE_REDUCTION: one k_sweep_sr per pass; r, s (q64), w double-buffered
+    bool alg_sr = false;
+    dim3 grid_sr;
+    int nblk_sr = 0;
+    double *r64b = nullptr, *s64b = nullptr, *w64a = nullptr, *w64b = nullptr;
+    cudaGraphExec_t graph_sr = nullptr;
     double mg_omega = 0.8;
     int kernels_per_pass = 2;             // kernel launches in one Algorithm-1 pass of the graphs
     int spmv_pipe = 1;                    // FP64 SpMV sweep with u, p, q loads issued ahead (PCG_SPMV_PIPE=0: plain)
@@ -380,6 +387,18 @@ int ensure_ws64(pcg_t h) {
     int rc;
     for (double** p : {&h->u64, &h->r64, &h->z64, &h->p64, &h->q64})
         if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
+    return PCG_OK;
+}
+
+// PCG_ALG_SINGLE_REDUCTION: the second buffers of r and s, both of w, and
+// the shared-memory limit of its sweep (n_z x 108 doubles)
+int ensure_ws_sr(pcg_t h) {
+    if (h->w64b) return PCG_OK;
+    int rc;
+    for (double** p : {&h->r64b, &h->s64b, &h->w64a, &h->w64b})
+        if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
+    PCG_CK(h, cudaFuncSetAttribute(pcg::k_sweep_sr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(double) * pcg::SR_NH * pcg::SR_MAX_NZ)));
     return PCG_OK;
 }
 
@@ -794,6 +813,31 @@ int capture_passes(pcg_t h, OpView<T> v, T* u, T* r, T* z, T* p, T* q, SolveStat
     return PCG_OK;
 }
 
+// Capture `ppl` passes of the single-reduction PCG (one k_sweep_sr each);
+// pass i reads buffer i % 2 of r, s, w and writes the other one.  x is u64,
+// u is z64, p is p64, s is q64 / s64b.
+int capture_passes_sr(pcg_t h, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    const size_t smem = sizeof(double) * pcg::SR_NH * h->nz;
+    double* rb[2] = {h->r64, h->r64b};
+    double* sb[2] = {h->q64, h->s64b};
+    double* wb[2] = {h->w64a, h->w64b};
+    PCG_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < h->ppl; ++i) {
+        const int a = i & 1, b = a ^ 1;
+        pcg::k_sweep_sr<<<h->grid_sr, pcg::SR_NT, smem, h->cap_stream>>>(
+            h->view64(), h->u64, h->z64, h->p64, rb[a], rb[b], sb[a], sb[b], wb[a], wb[b], h->st, h->partials,
+            h->counters, h->nblk_sr);
+    }
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess) return fail(h, PCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, PCG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    h->kernels_per_pass = 1;
+    return PCG_OK;
+}
+
 // Run passes until every rhs is done (or `max_launch` graph launches).
 // Two graph launches are kept in flight; after each, the per-rhs states are
 // copied to a pinned slot and polled when the launch's event completes.
@@ -830,7 +874,10 @@ double now_ms() {
 int solve_fp64(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_stats_t* stats) {
     int rc;
     if ((rc = ensure_ws64(h))) return rc;
-    if (!h->graph64) {
+    if (h->alg_sr) {
+        if ((rc = ensure_ws_sr(h))) return rc;
+        if (!h->graph_sr && (rc = capture_passes_sr(h, &h->graph_sr))) return rc;
+    } else if (!h->graph64) {
         if ((rc = capture_passes<double>(h, h->view64(), h->u64, h->r64, h->z64, h->p64, h->q64, h->st, &h->graph64)))
             return rc;
     }
@@ -842,10 +889,14 @@ int solve_fp64(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_s
                                                         h->nblocks, 0);
     PCG_CK(h, cudaMemsetAsync(h->p64, 0, sizeof(double) * h->ntot, s));
     PCG_CK(h, cudaMemsetAsync(h->q64, 0, sizeof(double) * h->ntot, s));
+    if (h->alg_sr) {   // u = w = 0 before the first pass (p and s are cleared above)
+        PCG_CK(h, cudaMemsetAsync(h->z64, 0, sizeof(double) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->w64a, 0, sizeof(double) * h->ntot, s));
+    }
     PCG_CK(h, cudaGetLastError());
     h->launches += 2;
     const long long max_launch = ((long long)maxit + 1 + h->ppl - 1) / h->ppl + 1;
-    if ((rc = run_graph(h, h->graph64, h->st, max_launch))) return rc;
+    if ((rc = run_graph(h, h->alg_sr ? h->graph_sr : h->graph64, h->st, max_launch))) return rc;
     pcg::k_finish<<<h->grid, h->block, 0, s>>>(h->nx, h->ny, h->nz, h->plane, h->vol, x, h->u64, h->p64, h->st);
     pcg::k_residual<double><<<h->grid, h->block, 0, s>>>(v, b, x, nullptr, (double*)nullptr, h->st, h->partials,
                                                         h->counters, h->nblocks, 1);
@@ -1035,6 +1086,11 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
         if (opts->passes_per_launch > 0) h->ppl = opts->passes_per_launch;
         h->stream = (cudaStream_t)opts->stream;
         h->precond = opts->preconditioner;
+        if (opts->algorithm != PCG_ALG_INTERLEAVED && opts->algorithm != PCG_ALG_SINGLE_REDUCTION) {
+            delete h;
+            return fail(nullptr, PCG_ERR_INVALID_ARG, "unknown algorithm");
+        }
+        h->alg_sr = opts->algorithm == PCG_ALG_SINGLE_REDUCTION;
     }
     if (h->precision != PCG_FP64 && h->precision != PCG_MIXED) {
         delete h;
@@ -1050,6 +1106,13 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG, "the multigrid preconditioner is available with PCG_FP64 only");
     }
+    if (h->alg_sr && (h->precision != PCG_FP64 || h->precond != PCG_PREC_LINE || h->mg_f32 ||
+                      h->nz > pcg::SR_MAX_NZ || h->nrhs > 65535 || (h->ny + pcg::SR_TY - 1) / pcg::SR_TY > 65535)) {
+        delete h;
+        return fail(nullptr, PCG_ERR_INVALID_ARG,
+                    "PCG_ALG_SINGLE_REDUCTION needs PCG_FP64, PCG_PREC_LINE and n_z <= " +
+                        std::to_string(pcg::SR_MAX_NZ));
+    }
     if (const char* e = std::getenv("PCG_MG_RESID_THREADS")) h->mg_resid_threads = std::atoll(e);   // experiments
     if (const char* e = std::getenv("PCG_MG_FEW")) h->mg_few = std::atoll(e);                        // experiments
     if (const char* e = std::getenv("PCG_MG_RESID_PB")) h->mg_resid_pb = std::atoi(e);                // experiments
@@ -1058,6 +1121,11 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->block = dim3(BX, BY, 1);
     h->grid = dim3((h->nx + BX - 1) / BX, (h->ny + BY - 1) / BY, h->nrhs);
     h->nblocks = (int)(h->grid.x * h->grid.y);
+    if (h->alg_sr) {
+        h->grid_sr = dim3((h->nx + pcg::SR_TX - 1) / pcg::SR_TX, (h->ny + pcg::SR_TY - 1) / pcg::SR_TY, h->nrhs);
+        h->nblk_sr = (int)(h->grid_sr.x * h->grid_sr.y);
+        h->ppl += h->ppl & 1;   // passes alternate the r, s, w buffers: an even count ends where it began
+    }
     {
         // The one-thread-per-column sweeps keep every tile resident at once, so
         // the SM with the most tiles sets their duration: take the tile height
@@ -1185,7 +1253,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if ((rc = dmalloc(h, &h->st, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->st_in, h->nrhs))) return bail(rc);
     if ((rc = dmalloc(h, &h->d_active, h->nrhs))) return bail(rc);
-    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(std::max(std::max(h->nblocks, 2 * h->nblk_c), h->prec_items), std::max(std::max(h->nblk_a, h->nblk_b), 2 * h->nblk_t)) * 4))) return bail(rc);
+    if ((rc = dmalloc(h, &h->partials, (size_t)h->nrhs * std::max(std::max(std::max(h->nblocks, 2 * h->nblk_c), h->prec_items), std::max(std::max(std::max(h->nblk_a, h->nblk_b), 2 * h->nblk_t), h->nblk_sr)) * 4))) return bail(rc);
     if ((rc = dmalloc(h, &h->counters, h->nrhs))) return bail(rc);
     e = cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * h->nrhs, h->stream);
     if (e != cudaSuccess) { h->err = std::string("cudaMemset: ") + cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
@@ -1358,6 +1426,9 @@ void pcg_destroy(pcg_t h) {
     if (h->mg_free) cudaFree(h->mg_free);
     if (h->graph64) cudaGraphExecDestroy(h->graph64);
     if (h->graph32) cudaGraphExecDestroy(h->graph32);
+    if (h->graph_sr) cudaGraphExecDestroy(h->graph_sr);
+    for (void* p : {(void*)h->r64b, (void*)h->s64b, (void*)h->w64a, (void*)h->w64b})
+        if (p) cudaFree(p);
     for (void* p : {(void*)h->u64, (void*)h->r64, (void*)h->z64, (void*)h->p64, (void*)h->q64, (void*)h->u32,
                     (void*)h->r32, (void*)h->z32, (void*)h->p32, (void*)h->q32, (void*)h->hb, (void*)h->hx,
                     (void*)h->st, (void*)h->st_in, (void*)h->d_active, (void*)h->partials, (void*)h->counters,

@@ -62,12 +62,21 @@ def test_create_rejects_bad_arguments(lib, field, value):
     assert msg
 
 
-@pytest.mark.parametrize("over", [{"preconditioner": 5}, {"preconditioner": 1, "precision": 1}, {"precision": 3}])
+@pytest.mark.parametrize("over", [{"preconditioner": 5}, {"preconditioner": 1, "precision": 1}, {"precision": 3},
+                                  {"algorithm": 2}, {"algorithm": 1, "precision": 1},
+                                  {"algorithm": 1, "preconditioner": 1}, {"algorithm": 1, "preconditioner": 2}])
 def test_create_rejects_bad_options(lib, over):
-    # unknown preconditioner; multigrid is FP64 only; unknown precision
+    # unknown preconditioner; multigrid is FP64 only; unknown precision; unknown
+    # algorithm; the single-reduction sweep is FP64 with the line preconditioner only
     rc, h, msg, _ = _create(W.small_box(), **over)
     assert rc == pkg.PCG_ERR_INVALID_ARG and not h.value, (rc, msg)
     assert msg
+
+
+def test_single_reduction_rejects_deep_columns(lib):
+    # its sweep keeps n_z x 108 doubles of u in shared memory
+    rc, h, msg, _ = _create(W.box_problem(4, 4, 300, 0.01), algorithm=pkg.PCG_ALG_SINGLE_REDUCTION)
+    assert rc == pkg.PCG_ERR_INVALID_ARG and "n_z <= 256" in msg
 
 
 def test_create_rejects_non_monotone_levels(lib):
