@@ -517,8 +517,9 @@ def main():
     ap.add_argument("--profile-vcycle", choices=["fp64", "fp32"], default=None,
                     help="run five multigrid V-cycles (pcg_precond) on the 256x256x128 box and print the mean ms "
                          "per cycle of the last four (a small case for ncu)")
-    ap.add_argument("--profile-sweeps", choices=["fp64", "mixed"], default=None,
-                    help="profiling case: 3 passes of the fused sweeps on the benchmark grid, then exit")
+    ap.add_argument("--profile-sweeps", choices=["fp64", "mixed", "sr"], default=None,
+                    help="profiling case on the benchmark grid, then exit: 3 passes of the fused sweeps (fp64, mixed) "
+                         "or 3 iterations of the single-reduction solve (sr)")
     args = ap.parse_args()
     world, rank, local = dist_init()
 
@@ -568,6 +569,12 @@ def main():
     if args.profile_sweeps:
         p = W.medium_box()
         bp = torch.from_numpy(W.medium_box_rhs(p).ravel()).to(dev)
+        if args.profile_sweeps == "sr":            # three iterations of the single-reduction sweep
+            with pkg.Solver(p, algorithm="single-reduction") as s:
+                x = torch.zeros_like(bp)
+                st = s.solve(bp, x, tol=0.0, maxit=3)
+                print(json.dumps({"iterations": st.iterations, "status": st.status_name}))
+            return
         with pkg.Solver(p) as s:
             print(s.pcg_time_sweeps(bp, args.profile_sweeps, passes=3))
         return
