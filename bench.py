@@ -654,15 +654,17 @@ def main():
     xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
     solver.solve_host(bh, xh, tol=TOL, maxit=100000)
     e2e_t = []
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.fill_(1.0)
-        torch.cuda.synchronize(dev)
-        xh[:] = 0.0
-        t0 = time.perf_counter()
-        solver.solve_host(bh, xh, tol=TOL, maxit=100000)
-        e2e_t.append(time.perf_counter() - t0)
+    with ClockSampler(local) as clk_e2e:
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize(dev)
+            xh[:] = 0.0
+            t0 = time.perf_counter()
+            solver.solve_host(bh, xh, tol=TOL, maxit=100000)
+            e2e_t.append(time.perf_counter() - t0)
     e2e = {"value": world / statistics.mean(e2e_t), "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * n,
-           "d2h_bytes_per_step": 8 * n}
+           "d2h_bytes_per_step": 8 * n, "ms_per_step": [round(t * 1e3, 2) for t in e2e_t],
+           "clocks": clk_e2e.summary()}
 
     # mixed precision form of the same solve
     mixed = None
