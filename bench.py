@@ -395,25 +395,29 @@ def run_other_workload(args, dev, pkg, W, torch):
 
 
 def run_single_reduction(args, dev, pkg, W, torch):
-    """FP64 solves to 1e-8 with the single-reduction PCG (one sweep and one
+    """Solves to 1e-8 with the single-reduction PCG (one sweep and one
     reduction per iteration, PCG_ALG_SINGLE_REDUCTION) next to Algorithm 1
-    (two sweeps), on the 32x32x16 box (latency-bound) and the 256x256x128 box:
-    solves/s, ms per iteration, iterations and the distance of the solutions."""
+    (two sweeps): FP64 on the 32x32x16 box (latency-bound) and the
+    256x256x128 box, and the mixed form (the single-reduction sweep as its FP32
+    inner solve) on the 256x256x128 and 1024x1024x128 boxes: solves/s, ms per
+    (inner) iteration, iterations and the distance of the solutions."""
     import numpy as np
-    cases = [("box32x32x16", W.small_box(), lambda p: W.rhs_for(p, seed=0)),
-             ("box256x256x128", W.medium_box(), lambda p: W.medium_box_rhs(p))]
+    cases = [("box32x32x16", W.small_box(), lambda p: W.rhs_for(p, seed=0), "fp64"),
+             ("box256x256x128", W.medium_box(), lambda p: W.medium_box_rhs(p), "fp64"),
+             ("box256x256x128_mixed", W.medium_box(), lambda p: W.medium_box_rhs(p), "mixed"),
+             ("box1024x1024x128_sin_mixed", W.large_box(), lambda p: W.rhs_for(p, seed=0), "mixed")]
     stream = torch.cuda.current_stream(dev)
     out = {"metric": "PCG solves/s", "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
            "data": "synthetic", "workload": "single-reduction", "dtype": "f64", "tol": TOL, "cases": {}}
-    for name, p, rhs in cases:
+    for name, p, rhs, prec in cases:
         b = torch.from_numpy(np.ascontiguousarray(rhs(p)).ravel()).to(dev)
         res, xs = {}, {}
         for alg in ("interleaved", "single-reduction"):
-            with pkg.Solver(p, algorithm=alg, stream=stream.cuda_stream) as s:
+            with pkg.Solver(p, algorithm=alg, precision=prec, stream=stream.cuda_stream) as s:
                 x = torch.zeros_like(b)
                 s.solve(b, x, tol=TOL, maxit=100000)           # warm-up (graph capture)
                 times = []
-                for _ in range(max(3, min(args.steps, 10))):
+                for _ in range(max(3, min(args.steps, 10 if p.n_cells < 1e8 else 3))):
                     x.zero_()
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
@@ -424,8 +428,9 @@ def run_single_reduction(args, dev, pkg, W, torch):
                     times.append(e0.elapsed_time(e1))
                 ms = statistics.median(times)
                 res[alg] = {"solves_per_s": 1000.0 / ms, "ms": ms, "iterations": st.iterations,
-                            "ms_per_iteration": ms / max(1, st.iterations), "relres_true": st.relres_true,
-                            "kernel_launches_per_solve": s.kernel_launches, "status": st.status_name}
+                            "outer_sweeps": st.outer_sweeps, "ms_per_iteration": ms / max(1, st.iterations),
+                            "relres_true": st.relres_true, "kernel_launches_per_solve": s.kernel_launches,
+                            "status": st.status_name}
                 xs[alg] = x.clone()
         res["single_reduction_speedup"] = res["single-reduction"]["solves_per_s"] / res["interleaved"]["solves_per_s"]
         res["relative_distance_of_solutions"] = float((xs["single-reduction"] - xs["interleaved"]).norm()

@@ -88,9 +88,10 @@ enum pcg_algorithm {
                                      iteration, two grid-wide reductions */
     PCG_ALG_SINGLE_REDUCTION = 1  /* the Chronopoulos-Gear rearrangement cited in Section 4.2: one sweep and one
                                      reduction per iteration, the line solves of each tile's ring of neighbouring
-                                     columns recomputed by the tile.  PCG_FP64 with PCG_PREC_LINE, n_z <= 256;
-                                     other combinations are rejected with PCG_ERR_INVALID_ARG.  x is current when
-                                     the stopping test fires. */
+                                     columns recomputed by the tile.  With PCG_FP64 it is the whole solve, with
+                                     PCG_MIXED the FP32 inner solve.  PCG_PREC_LINE and n_z <= 256 only; other
+                                     combinations are rejected with PCG_ERR_INVALID_ARG.  x is current when the
+                                     stopping test fires. */
 };
 
 typedef struct pcg_ctx* pcg_t;

@@ -125,7 +125,8 @@ struct pcg_ctx {
     dim3 grid_sr;
     int nblk_sr = 0;
     double *r64b = nullptr, *s64b = nullptr, *w64a = nullptr, *w64b = nullptr;
-    cudaGraphExec_t graph_sr = nullptr;
+    float *r32b = nullptr, *s32b = nullptr, *w32a = nullptr, *w32b = nullptr;   // the mixed form's inner solve
+    cudaGraphExec_t graph_sr = nullptr, graph_sr32 = nullptr;
     double mg_omega = 0.8;
     int kernels_per_pass = 2;             // kernel launches in one Algorithm-1 pass of the graphs
     int spmv_pipe = 1;                    // FP64 SpMV sweep with u, p, q loads issued ahead (PCG_SPMV_PIPE=0: plain)
@@ -390,15 +391,24 @@ int ensure_ws64(pcg_t h) {
     return PCG_OK;
 }
 
-// PCG_ALG_SINGLE_REDUCTION: the second buffers of r and s, both of w, and
-// the shared-memory limit of its sweep (n_z x 108 doubles)
-int ensure_ws_sr(pcg_t h) {
-    if (h->w64b) return PCG_OK;
+// PCG_ALG_SINGLE_REDUCTION: the second buffers of r and s, both of w (in the
+// precision of the iteration), and the shared-memory limit of its sweep
+// (n_z x 108 values)
+int ensure_ws_sr(pcg_t h, bool f32) {
     int rc;
-    for (double** p : {&h->r64b, &h->s64b, &h->w64a, &h->w64b})
-        if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
-    PCG_CK(h, cudaFuncSetAttribute(pcg::k_sweep_sr, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(double) * pcg::SR_NH * pcg::SR_MAX_NZ)));
+    if (f32) {
+        if (h->w32b) return PCG_OK;
+        for (float** p : {&h->r32b, &h->s32b, &h->w32a, &h->w32b})
+            if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
+        PCG_CK(h, cudaFuncSetAttribute(pcg::k_sweep_sr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * pcg::SrTile<float>::NH * pcg::SR_MAX_NZ)));
+    } else {
+        if (h->w64b) return PCG_OK;
+        for (double** p : {&h->r64b, &h->s64b, &h->w64a, &h->w64b})
+            if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
+        PCG_CK(h, cudaFuncSetAttribute(pcg::k_sweep_sr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * pcg::SrTile<double>::NH * pcg::SR_MAX_NZ)));
+    }
     return PCG_OK;
 }
 
@@ -814,20 +824,20 @@ int capture_passes(pcg_t h, OpView<T> v, T* u, T* r, T* z, T* p, T* q, SolveStat
 }
 
 // Capture `ppl` passes of the single-reduction PCG (one k_sweep_sr each);
-// pass i reads buffer i % 2 of r, s, w and writes the other one.  x is u64,
-// u is z64, p is p64, s is q64 / s64b.
-int capture_passes_sr(pcg_t h, cudaGraphExec_t* out) {
+// pass i reads buffer i % 2 of r, s, w and writes the other one.
+template <typename T>
+int capture_passes_sr(pcg_t h, OpView<T> v, T* x, T* u, T* p, T* ra, T* rb, T* sa, T* sb, T* wa, T* wb,
+                      SolveState* st, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
-    const size_t smem = sizeof(double) * pcg::SR_NH * h->nz;
-    double* rb[2] = {h->r64, h->r64b};
-    double* sb[2] = {h->q64, h->s64b};
-    double* wb[2] = {h->w64a, h->w64b};
+    const size_t smem = sizeof(T) * pcg::SrTile<T>::NH * h->nz;
+    T* rr[2] = {ra, rb};
+    T* ss[2] = {sa, sb};
+    T* ww[2] = {wa, wb};
     PCG_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < h->ppl; ++i) {
         const int a = i & 1, b = a ^ 1;
-        pcg::k_sweep_sr<<<h->grid_sr, pcg::SR_NT, smem, h->cap_stream>>>(
-            h->view64(), h->u64, h->z64, h->p64, rb[a], rb[b], sb[a], sb[b], wb[a], wb[b], h->st, h->partials,
-            h->counters, h->nblk_sr);
+        pcg::k_sweep_sr<T><<<h->grid_sr, pcg::SrTile<T>::NT, smem, h->cap_stream>>>(
+            v, x, u, p, rr[a], rr[b], ss[a], ss[b], ww[a], ww[b], st, h->partials, h->counters, h->nblk_sr);
     }
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess) return fail(h, PCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -874,9 +884,12 @@ double now_ms() {
 int solve_fp64(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_stats_t* stats) {
     int rc;
     if ((rc = ensure_ws64(h))) return rc;
-    if (h->alg_sr) {
-        if ((rc = ensure_ws_sr(h))) return rc;
-        if (!h->graph_sr && (rc = capture_passes_sr(h, &h->graph_sr))) return rc;
+    if (h->alg_sr) {   // x is u64, u is z64, p is p64, s is q64 / s64b
+        if ((rc = ensure_ws_sr(h, false))) return rc;
+        if (!h->graph_sr &&
+            (rc = capture_passes_sr<double>(h, h->view64(), h->u64, h->z64, h->p64, h->r64, h->r64b, h->q64, h->s64b,
+                                            h->w64a, h->w64b, h->st, &h->graph_sr)))
+            return rc;
     } else if (!h->graph64) {
         if ((rc = capture_passes<double>(h, h->view64(), h->u64, h->r64, h->z64, h->p64, h->q64, h->st, &h->graph64)))
             return rc;
@@ -925,7 +938,13 @@ int solve_fp64(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_s
 int solve_mixed(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_stats_t* stats) {
     int rc;
     if ((rc = ensure_ws32(h))) return rc;
-    if (!h->graph32) {
+    if (h->alg_sr) {   // inner solve: e is u32, u is z32, p is p32, s is q32 / s32b
+        if ((rc = ensure_ws_sr(h, true))) return rc;
+        if (!h->graph_sr32 &&
+            (rc = capture_passes_sr<float>(h, h->view32(), h->u32, h->z32, h->p32, h->r32, h->r32b, h->q32, h->s32b,
+                                           h->w32a, h->w32b, h->st_in, &h->graph_sr32)))
+            return rc;
+    } else if (!h->graph32) {
         if ((rc = capture_passes<float>(h, h->view32(), h->u32, h->r32, h->z32, h->p32, h->q32, h->st_in, &h->graph32)))
             return rc;
     }
@@ -995,10 +1014,14 @@ int solve_mixed(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_
         PCG_CK(h, cudaMemsetAsync(h->u32, 0, sizeof(float) * h->ntot, s));
         PCG_CK(h, cudaMemsetAsync(h->p32, 0, sizeof(float) * h->ntot, s));
         PCG_CK(h, cudaMemsetAsync(h->q32, 0, sizeof(float) * h->ntot, s));
+        if (h->alg_sr) {   // u = w = 0 before the first pass
+            PCG_CK(h, cudaMemsetAsync(h->z32, 0, sizeof(float) * h->ntot, s));
+            PCG_CK(h, cudaMemsetAsync(h->w32a, 0, sizeof(float) * h->ntot, s));
+        }
         PCG_CK(h, cudaGetLastError());
         h->launches += 2;
         const long long max_launch = ((long long)inner_cap + 1 + h->ppl - 1) / h->ppl + 1;
-        if ((rc = run_graph(h, h->graph32, h->st_in, max_launch))) return rc;
+        if ((rc = run_graph(h, h->alg_sr ? h->graph_sr32 : h->graph32, h->st_in, max_launch))) return rc;
         pcg::k_refine_update<<<h->grid, h->block, 0, s>>>(h->nx, h->ny, h->nz, h->plane, h->vol, x, h->u32, h->p32,
                                                          h->st_in, h->st, h->d_active);
         PCG_CK(h, cudaGetLastError());
@@ -1010,7 +1033,11 @@ int solve_mixed(pcg_t h, const double* b, double* x, double tol, int maxit, pcg_
             sweeps[r] += 1;
             inner_it[r] += std::max(0, h->h_st[nr + r].pass - 1);
             const int is = h->h_st[nr + r].status;
-            if (is == PCG_BREAKDOWN || is == PCG_TIMEOUT) { done[r] = 1; status[r] = is; }
+            // The single-reduction inner solve stops (alpha = 0, its correction so
+            // far kept) when FP32 rounding makes delta - beta gamma / alpha_old
+            // non-positive; the FP64 residual of the next sweep decides, and a
+            // non-finite one ends the solve there.
+            if (is == PCG_TIMEOUT || (is == PCG_BREAKDOWN && !h->alg_sr)) { done[r] = 1; status[r] = is; }
         }
     }
     int worst = PCG_OK;
@@ -1106,12 +1133,11 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG, "the multigrid preconditioner is available with PCG_FP64 only");
     }
-    if (h->alg_sr && (h->precision != PCG_FP64 || h->precond != PCG_PREC_LINE || h->mg_f32 ||
-                      h->nz > pcg::SR_MAX_NZ || h->nrhs > 65535 || (h->ny + pcg::SR_TY - 1) / pcg::SR_TY > 65535)) {
+    if (h->alg_sr && (h->precond != PCG_PREC_LINE || h->mg_f32 || h->nz > pcg::SR_MAX_NZ || h->nrhs > 65535 ||
+                      (h->ny + pcg::SR_TY - 1) / pcg::SR_TY > 65535)) {
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG,
-                    "PCG_ALG_SINGLE_REDUCTION needs PCG_FP64, PCG_PREC_LINE and n_z <= " +
-                        std::to_string(pcg::SR_MAX_NZ));
+                    "PCG_ALG_SINGLE_REDUCTION needs PCG_PREC_LINE and n_z <= " + std::to_string(pcg::SR_MAX_NZ));
     }
     if (const char* e = std::getenv("PCG_MG_RESID_THREADS")) h->mg_resid_threads = std::atoll(e);   // experiments
     if (const char* e = std::getenv("PCG_MG_FEW")) h->mg_few = std::atoll(e);                        // experiments
@@ -1122,7 +1148,10 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->grid = dim3((h->nx + BX - 1) / BX, (h->ny + BY - 1) / BY, h->nrhs);
     h->nblocks = (int)(h->grid.x * h->grid.y);
     if (h->alg_sr) {
-        h->grid_sr = dim3((h->nx + pcg::SR_TX - 1) / pcg::SR_TX, (h->ny + pcg::SR_TY - 1) / pcg::SR_TY, h->nrhs);
+        // the tile of the precision the single-reduction sweep runs in (the
+        // whole solve in FP64, the inner solve of the mixed form in FP32)
+        const int tx = h->precision == PCG_MIXED ? pcg::SrTile<float>::TX : pcg::SrTile<double>::TX;
+        h->grid_sr = dim3((h->nx + tx - 1) / tx, (h->ny + pcg::SR_TY - 1) / pcg::SR_TY, h->nrhs);
         h->nblk_sr = (int)(h->grid_sr.x * h->grid_sr.y);
         h->ppl += h->ppl & 1;   // passes alternate the r, s, w buffers: an even count ends where it began
     }
@@ -1427,7 +1456,9 @@ void pcg_destroy(pcg_t h) {
     if (h->graph64) cudaGraphExecDestroy(h->graph64);
     if (h->graph32) cudaGraphExecDestroy(h->graph32);
     if (h->graph_sr) cudaGraphExecDestroy(h->graph_sr);
-    for (void* p : {(void*)h->r64b, (void*)h->s64b, (void*)h->w64a, (void*)h->w64b})
+    if (h->graph_sr32) cudaGraphExecDestroy(h->graph_sr32);
+    for (void* p : {(void*)h->r64b, (void*)h->s64b, (void*)h->w64a, (void*)h->w64b, (void*)h->r32b, (void*)h->s32b,
+                    (void*)h->w32a, (void*)h->w32b})
         if (p) cudaFree(p);
     for (void* p : {(void*)h->u64, (void*)h->r64, (void*)h->z64, (void*)h->p64, (void*)h->q64, (void*)h->u32,
                     (void*)h->r32, (void*)h->z32, (void*)h->p32, (void*)h->q32, (void*)h->hb, (void*)h->hx,

@@ -22,13 +22,20 @@
 
 namespace pcg {
 
-constexpr int SR_TX = 16, SR_TY = 4;                  // a block's own columns
-constexpr int SR_HX = SR_TX + 2, SR_HY = SR_TY + 2;   // with the ring around them
-constexpr int SR_NH = SR_HX * SR_HY;                  // 108 line solves per block
-constexpr int SR_NT = 128;                            // threads per block
-constexpr int SR_MAX_NZ = 256;                        // u of all 108 columns in shared memory
+// A block's tile of own columns, per precision: in FP32 a warp covers 32
+// columns of a row (whole 128-byte lines); in FP64 16 x 4, so that n_z x 108
+// doubles of shared memory still allow n_z up to 256.
+template <typename T>
+struct SrTile {
+    static constexpr int TX = sizeof(T) == 4 ? 32 : 16, TY = 4;
+    static constexpr int HX = TX + 2, HY = TY + 2;   // with the ring around them
+    static constexpr int NH = HX * HY;               // line solves per block: 204 (FP32), 108 (FP64)
+    static constexpr int NT = 2 * TX * TY;           // threads: a ring slot each, then two per own column
+    static_assert(NT >= NH, "phase 1 takes a ring slot per thread");
+};
+constexpr int SR_TY = 4;
+constexpr int SR_MAX_NZ = 256;                        // u of the tile and its ring in shared memory
 constexpr int SR_PB = 8;                              // levels whose loads are issued ahead
-static_assert(SR_NT == 2 * SR_TX * SR_TY && SR_NT >= SR_NH, "phase 1 takes a slot per thread, phase 2 two threads per column");
 
 // Scalar step after the reduction of pass k: the stopping test on ||r||,
 // then beta and alpha for pass k + 1.  x is current when the test fires, so
@@ -72,34 +79,42 @@ __device__ __forceinline__ void sr_epilogue(SolveState* st, double rrv, double g
     st->kappa_old = g;
 }
 
-// One pass, FP64.  Grid (ceil(n_x/16), ceil(n_y/4), nrhs), SR_NT threads,
-// n_z * SR_NH doubles of dynamic shared memory.
-//   Phase 1 (thread t < 108 takes ring slot t): s' = w + beta s,
-//   r' = r - alpha s', then the Thomas recurrences of Algorithm 3 in the
-//   c-form (y_k = r'_k + c_{k-1} y_{k-1}, t_k = y_k / D_k, gamma += t_k y_k,
-//   u_k = t_k + c_k u_{k+1}) into shared memory; own columns store r', s'
-//   and sum ||r'||^2 and gamma.
-//   Phase 2 (threads t and t + 64 take the lower and upper half of own column
-//   t): w' = A u' in flux form from shared memory (as k_apply), p' = u + beta p,
-//   x += alpha p', delta += w' u'; stores u', p', x, w'.
-// The last block to finish forms the scalars (sr_epilogue).
-__global__ __launch_bounds__(SR_NT) void k_sweep_sr(OpView<double> op, double* __restrict__ x,
-                                                    double* __restrict__ u, double* __restrict__ p,
-                                                    const double* __restrict__ r_in, double* __restrict__ r_out,
-                                                    const double* __restrict__ s_in, double* __restrict__ s_out,
-                                                    const double* __restrict__ w_in, double* __restrict__ w_out,
-                                                    SolveState* __restrict__ states, double* __restrict__ partials,
-                                                    unsigned* __restrict__ counters, int nblocks) {
-    extern __shared__ double sh_u[];   // [n_z][SR_NH]
+// One pass in precision T.  Grid (ceil(n_x/TX), ceil(n_y/4), nrhs), NT
+// threads, n_z * NH values of T in dynamic shared memory (SrTile<T>).
+//   Phase 1 (thread t < NH takes ring slot t): s' = w + beta s,
+//   r' = r - alpha s', then the Thomas recurrences of Algorithm 3 into shared
+//   memory, in FP64 in the c-form of the FP64 sweeps
+//     y_k = r'_k + c_{k-1} y_{k-1},  t_k = y_k / D_k,  u_k = t_k + c_k u_{k+1},
+//   in FP32 in the excess form of the FP32 sweeps (e = E/D, E = D - W)
+//     y_k = (r'_k - e_{k-1} y_{k-1}) + y_{k-1},  u_k = u_{k+1} + (y_k - E_k u_{k+1}) / D_k;
+//   gamma = <r', u'> = sum_k y_k^2 / D_k either way.  Own columns store r'
+//   and s' and sum ||r'||^2 and gamma (in FP32 as plain sums over 8 levels,
+//   both non-negative, added to the compensated accumulator).
+//   Phase 2 (threads t and t + TX TY take the lower and upper half of own
+//   column t): w' = A u' in flux form from shared memory (as k_apply), p' = u + beta p,
+//   x += alpha p', delta += w' u' (compensated in FP32); stores u', p', x, w'.
+// The last block to finish forms the scalars in FP64 (sr_epilogue).
+template <typename T>
+__global__ __launch_bounds__(SrTile<T>::NT) void k_sweep_sr(OpView<T> op, T* __restrict__ x, T* __restrict__ u,
+                                                    T* __restrict__ p, const T* __restrict__ r_in,
+                                                    T* __restrict__ r_out, const T* __restrict__ s_in,
+                                                    T* __restrict__ s_out, const T* __restrict__ w_in,
+                                                    T* __restrict__ w_out, SolveState* __restrict__ states,
+                                                    double* __restrict__ partials, unsigned* __restrict__ counters,
+                                                    int nblocks) {
+    constexpr bool F64 = sizeof(T) == 8;
+    constexpr int SR_TX = SrTile<T>::TX, SR_HX = SrTile<T>::HX, SR_NH = SrTile<T>::NH;
+    extern __shared__ __align__(16) unsigned char sr_smem[];
+    T* sh_u = reinterpret_cast<T*>(sr_smem);   // [n_z][NH]
     const int rhs = blockIdx.z;
     SolveState* st = states + rhs;
     if (st->done) return;
-    const double alpha = st->alpha, beta = st->beta;
+    const T alpha = (T)st->alpha, beta = (T)st->beta;
     const int nz = op.nz;
     const long long pl = op.plane, base = (long long)rhs * op.vol;
     const int i0 = blockIdx.x * SR_TX, j0 = blockIdx.y * SR_TY;
     const int tid = threadIdx.x;
-    Acc<double> acc[3];   // ||r'||^2, gamma, delta over the block's own columns
+    Acc<T> acc[3];   // ||r'||^2, gamma, delta over the block's own columns
     if (tid < SR_NH) {
         const int hx = tid % SR_HX, hy = tid / SR_HX;
         int i = i0 + hx - 1, j = j0 + hy - 1;
@@ -111,12 +126,12 @@ __global__ __launch_bounds__(SR_NT) void k_sweep_sr(OpView<double> op, double* _
         const long long c = (long long)j * op.nx + i;
         const int cls = op.cls_mode == 0 ? 0 : (op.cls_mode == 1 ? j : (int)c);
         const long long fs = op.ncls;
-        const double* fg = op.fg + cls;
-        const double* fc = op.fc + cls;
+        const T* fg = op.fg + cls;
+        const T* fx = (F64 ? op.fc : op.fe) + cls;   // c = W/D (FP64) or E = D - W (FP32)
         const long long o0 = base + c;
         // the loads of the next SR_PB levels are issued before the current SR_PB are computed
-        double ra[SR_PB], sa[SR_PB], wa[SR_PB];
-        auto fetch = [&](int kb, double(&vr)[SR_PB], double(&vs)[SR_PB], double(&vw)[SR_PB]) {
+        T ra[SR_PB], sa[SR_PB], wa[SR_PB];
+        auto fetch = [&](int kb, T(&vr)[SR_PB], T(&vs)[SR_PB], T(&vw)[SR_PB]) {
 #pragma unroll
             for (int t = 0; t < SR_PB; ++t) {
                 const int k = kb + t;
@@ -129,27 +144,45 @@ __global__ __launch_bounds__(SR_NT) void k_sweep_sr(OpView<double> op, double* _
             }
         };
         fetch(0, ra, sa, wa);
-        double y = 0.0, cprev = 0.0;
+        T y = T(0), cprev = T(0);   // cprev: c_{k-1} (FP64) or e_{k-1} = E_{k-1} / D_{k-1} (FP32)
         for (int kb = 0; kb < nz; kb += SR_PB) {
-            double rx[SR_PB], sx[SR_PB], wx[SR_PB];
+            T rx[SR_PB], sx[SR_PB], wx[SR_PB];
             fetch(kb + SR_PB, rx, sx, wx);
+            T rr_chunk = T(0), g_chunk = T(0);
 #pragma unroll
             for (int t = 0; t < SR_PB; ++t) {
                 const int k = kb + t;
                 if (k < nz) {
                     const long long o = o0 + (long long)k * pl;
-                    const double sn = fma(beta, sa[t], wa[t]);
-                    const double rn = fma(-alpha, sn, ra[t]);
-                    y = fma(cprev, y, rn);
-                    const double tk = ldro(fg + k * fs) * y;
+                    const T sn = fma(beta, sa[t], wa[t]);
+                    const T rn = fma(-alpha, sn, ra[t]);
+                    const T gk = ldro(fg + k * fs);
+                    if constexpr (F64) {
+                        y = fma(cprev, y, rn);
+                        const T tk = gk * y;
+                        if (own) {
+                            acc[0].add_prod(rn, rn);
+                            acc[1].add_prod(tk, y);
+                        }
+                        sh_u[k * SR_NH + tid] = tk;
+                        cprev = ldro(fx + k * fs);
+                    } else {
+                        y = fma(-cprev, y, rn) + y;
+                        rr_chunk = fma(rn, rn, rr_chunk);
+                        g_chunk = fma(gk * y, y, g_chunk);
+                        sh_u[k * SR_NH + tid] = y;
+                        cprev = ldro(fx + k * fs) * gk;
+                    }
                     if (own) {
                         s_out[o] = sn;
                         r_out[o] = rn;
-                        acc[0].add_prod(rn, rn);
-                        acc[1].add_prod(tk, y);
                     }
-                    sh_u[k * SR_NH + tid] = tk;
-                    cprev = ldro(fc + k * fs);
+                }
+            }
+            if constexpr (!F64) {
+                if (own) {
+                    acc[0].add(rr_chunk);
+                    acc[1].add(g_chunk);
                 }
             }
 #pragma unroll
@@ -159,10 +192,12 @@ __global__ __launch_bounds__(SR_NT) void k_sweep_sr(OpView<double> op, double* _
                 wa[t] = wx[t];
             }
         }
-        double un = 0.0;
+        T un = T(0);
         for (int k = nz - 1; k >= 0; --k) {
-            un = fma(ldro(fc + k * fs), un, sh_u[k * SR_NH + tid]);
-            sh_u[k * SR_NH + tid] = un;
+            T* sk = sh_u + k * SR_NH + tid;
+            if constexpr (F64) un = fma(ldro(fx + k * fs), un, *sk);
+            else un = fma(ldro(fg + k * fs), fma(-ldro(fx + k * fs), un, *sk), un);
+            *sk = un;
         }
     }
     __syncthreads();
@@ -171,13 +206,13 @@ __global__ __launch_bounds__(SR_NT) void k_sweep_sr(OpView<double> op, double* _
         // from below is recomputed at the split, with the same operands)
         const int oc = tid % (SR_TX * SR_TY), half = tid / (SR_TX * SR_TY);
         const int tx = oc % SR_TX, ty = oc / SR_TX;
-        const Col<double> col = make_col(op, i0 + tx, j0 + ty);
+        const Col<T> col = make_col(op, i0 + tx, j0 + ty);
         const int k0 = half * (nz / 2), k1 = half ? nz : nz / 2;
         if (col.valid && k0 < k1) {
             const int sc = (ty + 1) * SR_HX + tx + 1;
             const long long o0 = base + col.c;
-            double pa[SR_PB], ua[SR_PB], xa[SR_PB];
-            auto fetch = [&](int kb, double(&vp)[SR_PB], double(&vu)[SR_PB], double(&vx)[SR_PB]) {
+            T pa[SR_PB], ua[SR_PB], xa[SR_PB];
+            auto fetch = [&](int kb, T(&vp)[SR_PB], T(&vu)[SR_PB], T(&vx)[SR_PB]) {
 #pragma unroll
                 for (int t = 0; t < SR_PB; ++t) {
                     const int k = kb + t;
@@ -190,26 +225,25 @@ __global__ __launch_bounds__(SR_NT) void k_sweep_sr(OpView<double> op, double* _
                 }
             };
             fetch(k0, pa, ua, xa);
-            double zc = sh_u[k0 * SR_NH + sc];
-            double fprev = k0 > 0 ? ldro(op.wv + k0 - 1) * (sh_u[(k0 - 1) * SR_NH + sc] - zc) : 0.0;
+            T zc = sh_u[k0 * SR_NH + sc];
+            T fprev = k0 > 0 ? ldro(op.wv + k0 - 1) * (sh_u[(k0 - 1) * SR_NH + sc] - zc) : T(0);
             for (int kb = k0; kb < k1; kb += SR_PB) {
-                double px[SR_PB], ux[SR_PB], xx[SR_PB];
+                T px[SR_PB], ux[SR_PB], xx[SR_PB];
                 fetch(kb + SR_PB, px, ux, xx);
 #pragma unroll
                 for (int t = 0; t < SR_PB; ++t) {
                     const int k = kb + t;
                     if (k < k1) {
-                        const double* sl = sh_u + k * SR_NH;
-                        const double zu = (k + 1 < nz) ? sl[SR_NH + sc] : zc;
-                        const double f = ldro(op.wv + k) * (zc - zu);
-                        double h = col.me * (zc - sl[sc + 1]);
+                        const T* sl = sh_u + k * SR_NH;
+                        const T zu = (k + 1 < nz) ? sl[SR_NH + sc] : zc;
+                        const T f = ldro(op.wv + k) * (zc - zu);
+                        T h = col.me * (zc - sl[sc + 1]);
                         h = fma(col.mw, zc - sl[sc - 1], h);
                         h = fma(col.mn, zc - sl[sc + SR_HX], h);
                         h = fma(col.ms, zc - sl[sc - SR_HX], h);
-                        const double wn =
-                            fma(ldro(op.dk + k), h, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+                        const T wn = fma(ldro(op.dk + k), h, col.area * fma(ldro(op.mass + k), zc, f - fprev));
                         const long long o = o0 + (long long)k * pl;
-                        const double pn = fma(beta, pa[t], ua[t]);
+                        const T pn = fma(beta, pa[t], ua[t]);
                         x[o] = fma(alpha, pn, xa[t]);
                         p[o] = pn;
                         u[o] = zc;

@@ -63,11 +63,11 @@ def test_create_rejects_bad_arguments(lib, field, value):
 
 
 @pytest.mark.parametrize("over", [{"preconditioner": 5}, {"preconditioner": 1, "precision": 1}, {"precision": 3},
-                                  {"algorithm": 2}, {"algorithm": 1, "precision": 1},
-                                  {"algorithm": 1, "preconditioner": 1}, {"algorithm": 1, "preconditioner": 2}])
+                                  {"algorithm": 2}, {"algorithm": 1, "preconditioner": 1},
+                                  {"algorithm": 1, "preconditioner": 2}])
 def test_create_rejects_bad_options(lib, over):
     # unknown preconditioner; multigrid is FP64 only; unknown precision; unknown
-    # algorithm; the single-reduction sweep is FP64 with the line preconditioner only
+    # algorithm; the single-reduction sweep has the line preconditioner only
     rc, h, msg, _ = _create(W.small_box(), **over)
     assert rc == pkg.PCG_ERR_INVALID_ARG and not h.value, (rc, msg)
     assert msg

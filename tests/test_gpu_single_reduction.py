@@ -10,12 +10,15 @@ Chronopoulos-Gear form cited in Section 4.2) with the oracle's
   iterations, and the reported true residual is the oracle's evaluation.
 * A batch of right-hand sides equals its single solves bitwise; b = 0,
   warm starts and maxit = 0 behave as in Algorithm 1's path.
+* The mixed form with the single-reduction inner solve (FP32 sweep, excess-
+  form Thomas, compensated sums) reaches the FP64 oracle's solution to 1e-8,
+  and its batch equals its single solves bitwise.
 """
 import numpy as np
 import pytest
 
 import workloads as W
-from oracle import FluxOperator, LinePreconditioner, assemble_csr, pcg_single_reduction
+from oracle import FluxOperator, LinePreconditioner, assemble_csr, pcg_interleaved, pcg_single_reduction
 
 pytestmark = pytest.mark.gpu
 
@@ -115,3 +118,34 @@ def test_zero_rhs_and_warm_start_and_maxit0(torch_cuda):
         st3 = s.solve(_dev(torch, b), x0, tol=1e-8, maxit=0)
         assert st3.status == 4 and st3.iterations == 0
         assert bool((x0 == 0.25).all())
+
+
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_mixed_matches_fp64_oracle(torch_cuda, name, p):
+    torch = torch_cuda
+    b = W.rhs_for(p, seed=0, smooth=(p.kind == W.GEOM_BOX))
+    ref = pcg_interleaved(FluxOperator(p), LinePreconditioner(assemble_csr(p), p), b, eps=1e-12, maxiter=20000)
+    with _solver(p, precision="mixed") as s:
+        x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        st = s.solve(_dev(torch, b), x, tol=1e-10, maxit=20000)
+    assert st.status == 0, st
+    err = np.linalg.norm(x.cpu().numpy().reshape(p.shape) - ref.x) / np.linalg.norm(ref.x)
+    assert err < 1e-8, (err, st)
+
+
+def test_mixed_batch_equals_single_bitwise(torch_cuda):
+    torch = torch_cuda
+    p = W.box_problem(40, 24, 12, 0.01)
+    bs = W.batched_rhs(p, [0, 5, 9])
+    bs[1] *= 1e-3
+    with _solver(p, nrhs=3, precision="mixed") as s:
+        xb = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
+        s.solve(_dev(torch, bs), xb, tol=1e-9, maxit=5000)
+        stats = [s.pcg_rhs_stats(r) for r in range(3)]
+    xb = xb.cpu().numpy().reshape(bs.shape)
+    with _solver(p, precision="mixed") as s1:
+        for r in range(3):
+            x1 = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+            st = s1.solve(_dev(torch, bs[r]), x1, tol=1e-9, maxit=5000)
+            assert st.iterations == stats[r].iterations and st.outer_sweeps == stats[r].outer_sweeps
+            assert np.array_equal(x1.cpu().numpy().reshape(p.shape), xb[r])
