@@ -141,3 +141,22 @@ def test_fp32_vcycle_inside_fp64_cg(torch_cuda, name, p):
     assert st.iterations <= 1.3 * ref_mg.iterations + 3, (st.iterations, ref_mg.iterations)
     xg = x.cpu().numpy().reshape(p.shape)
     assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) < 1e-8
+
+
+def test_mg_f32_batch_equals_single_bitwise(torch_cuda):
+    import paper_1302_7193_gb300 as pkg
+    torch = torch_cuda
+    p = W.box_problem(32, 16, 12, 0.01)
+    bs = W.batched_rhs(p, [0, 5, 9])
+    bs[1] *= 1e-3
+    with pkg.Solver(p, nrhs=3, preconditioner="multigrid-f32") as s:
+        xb = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
+        s.solve(_dev(torch, bs), xb, tol=1e-9, maxit=500)
+        stats = [s.pcg_rhs_stats(r) for r in range(3)]
+    xb = xb.cpu().numpy().reshape(bs.shape)
+    with pkg.Solver(p, preconditioner="multigrid-f32") as s1:
+        for r in range(3):
+            x1 = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+            st = s1.solve(_dev(torch, bs[r]), x1, tol=1e-9, maxit=500)
+            assert st.iterations == stats[r].iterations
+            assert np.array_equal(x1.cpu().numpy().reshape(p.shape), xb[r])
