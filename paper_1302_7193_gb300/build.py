@@ -17,6 +17,7 @@ LIB = os.path.join(HERE, "libpcg.so")
 SOURCES = [os.path.join(HERE, "csrc", "pcg.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "kernels.cuh"), os.path.join(HERE, "csrc", "serve.cuh"),
                   os.path.join(HERE, "csrc", "multigrid.cuh"),
+                  os.path.join(HERE, "csrc", "single_reduction.cuh"), os.path.join(HERE, "csrc", "serve_kernels.cuh"),
                   os.path.join(ROOT, "include", "pcg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1361,167 +1361,6 @@ __global__ __launch_bounds__(256, 2) void k_sweep_prec_tma(
 }
 
 // ---------------------------------------------------------------------------
-// Served batch: persistent sweeps over work lists of (request slot, item).
-//
-// Every admitted request owns a slot with its own tables, vectors, partials,
-// arrival counter and scalar state.  One launch of each kernel walks all
-// items of all requests in the inner phase (grid-stride), so many small
-// solves fill the GPU together; the last item of a request to finish forms
-// that request's scalars exactly as the per-solve kernels do, so a request's
-// arithmetic does not depend on which other requests share the launch.
-//   k_serve_prec: 256-thread blocks; an item is `rows` rows of 32 columns,
-//     each column split into nch chunks of 16 levels (one warp per chunk,
-//     prec_chunked_body); columns of more than 128 levels take one thread
-//     per column (8 rows per item, prec_column).
-//   k_serve_spmv: 128-thread blocks; an item is a 32 x 4-column tile of one
-//     16-level chunk, staged in shared memory by bulk tensor copies (tensor
-//     maps of the request in device memory) or, when the request's rows are
-//     not 16-byte multiples, by the threads; then spmv_tile_compute.
-// ---------------------------------------------------------------------------
-constexpr int SERVE_LZ = 16, SERVE_BY = 4;
-
-struct ServeSlot {
-    OpView<float> op;           // FP32 tables of the request
-    float *u, *r, *z, *p, *q;   // inner FP32 vectors
-    SolveState* st;             // inner state
-    double* partials;           // [max(nprec, nspmv)][4]
-    unsigned* counter;
-    int gx;                     // tiles of 32 columns per row
-    int nch;                    // chunks of 16 levels per column
-    int rows;                   // preconditioner: rows per item
-    int colmode;                // preconditioner: 1 = one thread per column (n_z > 128)
-    int nprec;                  // preconditioner items
-    int nspmv;                  // SpMV items: gx * ceil(n_y / 8) * nch
-    const CUtensorMap* tmaps;   // [4] u, p, q, z (boxes as k_sweep_spmv_tma), or null
-};
-
-template <int MINB>
-__global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __restrict__ slots,
-                                                         const int2* __restrict__ items,
-                                                         const int* __restrict__ n_items) {
-    __shared__ float sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
-    const int n = *n_items;
-    const int lane = threadIdx.x, w = threadIdx.y;
-    for (int it = blockIdx.x; it < n; it += gridDim.x) {
-        const int2 wk = items[it];
-        const ServeSlot& s = slots[wk.x];
-        SolveState* st = s.st;
-        if (!st->done) {
-            const float alpha = (float)st->alpha;
-            const int bx = wk.y % s.gx, jb = wk.y / s.gx;
-            Acc<float> acc[2];
-            if (s.colmode) {
-                const Col<float> col = make_col(s.op, bx * 32 + lane, jb * 8 + w);
-                if (col.valid) prec_column<float>(s.op, col, s.r + col.c, s.q + col.c, s.z + col.c, alpha, acc[0], acc[1]);
-            } else {
-                // warp w: row w / nch of the item, chunk w % nch; warps past
-                // rows * nch only take part in the barriers
-                const int row = w / s.nch, ch = w - row * s.nch;
-                const int j = row < s.rows ? jb * s.rows + row : s.op.ny;
-                const Col<float> col = make_col(s.op, bx * 32 + lane, j);
-                prec_chunked_body<float, SERVE_LZ>(s.op, col, lane, ch, s.nch, row * s.nch, s.r, s.q, s.z, alpha, acc,
-                                                   sh_y, sh_c, sh_z, sh_d);
-            }
-            double v[2];
-            if (grid_sum_acc<2>(acc, s.partials, s.counter, s.nprec, wk.y, v)) prec_epilogue(st, v[0], v[1]);
-        }
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(reinterpret_cast<uint64_t>(m)) : "memory");
-}
-
-__global__ __launch_bounds__(BX * SERVE_BY) void k_serve_spmv(const ServeSlot* __restrict__ slots,
-                                                             const int2* __restrict__ items,
-                                                    const int* __restrict__ n_items) {
-    using TT = SpmvTmaTile<SERVE_LZ, SERVE_BY>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float* zs = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float* us = zs + TT::ZN;
-    float* ps = us + TT::VN;
-    float* qs = ps + TT::VN;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(qs + TT::VN);
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const uint32_t b = smem_u32(bar);
-    if (tid == 0) mbar_init(b);
-    __syncthreads();
-    uint32_t parity = 0;
-    bool broken = false;        // a staged copy timed out: this block computes nothing more
-    int last_slot = -1;         // slot whose tensor maps thread 0 acquired last
-    const int n = *n_items;
-    for (int it = blockIdx.x; it < n; it += gridDim.x) {
-        const int2 wk = items[it];
-        const ServeSlot& s = slots[wk.x];
-        SolveState* st = s.st;
-        if (!st->done) {
-            const OpView<float>& op = s.op;
-            const int ch = wk.y % s.nch, tile = wk.y / s.nch;
-            const int i0 = (tile % s.gx) * BX, j0 = (tile / s.gx) * SERVE_BY, k0 = ch * SERVE_LZ;
-            const int kn = min(SERVE_LZ, op.nz - k0);
-            bool landed = !broken;
-            if (broken) {
-                if (tid == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT: this item is not computed
-            } else if (s.tmaps) {
-                if (tid == 0) {
-                    if (wk.x != last_slot) {
-                        for (int m = 0; m < 4; ++m) tmap_acquire(s.tmaps + m);
-                        last_slot = wk.x;
-                    }
-                    // earlier items may have written the tiles through the generic proxy
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect(b, TT::BYTES);
-                    tma_load_3d(smem_u32(zs), s.tmaps + 3, i0 - TMA_HALO_X, j0 - 1, k0 - 1, b);
-                    tma_load_3d(smem_u32(us), s.tmaps + 0, i0, j0, k0, b);
-                    tma_load_3d(smem_u32(ps), s.tmaps + 1, i0, j0, k0, b);
-                    tma_load_3d(smem_u32(qs), s.tmaps + 2, i0, j0, k0, b);
-                }
-                // one verdict for the whole block
-                landed = __syncthreads_and(mbar_wait(b, parity, 1 << 22) ? 1 : 0) != 0;
-                if (!landed) {
-                    if (tid == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT
-                    mbar_wait(b, parity, 1 << 22);
-                    broken = true;
-                }
-                parity ^= 1u;
-            } else {
-                // staged by the threads, cells outside the grid as zeros
-                constexpr int NTH = BX * SERVE_BY;
-                for (int e = tid; e < TT::ZN; e += NTH) {
-                    const int xx = e % TT::ZX, yy = (e / TT::ZX) % TT::ZY, zz = e / (TT::ZX * TT::ZY);
-                    const int gi = i0 - TMA_HALO_X + xx, gj = j0 - 1 + yy, gk = k0 - 1 + zz;
-                    const bool in = gi >= 0 && gi < op.nx && gj >= 0 && gj < op.ny && gk >= 0 && gk < op.nz;
-                    zs[e] = in ? ldro(s.z + (long long)gk * op.plane + (long long)gj * op.nx + gi) : 0.f;
-                }
-                for (int e = tid; e < TT::VN; e += NTH) {
-                    const int xx = e % BX, yy = (e / BX) % SERVE_BY, zz = e / (BX * SERVE_BY);
-                    const int gi = i0 + xx, gj = j0 + yy, gk = k0 + zz;
-                    const bool in = gi < op.nx && gj < op.ny && gk < op.nz;
-                    const long long o = (long long)gk * op.plane + (long long)gj * op.nx + gi;
-                    us[e] = in ? s.u[o] : 0.f;
-                    ps[e] = in ? s.p[o] : 0.f;
-                    qs[e] = in ? s.q[o] : 0.f;
-                }
-                __syncthreads();
-            }
-            Acc<float> sig[1];
-            const Col<float> col = make_col(op, i0 + tx, j0 + ty);
-            if (landed && col.valid && kn > 0) {
-                const bool in_e = col.ce == col.c + 1, in_w = col.cw == col.c - 1;
-                const bool in_n = col.cn == col.c + op.nx, in_s = col.cs == col.c - op.nx;
-                spmv_tile_compute<SERVE_LZ, SERVE_BY>(op, col, tx, ty, k0, kn, zs, us, ps, qs, s.z, s.u, s.p, s.q,
-                                                      (float)st->alpha, (float)st->beta, in_e, in_w, in_n, in_s,
-                                                      sig[0]);
-            }
-            double v[1];
-            if (grid_sum_acc<1>(sig, s.partials, s.counter, s.nspmv, wk.y, v)) spmv_epilogue(st, v[0]);
-        }
-        __syncthreads();    // the tiles are refilled by the next item
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Residual r = b - A x in FP64, with reductions of <b,b>, <r,r>, sum(r) and
 // the rounding floor sum_i ulp(x_i)^2/12 ||A e_i||^2 (the expected squared
 // residual of x rounded to FP64: no FP64 vector gets closer to b than this).

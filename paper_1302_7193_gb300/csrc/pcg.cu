@@ -23,6 +23,7 @@
 #include "kernels.cuh"
 #include "multigrid.cuh"
 #include "single_reduction.cuh"
+#include "serve_kernels.cuh"
 
 using pcg::BX;
 using pcg::BY;

@@ -45,7 +45,8 @@ struct ServeReq {
     double total_mass = 0.0;
     int gx = 0, gy = 0, ntiles = 0;          // 32 x 4 tiles (residual kernels)
     int nch = 1, rows = 1, colmode = 0, nprec = 0, nspmv = 0;   // served sweep items
-    CUtensorMap* tmaps = nullptr;            // device copies of the u, p, q, z maps, or null
+    CUtensorMap* tmaps = nullptr;            // device copies of the u, p, q, z maps and the r, q item maps, or null
+    int prec_tma = 0;                        // the preconditioner items are staged (maps 4 and 5)
     std::vector<double> hist;
     double bb = 0.0, last_rr = 0.0, floor_rel = 0.0;
     int sweeps = 0, inner_its = 0, status = PCG_NOT_CONVERGED, stag = 0;
@@ -83,6 +84,7 @@ struct pcg_server {
     cudaGraphExec_t graph = nullptr;
     int blocks_prec = 152 * 3, blocks_spmv = 152 * 2;   // persistent grids (resident blocks on every SM)
     int no_tma = 0;                     // PCG_SERVE_TMA=0: stage the SpMV tiles by the threads
+    int no_prec_tma = 0;                // PCG_SERVE_PREC_TMA=0: preconditioner items read r, q directly
     int prec_minb = 2;                  // PCG_SERVE_PREC_MINB=3: preconditioner kernel with 3 blocks per SM
     long long active_cap = 0;           // PCG_SERVE_ACTIVE: admit while the admitted unknowns stay below this (0: no cap)
     long long active_unknowns = 0;      // unknowns of the admitted requests
@@ -141,7 +143,7 @@ size_t request_bytes(const pcg_grid_t& g, int cls_mode) {
     const ServeItems it = serve_items(g);
     const size_t nparts = std::max(ntiles, (size_t)std::max(it.nprec, it.nspmv));
     return align_up(ntab * 8) + align_up(ntab * 4) + 2 * align_up(vol * 8) + 5 * align_up(vol * 4) +
-           align_up(nparts * 4 * 8) + align_up(4 * sizeof(CUtensorMap)) + 256;
+           align_up(nparts * 4 * 8) + align_up(6 * sizeof(CUtensorMap)) + 256;
 }
 
 int admit(pcg_server_t s, ServeReq* q) {
@@ -185,7 +187,7 @@ int admit(pcg_server_t s, ServeReq* q) {
     q->partials = (double*)m;
     m += align_up((size_t)std::max(q->ntiles, std::max(q->nprec, q->nspmv)) * 4 * 8);
     q->tmaps = (CUtensorMap*)m;             // 256-byte aligned like every carved region
-    m += align_up(4 * sizeof(CUtensorMap));
+    m += align_up(6 * sizeof(CUtensorMap));
     q->counter = (unsigned*)m;
     // tables: same carving as a solver handle
     auto carve = [&](auto& op, auto* base) {
@@ -218,19 +220,25 @@ int admit(pcg_server_t s, ServeReq* q) {
     SRV_CK(s, cudaMemsetAsync(q->xd, 0, vol * 8, st));
     SRV_CK(s, cudaMemsetAsync(q->counter, 0, sizeof(unsigned), st));
     {
-        // tensor maps of the SpMV sweep's staged tiles (boxes as k_sweep_spmv_tma);
-        // without them the tiles are staged by the threads
-        CUtensorMap hm[4];
+        // tensor maps of the SpMV sweep's staged tiles (boxes as k_sweep_spmv_tma)
+        // and of the preconditioner items' r and q (32 columns x rows x all
+        // chunks); without them the threads stage the tiles and read r, q
+        CUtensorMap hm[6];
         const unsigned zx = BX + 2 * pcg::TMA_HALO_X;
         const bool ok = encode_map_dims(&hm[0], q->u, nx, ny, nz, BX, pcg::SERVE_BY, pcg::SERVE_LZ) &&
                         encode_map_dims(&hm[1], q->p, nx, ny, nz, BX, pcg::SERVE_BY, pcg::SERVE_LZ) &&
                         encode_map_dims(&hm[2], q->q, nx, ny, nz, BX, pcg::SERVE_BY, pcg::SERVE_LZ) &&
                         encode_map_dims(&hm[3], q->z, nx, ny, nz, zx, pcg::SERVE_BY + 2, pcg::SERVE_LZ + 2);
+        const unsigned pz = (unsigned)(q->nch * pcg::SERVE_LZ);
+        q->prec_tma = ok && !s->no_prec_tma && !q->colmode && (unsigned)q->rows * pz <= (unsigned)(8 * pcg::SERVE_LZ) &&
+                      encode_map_dims(&hm[4], q->r, nx, ny, nz, BX, (unsigned)q->rows, pz) &&
+                      encode_map_dims(&hm[5], q->q, nx, ny, nz, BX, (unsigned)q->rows, pz);
         if (ok && !s->no_tma) {
             // pageable source: the call returns once the maps have been staged
             SRV_CK(s, cudaMemcpyAsync(q->tmaps, hm, sizeof(hm), cudaMemcpyHostToDevice, st));
         } else {
             q->tmaps = nullptr;
+            q->prec_tma = 0;
         }
     }
     SRV_CK(s, cudaGetLastError());
@@ -254,6 +262,7 @@ int admit(pcg_server_t s, ServeReq* q) {
     hs.nprec = q->nprec;
     hs.nspmv = q->nspmv;
     hs.tmaps = q->tmaps;
+    hs.prec_tma = q->prec_tma;
     SRV_CK(s, cudaMemcpyAsync(s->d_slots + slot, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
     pcg::k_init_state<<<1, 32, 0, st>>>(s->d_states + 2 * slot, 2, 0.0, 0, nullptr);
     s->launches += 1;
@@ -382,9 +391,11 @@ int capture_epochs(pcg_server_t s) {
     SRV_CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int e = 0; e < s->epochs_per_launch; ++e) {
         if (s->prec_minb == 3)
-            pcg::k_serve_prec<3><<<s->blocks_prec, dim3(BX, 8, 1), 0, s->cap_stream>>>(s->d_slots, s->d_items, s->d_nitems);
+            pcg::k_serve_prec<3><<<s->blocks_prec, dim3(BX, 8, 1), pcg::SERVE_PREC_SMEM, s->cap_stream>>>(
+                s->d_slots, s->d_items, s->d_nitems);
         else
-            pcg::k_serve_prec<2><<<s->blocks_prec, dim3(BX, 8, 1), 0, s->cap_stream>>>(s->d_slots, s->d_items, s->d_nitems);
+            pcg::k_serve_prec<2><<<s->blocks_prec, dim3(BX, 8, 1), pcg::SERVE_PREC_SMEM, s->cap_stream>>>(
+                s->d_slots, s->d_items, s->d_nitems);
         pcg::k_serve_spmv<<<s->blocks_spmv, dim3(BX, pcg::SERVE_BY, 1), ServeSpmvTile::SMEM, s->cap_stream>>>(
             s->d_slots, s->d_items + s->items_cap, s->d_nitems + 1);
     }
@@ -458,6 +469,7 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (const char* e2 = std::getenv("PCG_SERVE_TMA")) s->no_tma = std::atoi(e2) == 0 ? 1 : 0;
+    if (const char* e5 = std::getenv("PCG_SERVE_PREC_TMA")) s->no_prec_tma = std::atoi(e5) == 0 ? 1 : 0;   // experiments
     // persistent grids: as many blocks as are resident on every SM at once
     if ((e = cudaFuncSetAttribute(pcg::k_serve_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)ServeSpmvTile::SMEM)) != cudaSuccess) {
@@ -465,11 +477,17 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
         return bail(PCG_ERR_CUDA);
     }
     if (const char* e3 = std::getenv("PCG_SERVE_PREC_MINB")) s->prec_minb = std::atoi(e3) == 3 ? 3 : 2;
+    for (auto fn : {pcg::k_serve_prec<2>, pcg::k_serve_prec<3>})
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcg::SERVE_PREC_SMEM)) !=
+            cudaSuccess) {
+            s->err = cudaGetErrorString(e);
+            return bail(PCG_ERR_CUDA);
+        }
     if (const char* e4 = std::getenv("PCG_SERVE_ACTIVE")) s->active_cap = std::atoll(e4);
     int occ_a = 0, occ_b = 0;
     cudaError_t eo = s->prec_minb == 3
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<3>, BX * 8, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<2>, BX * 8, 0);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<3>, BX * 8, pcg::SERVE_PREC_SMEM)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<2>, BX * 8, pcg::SERVE_PREC_SMEM);
     if (eo != cudaSuccess || occ_a < 1) occ_a = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, pcg::k_serve_spmv, BX * pcg::SERVE_BY,
                                                       ServeSpmvTile::SMEM) != cudaSuccess || occ_b < 1)

@@ -4,7 +4,10 @@
   while it runs (requests admitted and retired around it): bitwise, because
   a request's arithmetic does not depend on the others; the bar asked of the
   mixed path (1e-8 relative) is asserted as well.
-* Served results match the FP64 oracle to 1e-8.
+* Served results match the FP64 oracle to 1e-8, also in a mix that takes
+  every path of the preconditioner items at once: staged by bulk tensor
+  copies (with a box deeper than the grid), read directly (rows that are not
+  16-byte multiples) and one thread per column (more than 128 levels).
 * Admission respects the device-byte budget; a request larger than the budget
   is refused at submission; a request with a non-finite right-hand side ends
   in breakdown without disturbing the others.
@@ -116,3 +119,24 @@ def test_oversize_and_bad_requests(pkg):
         res = _drain(srv, [good_id, bad_id])
     assert res[good_id][1].status == 0
     assert res[bad_id][1].status == pkg.PCG_BREAKDOWN
+
+
+def test_every_preconditioner_path_in_one_mix(pkg):
+    probs = [W.box_problem(18, 10, 12, 0.01, name="rows-not-16B"),
+             W.box_problem(8, 8, 160, 0.01, name="column-mode"),
+             W.box_problem(40, 24, 40, 0.01, alpha="sin", name="staged-deep-box"),
+             W.latlon_problem(36, 16, 24, name="latlon-staged")]
+    mix = [(p, W.rhs_for(p, seed=i + 3)) for i, p in enumerate(probs)]
+    with pkg.Server(budget_bytes=1 << 30, max_slots=8) as srv:
+        ids = [srv.submit(q, bq, tol=1e-10) for q, bq in mix]
+        res = _drain(srv, list(ids))
+    for (p, b), rid in zip(mix, ids):
+        x, st = res[rid]
+        assert st.status == 0, (p.name, st)
+        ref = pcg_interleaved(FluxOperator(p), LinePreconditioner(assemble_csr(p), p), b, eps=1e-12, maxiter=20000)
+        assert np.linalg.norm(x - ref.x.ravel()) / np.linalg.norm(ref.x) < 1e-8, p.name
+    for k in (0, 1, 2):
+        with pkg.Server(budget_bytes=1 << 30, max_slots=8) as srv:
+            rid = srv.submit(*mix[k], tol=1e-10)
+            x_alone, st_alone = _drain(srv, [rid])[rid]
+        assert np.array_equal(x_alone, res[ids[k]][0]), probs[k].name
