@@ -86,7 +86,7 @@ enum pcg_preconditioner {
 enum pcg_algorithm {
     PCG_ALG_INTERLEAVED = 0,      /* Algorithm 1 of the paper: a preconditioner sweep and an SpMV sweep per
                                      iteration, two grid-wide reductions */
-    PCG_ALG_SINGLE_REDUCTION = 1  /* the Chronopoulos-Gear rearrangement cited in Section 4.2: one sweep and one
+    PCG_ALG_SINGLE_REDUCTION = 1  /* the Chronopoulos-Gear rearrangement cited in Section 4.3: one sweep and one
                                      reduction per iteration, the line solves of each tile's ring of neighbouring
                                      columns recomputed by the tile.  With PCG_FP64 it is the whole solve, with
                                      PCG_MIXED the FP32 inner solve.  PCG_PREC_LINE and n_z <= 256 only; other

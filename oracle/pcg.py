@@ -139,7 +139,7 @@ def pcg_single_reduction(A, precond: Callable, b: np.ndarray, x0: Optional[np.nd
                          eps: float = 1e-8, maxiter: int = 10000, tau: float = 0.0) -> PCGResult:
     """PCG with one reduction phase per iteration (Chronopoulos and Gear, 1989).
 
-    Section 4.2 of the paper points to this rearrangement of CG (fused loops
+    Section 4.3 of the paper points to this rearrangement of CG (fused loops
     with the inner products gathered in one place).  With u = M^{-1} r,
     w = A u, gamma = <r, u> and delta = <w, u>, the step lengths come from
     one reduction:

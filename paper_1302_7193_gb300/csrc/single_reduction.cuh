@@ -1,7 +1,7 @@
 // Single-reduction PCG (PCG_ALG_SINGLE_REDUCTION): one fused sweep per
 // iteration.
 //
-// Section 4.2 of the paper points to the CG rearrangement of Chronopoulos and
+// Section 4.3 of the paper points to the CG rearrangement of Chronopoulos and
 // Gear (1989), which gathers an iteration's inner products into one
 // reduction.  With u = M^{-1} r, w = A u, gamma = <r, u> and
 // delta = <w, u>:

@@ -1,5 +1,5 @@
 """Parity of the single-reduction PCG (PCG_ALG_SINGLE_REDUCTION, the
-Chronopoulos-Gear form cited in Section 4.2) with the oracle's
+Chronopoulos-Gear form cited in Section 4.3) with the oracle's
 ``pcg_single_reduction``.
 
 * Fixed iteration counts: the GPU iterates equal the oracle's to relative

@@ -11,7 +11,7 @@
   increases (a theorem of CG in exact arithmetic, observable here to rounding).
 * Algorithm 1 produces the textbook iterates (Section 4.3: the loop is only
   a reordering of the same operations), and so does the single-reduction
-  form (Chronopoulos-Gear, cited in Section 4.2), whose alpha comes from
+  form (Chronopoulos-Gear, cited in Section 4.3), whose alpha comes from
   gamma and delta by a recurrence instead of <p, A p>: a wrong recurrence
   (a dropped beta term, the old gamma in place of the new) changes the
   iterates from the second step on.
