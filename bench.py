@@ -34,15 +34,25 @@ TOL = 1e-8
 WORKLOAD = "box256x256x128_fp64_tol1e-8"
 
 
+def _kernels_code_hash(path: str) -> str:
+    """sha256 prefix of a CUDA source with comments and blank lines removed
+    (what the compiler sees; the key of the committed ncu traffic)."""
+    import hashlib
+    import re
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lines = [re.sub(r"//.*$", "", line).rstrip() for line in src.splitlines()]
+    return hashlib.sha256("\n".join(line for line in lines if line.strip()).encode()).hexdigest()[:16]
+
+
 def _captured_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or
-    None when the kernel source has changed since the capture."""
-    import hashlib
+    None when the kernel code has changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1302_7193_gb300", "csrc", "kernels.cuh"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != d.get("kernels_cuh_sha256_16"):
+        h = _kernels_code_hash(os.path.join(ROOT, "paper_1302_7193_gb300", "csrc", "kernels.cuh"))
+        if h != d.get("kernels_cuh_code_sha256_16"):
             return None
         return d["kernels"][kernel]["dram_bytes_per_launch"]
     except Exception:

@@ -16,7 +16,7 @@
  * and top of every column.  The operator is never stored: each application recomputes the
  * stencil from per-level profiles and per-column metric terms (Section 4.2).
  * The preconditioner is the vertical-line (block-Jacobi) preconditioner
- * M = block-diag(A), one tridiagonal solve per column (Section 4.1).  The
+ * M = block-diag(A), one tridiagonal solve per column (Section 4.2).  The
  * solver is the interleaved PCG loop of Algorithm 1 (Section 4.3) with its
  * two fused grid sweeps (Algorithms 2 and 3 of the appendix).
  *
@@ -68,7 +68,7 @@ enum pcg_precision {
     PCG_MIXED = 1              /* FP32 inner PCG inside FP64 iterative refinement */
 };
 enum pcg_preconditioner {
-    PCG_PREC_LINE = 0,         /* vertical-line preconditioner M = block-diag(A) (Section 4.1) */
+    PCG_PREC_LINE = 0,         /* vertical-line preconditioner M = block-diag(A) (Section 4.2) */
     PCG_PREC_MULTIGRID = 1,    /* one V-cycle of geometric multigrid with vertical line smoothing (the
                                   solver Section 8 names as the next step): n_x, n_y halved per level
                                   while both are even, the vertical grid kept; each level the same
@@ -174,7 +174,7 @@ int pcg_rhs_stats(pcg_t h, int rhs, pcg_stats_t* stats);
  * vectors.  x and y must not overlap.  Asynchronous on the handle's stream. */
 int pcg_apply_A(pcg_t h, const double* x, double* y);
 
-/* z = M^{-1} r, M = block-diag(A) (Section 4.1; one Thomas solve per
+/* z = M^{-1} r, M = block-diag(A) (Section 4.2; one Thomas solve per
  * column), FP64 device pointers, nrhs vectors; r and z must not overlap.
  * For a handle created with PCG_PREC_MULTIGRID, z = B r: one V-cycle from a
  * zero guess.  Asynchronous on the handle's stream. */

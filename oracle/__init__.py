@@ -16,7 +16,7 @@ discretisation  explicit CSR matrix of the finite-volume operator
                 (TridiagonalMatrix); Section 4.2 stencil), assembled from the
                 problem data with scipy.sparse, and the same operator applied
                 in flux form (FluxOperator), which the solvers use.
-linesolve       vertical-line preconditioner M = block-diag(A) (Section 4.1),
+linesolve       vertical-line preconditioner M = block-diag(A) (Section 4.2),
                 solved with LAPACK's tridiagonal LU (GTTRF/GTTRS), the routines
                 of the paper's CPU code (Section 6.2); on the whole grid, or on
                 selected columns for sampled checks of very large grids.

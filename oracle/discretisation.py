@@ -291,7 +291,7 @@ def apply_rows(p: Problem, x: np.ndarray, cells) -> np.ndarray:
 
 
 def column_blocks(a: sp.csr_matrix, p: Problem):
-    """Tridiagonal column blocks of A (the matrix M of Section 4.1).
+    """Tridiagonal column blocks of A (the matrix M of Section 4.2).
 
     Returns (lower, main, upper) of shape (n_y n_x, n_z) in column-contiguous
     order (the paper's CPU layout l = n_z nu(T) + k, Eq. (MemoryMappingCPU));

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Section 4.1 of the paper builds the preconditioner by dropping the couplings
+Section 4.2 of the paper builds the preconditioner by dropping the couplings
 between different vertical columns, so that M is block diagonal with one
 symmetric tridiagonal block A_T per column; each block is solved on its own.
 This oracle forms one tridiagonal system of size n in the column-contiguous
@@ -136,7 +136,7 @@ def _flux_apply(s, w, z):
 
 
 def solve_columns(p: Problem, r_cols: np.ndarray, cols) -> np.ndarray:
-    """z = M^{-1} r on selected columns only (Section 4.1: each column's
+    """z = M^{-1} r on selected columns only (Section 4.2: each column's
     tridiagonal block A_T solved on its own), for sampled checks of very
     large grids.
 

@@ -19,7 +19,7 @@
 // and every neighbour enters through an exact difference, so A 1 = |T| m
 // exactly and near-constant vectors lose no precision to cancellation.
 //
-// Preconditioner (Section 4.1, Eq. (MatrixFreeTridiagonalSystem)): per
+// Preconditioner (Section 4.2, Eq. (MatrixFreeTridiagonalSystem)): per
 // column M = L D L^T with pivots D_k = W_k + E_k (W_k = |T| w_k the coupling
 // to level k+1, E_k >= 0 the pivot's excess over it).  With precomputed
 // g_k = 1/D_k and E_k the two Thomas sweeps read

@@ -1,6 +1,6 @@
 """Pins of the oracle's line preconditioner and PCG loops.
 
-* M = block-diag(A) (Section 4.1): the LAPACK tridiagonal solve of every
+* M = block-diag(A) (Section 4.2): the LAPACK tridiagonal solve of every
   column equals a dense LU solve of the block cut out of the assembled A;
   the column-by-column solve used for sampled checks of large grids equals
   it too.
