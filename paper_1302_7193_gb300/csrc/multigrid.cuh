@@ -168,6 +168,100 @@ __global__ __launch_bounds__(NT) void k_mg_resid(OpView<T> op, const T* __restri
     }
 }
 
+// rc = R (r - A z): the residual of the downward leg, restricted as it is
+// formed (k_mg_resid followed by k_mg_restrict, without writing t).  Blocks of
+// 32 x 2 fine columns (an even pair of rows; n_x and n_y are even on every
+// level that is restricted); blockIdx.z = rhs * ksplit + part as in
+// k_mg_resid.  Each coarse cell sums its four fine residuals in the order of
+// k_mg_restrict, ((t(2J,2I) + t(2J,2I+1)) + t(2J+1,2I)) + t(2J+1,2I+1): the
+// x pair by a shuffle, the row 2J+1 values through shared memory once per PB
+// levels.
+template <typename T, int PB>
+__global__ __launch_bounds__(64) void k_mg_resid_restrict(OpView<T> op, const T* __restrict__ r,
+                                                          const T* __restrict__ z, T* __restrict__ rc,
+                                                          const SolveState* __restrict__ st, int ksplit) {
+    __shared__ T sh[PB][32];
+    const int rhs = blockIdx.z / ksplit;
+    const int part = blockIdx.z - rhs * ksplit;
+    if (st[rhs].done) return;
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const Col<T> col = make_col(op, blockIdx.x * 32 + lane, blockIdx.y * 2 + ty);
+    const int nz = op.nz;
+    const int k0 = (int)((long long)part * nz / ksplit), k1 = (int)((long long)(part + 1) * nz / ksplit);
+    const long long pl = op.plane, base = (long long)rhs * op.vol;
+    const T* __restrict__ zb = z + base;
+    const T* __restrict__ rb = r + base + col.c;
+    const int nxc = op.nx / 2;
+    const long long planec = pl / 4;
+    const int ic = blockIdx.x * 16 + lane / 2, jc = blockIdx.y;
+    T* __restrict__ rcb = rc + (long long)rhs * planec * nz + (long long)jc * nxc + ic;
+    T qz[PB], qe[PB], qw[PB], qn[PB], qs[PB], qr[PB];
+    // lanes outside the grid (levels narrower than 32 columns) load nothing
+    // and contribute zeros, but take part in the shuffles and barriers
+    auto fetch = [&](int kb, T(&vz)[PB], T(&ve)[PB], T(&vw)[PB], T(&vn)[PB], T(&vs)[PB], T(&vr)[PB]) {
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            const int k = kb + u;
+            if (col.valid && k < k1) {
+                const T* zl = zb + (long long)k * pl;
+                vz[u] = ldro(zl + col.c);
+                ve[u] = ldro(zl + col.ce);
+                vw[u] = ldro(zl + col.cw);
+                vn[u] = ldro(zl + col.cn);
+                vs[u] = ldro(zl + col.cs);
+                vr[u] = rb[(long long)k * pl];
+            }
+        }
+    };
+    fetch(k0, qz, qe, qw, qn, qs, qr);
+    const T zend = (col.valid && k1 < nz) ? ldro(zb + (long long)k1 * pl + col.c) : T(0);
+    T fprev = (col.valid && k0 > 0) ? ldro(op.wv + k0 - 1) * (ldro(zb + (long long)(k0 - 1) * pl + col.c) - qz[0]) : T(0);
+    for (int kb = k0; kb < k1; kb += PB) {
+        T xz[PB], xe[PB], xw[PB], xn[PB], xs[PB], xr[PB];
+        fetch(kb + PB, xz, xe, xw, xn, xs, xr);
+        T tv[PB];
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            const int k = kb + u;
+            tv[u] = T(0);
+            if (col.valid && k < k1) {
+                const T zc = qz[u];
+                const T zu = (k + 1 < k1) ? (u + 1 < PB ? qz[u + 1] : xz[0]) : (k1 < nz ? zend : zc);
+                const T f = ldro(op.wv + k) * (zc - zu);
+                T h = col.me * (zc - qe[u]);
+                h = fma(col.mw, zc - qw[u], h);
+                h = fma(col.mn, zc - qn[u], h);
+                h = fma(col.ms, zc - qs[u], h);
+                const T az = fma(ldro(op.dk + k), h, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+                tv[u] = qr[u] - az;
+                fprev = f;
+            }
+        }
+        if (ty == 1) {
+#pragma unroll
+            for (int u = 0; u < PB; ++u) sh[u][lane] = tv[u];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            const T right = __shfl_down_sync(0xffffffffu, tv[u], 1);
+            const int k = kb + u;
+            if (ty == 0 && !(lane & 1) && col.valid && k < k1)
+                rcb[(long long)k * planec] = ((tv[u] + right) + sh[u][lane]) + sh[u][lane + 1];
+        }
+        __syncthreads();   // the rows 2J+1 of the next PB levels overwrite sh
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            qz[u] = xz[u];
+            qe[u] = xe[u];
+            qw[u] = xw[u];
+            qn[u] = xn[u];
+            qs[u] = xs[u];
+            qr[u] = xr[u];
+        }
+    }
+}
+
 // z = (acc ? z : 0) + omega M^{-1} rin on levels with few columns: the
 // chunked (substructured) Thomas solve of prec_chunked_body, one warp per
 // 16-level chunk of 32 columns of one row (block (32, n_z/16)), so that a

@@ -121,6 +121,7 @@ struct pcg_ctx {
     long long mg_resid_threads = 524288;  // k_mg_resid splits columns until this many threads run
     long long mg_few = 0;                 // chunked line solve below this many columns (0: by precision)
     int mg_resid_pb = 0;                  // k_mg_resid prefetch depth, 1, 2 or 4 levels (0: by precision)
+    int mg_fuse = 1;                      // downward residual and restriction in one kernel
     // PCG_ALG_SINGLE_REDUCTION: one k_sweep_sr per pass; r, s (q64), w double-buffered
     bool alg_sr = false;
     dim3 grid_sr;
@@ -695,7 +696,20 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
     for (int l = 0; l + 1 < L; ++l) {
         smooth_first(l, omega);
         for (int k = 1; k < h->mg_nu; ++k) smooth_more(l);
-        pcg_t hc = H(l + 1);
+        pcg_t hl = H(l), hc = H(l + 1);
+        if (h->mg_fuse && hl->ny / 2 <= 65535) {
+            // the residual restricted as it is formed (t is not written)
+            const int ks = ksplit(hl);
+            const dim3 g((hl->nx + 31) / 32, hl->ny / 2, hl->nrhs * ks);
+            if constexpr (sizeof(V) == 4)
+                pcg::k_mg_resid_restrict<V, 4><<<g, dim3(32, 2), 0, s>>>(level_view<V>(hl), R(l), Z(l),
+                                                                        const_cast<V*>(R(l + 1)), st, ks);
+            else
+                pcg::k_mg_resid_restrict<V, 2><<<g, dim3(32, 2), 0, s>>>(level_view<V>(hl), R(l), Z(l),
+                                                                        const_cast<V*>(R(l + 1)), st, ks);
+            ++n;
+            continue;
+        }
         resid(l);
         const CellLaunch cl = cell_launch(hc->nx, hc->ny, hc->nz, hc->nrhs);
         pcg::k_mg_restrict<V><<<cl.g, cl.b, 0, s>>>(T(l), const_cast<V*>(R(l + 1)), hc->nx, hc->ny, hc->nz, hc->nrhs,
@@ -1143,6 +1157,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if (const char* e = std::getenv("PCG_MG_RESID_THREADS")) h->mg_resid_threads = std::atoll(e);   // experiments
     if (const char* e = std::getenv("PCG_MG_FEW")) h->mg_few = std::atoll(e);                        // experiments
     if (const char* e = std::getenv("PCG_MG_RESID_PB")) h->mg_resid_pb = std::atoi(e);                // experiments
+    if (const char* e = std::getenv("PCG_MG_FUSE")) h->mg_fuse = std::atoi(e) ? 1 : 0;                 // experiments
     h->rhs_stats.assign(h->nrhs, pcg_stats_t{});
     if (const char* tr = std::getenv("PCG_TRACE")) h->trace = std::atoi(tr);
     h->block = dim3(BX, BY, 1);
