@@ -201,7 +201,19 @@ def pcg_create(problem, nrhs: int = 1, precision: int = PCG_FP64, inner_tol: flo
 
 class Solver:
     """One pcg_t handle.  Vectors are torch tensors of nrhs * n_z * n_y * n_x
-    elements in the layout [nrhs][n_z][n_y][n_x]."""
+    elements in the layout [nrhs][n_z][n_y][n_x].
+
+    precision:      "fp64" (PCG_FP64) or "mixed" (PCG_MIXED: FP32 inner PCG
+                    inside FP64 iterative refinement).
+    preconditioner: "line" (the paper's vertical-line preconditioner),
+                    "multigrid" (one V-cycle with line smoothing, FP64) or
+                    "multigrid-f32" (the same V-cycle in FP32 inside the FP64
+                    CG); the multigrid options need precision "fp64".
+    algorithm:      "interleaved" (Algorithm 1, two sweeps per iteration) or
+                    "single-reduction" (one sweep and one reduction per
+                    iteration; line preconditioner, n_z <= 256).
+    Further keyword arguments go to pcg_create (inner_tol, inner_maxit,
+    max_outer, passes_per_launch, stream)."""
 
     def __init__(self, problem, nrhs: int = 1, precision: str = "fp64", preconditioner: str = "line",
                  algorithm: str = "interleaved", **kw):
