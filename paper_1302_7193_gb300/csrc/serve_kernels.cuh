@@ -155,9 +155,14 @@ __global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __res
     if (pend1) mbar_wait(bar1, par1, 1 << 22);
 }
 
+// The SpMV items are taken in arrival order from `fetch` (zeroed before the
+// launch), so blocks that draw cheap items (requests that stopped earlier in
+// the graph, short columns) take more of them.
 __global__ __launch_bounds__(BX * SERVE_BY) void k_serve_spmv(const ServeSlot* __restrict__ slots,
                                                              const int2* __restrict__ items,
-                                                    const int* __restrict__ n_items) {
+                                                             const int* __restrict__ n_items,
+                                                             unsigned* __restrict__ fetch) {
+    __shared__ int s_item;
     using TT = SpmvTmaTile<SERVE_LZ, SERVE_BY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* zs = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -173,7 +178,11 @@ __global__ __launch_bounds__(BX * SERVE_BY) void k_serve_spmv(const ServeSlot* _
     bool broken = false;        // a staged copy timed out: this block computes nothing more
     int last_slot = -1;         // slot whose tensor maps thread 0 acquired last
     const int n = *n_items;
-    for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(fetch, 1u);
+        __syncthreads();
+        const int it = s_item;  // rewritten only after the barrier that ends this item
+        if (it >= n) break;
         const int2 wk = items[it];
         const ServeSlot& s = slots[wk.x];
         SolveState* st = s.st;
