@@ -79,7 +79,7 @@ struct pcg_server {
     int2* h_items = nullptr;            // pinned mirror
     int* h_nitems = nullptr;            // pinned [2]
     int* d_one = nullptr;
-    unsigned* d_fetch = nullptr;        // [epochs_per_launch]: next SpMV item of each epoch's launch
+    unsigned* d_fetch = nullptr;        // [epochs_per_launch][2]: next item of each epoch's two launches
     int items_cap = 0;
     bool items_dirty = true;
     cudaGraphExec_t graph = nullptr;
@@ -390,17 +390,17 @@ int rebuild_items(pcg_server_t s) {
 int capture_epochs(pcg_server_t s) {
     cudaGraph_t g = nullptr;
     SRV_CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-    // the SpMV launches take their items in arrival order from these counters
-    SRV_CK(s, cudaMemsetAsync(s->d_fetch, 0, sizeof(unsigned) * (size_t)s->epochs_per_launch, s->cap_stream));
+    // every launch takes its items in arrival order from a counter of its own
+    SRV_CK(s, cudaMemsetAsync(s->d_fetch, 0, 2 * sizeof(unsigned) * (size_t)s->epochs_per_launch, s->cap_stream));
     for (int e = 0; e < s->epochs_per_launch; ++e) {
         if (s->prec_minb == 3)
             pcg::k_serve_prec<3><<<s->blocks_prec, dim3(BX, 8, 1), pcg::SERVE_PREC_SMEM, s->cap_stream>>>(
-                s->d_slots, s->d_items, s->d_nitems);
+                s->d_slots, s->d_items, s->d_nitems, s->d_fetch + 2 * e);
         else
             pcg::k_serve_prec<2><<<s->blocks_prec, dim3(BX, 8, 1), pcg::SERVE_PREC_SMEM, s->cap_stream>>>(
-                s->d_slots, s->d_items, s->d_nitems);
+                s->d_slots, s->d_items, s->d_nitems, s->d_fetch + 2 * e);
         pcg::k_serve_spmv<<<s->blocks_spmv, dim3(BX, pcg::SERVE_BY, 1), ServeSpmvTile::SMEM, s->cap_stream>>>(
-            s->d_slots, s->d_items + s->items_cap, s->d_nitems + 1, s->d_fetch + e);
+            s->d_slots, s->d_items + s->items_cap, s->d_nitems + 1, s->d_fetch + 2 * e + 1);
     }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
     if (e != cudaSuccess) return sfail(s, PCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -453,7 +453,7 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
         {(void**)&s->d_items, 2 * sizeof(int2) * (size_t)s->items_cap},
         {(void**)&s->d_nitems, 2 * sizeof(int)},
         {(void**)&s->d_one, sizeof(int)},
-        {(void**)&s->d_fetch, sizeof(unsigned) * (size_t)std::max(s->epochs_per_launch, 1)},
+        {(void**)&s->d_fetch, 2 * sizeof(unsigned) * (size_t)std::max(s->epochs_per_launch, 1)},
     };
     for (auto& a : dev_allocs)
         if ((e = cudaMalloc(a.p, a.b)) != cudaSuccess) { *a.p = nullptr; s->err = "cudaMalloc failed"; return bail(PCG_ERR_OOM); }

@@ -51,12 +51,18 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
+// Items are taken in arrival order from `fetch` (zeroed before the launch):
+// thread 0 draws an item when it refills a stage, so a block's stages hold its
+// items in the order drawn, and once one of them is past the end of the list
+// every later draw of the block is too.
 template <int MINB>
 __global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __restrict__ slots,
                                                          const int2* __restrict__ items,
-                                                         const int* __restrict__ n_items) {
+                                                         const int* __restrict__ n_items,
+                                                         unsigned* __restrict__ fetch) {
     __shared__ float sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
-    __shared__ int staged[2];   // stage g holds the bulk copies of its next item (1) or nothing (0)
+    __shared__ int staged[2];       // stage g holds the bulk copies of its item (1) or nothing (0)
+    __shared__ int stage_item[2];   // the item drawn for stage g (n or more: none)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* sbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 4 * SERVE_PVN);
@@ -65,8 +71,11 @@ __global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __res
     const int n = *n_items;
     int last_slot = -1;   // thread 0: the slot whose maps it acquired last
     bool ok = true;       // false once a copy failed to land in time: no more copies are started
-    // thread 0: start the copies of item `it` into stage g if its request is staged and running
-    auto issue = [&](int it, int g) {
+    // thread 0: draw the next item for stage g and start its copies if its
+    // request is staged and running
+    auto issue = [&](int g) {
+        const int it = (int)atomicAdd(fetch, 1u);
+        stage_item[g] = it;
         int go = 0;
         if (ok && it < n) {
             const int2 wk = items[it];
@@ -93,19 +102,20 @@ __global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __res
     if (tid == 0) {
         mbar_init(bar0);
         mbar_init(bar1);
-        issue(blockIdx.x, 0);
-        issue(blockIdx.x + gridDim.x, 1);
+        issue(0);
+        issue(1);
     }
     __syncthreads();
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = false, pend1 = false;   // a copy into the stage that has not been seen to land
-    int k = 0;
-    for (int it = blockIdx.x; it < n; it += gridDim.x, ++k) {
+    for (int k = 0;; ++k) {
         const int g = k & 1;
+        // stage_item[g] and staged[g] were written before the barriers of the previous item
+        const int it = stage_item[g];
+        if (it >= n) break;
         const int2 wk = items[it];
         const ServeSlot& s = slots[wk.x];
         SolveState* st = s.st;
-        // staged[g] was written before the barriers of the previous item
         const bool was_staged = staged[g] != 0;
         bool landed = true;
         if (was_staged) {
@@ -145,12 +155,13 @@ __global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __res
             double v[2];
             if (grid_sum_acc<2>(acc, s.partials, s.counter, s.nprec, wk.y, v)) prec_epilogue(st, v[0], v[1]);
         }
-        __syncthreads();   // the stage has been read: refill it with the item two ahead
-        if (tid == 0) issue(it + 2 * gridDim.x, g);
+        __syncthreads();   // the stage has been read: refill it with the next item drawn
+        if (tid == 0) issue(g);
     }
     // copies that did not land in time are waited for (again with a limit)
     // before the block's shared memory is released; an issued copy whose item
-    // this block never reached cannot exist (items are taken in issue order)
+    // this block never reached cannot exist (a block's draws increase, and the
+    // loop ends at the first draw past the end of the list)
     if (pend0) mbar_wait(bar0, par0, 1 << 22);
     if (pend1) mbar_wait(bar1, par1, 1 << 22);
 }
