@@ -30,3 +30,21 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_key_ignores_comments_but_not_code(tmp_path):
+    """The committed ncu traffic is keyed on the code of kernels.cuh: comment
+    and blank-line edits keep it, any change to the code voids it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "paper_1302_7193_gb300", "csrc", "kernels.cuh"), encoding="utf-8").read()
+    base = tmp_path / "a.cuh"
+    base.write_text(src)
+    h0 = bench._kernels_code_hash(str(base))
+    commented = tmp_path / "b.cuh"
+    commented.write_text("// a new comment line\n\n" + src.replace("namespace pcg {", "namespace pcg {  /* note */", 1))
+    assert bench._kernels_code_hash(str(commented)) == h0
+    changed = tmp_path / "c.cuh"
+    changed.write_text(src.replace("constexpr int BX = 32;", "constexpr int BX = 64;", 1))
+    assert "constexpr int BX = 32;" in src
+    assert bench._kernels_code_hash(str(changed)) != h0
