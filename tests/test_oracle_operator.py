@@ -237,3 +237,125 @@ def test_panel_edges_are_neumann():
     t = operator_terms(p)
     assert (t.mu_e[:, -1] == 0).all() and (t.mu_n[-1, :] == 0).all()
     assert (t.mu_e[:, :-1] > 0).all() and (t.mu_n[:-1, :] > 0).all()
+
+
+# The face weights of the panel, pinned independently of the oracle's
+# formulas.  Section 3.1 defines the horizontal coupling of two cells as the
+# length of their common edge divided by the distance between their
+# midpoints.  The checks below recompute both from normalised 3-D points
+# (great-circle arcs as atan2(|a x b|, a.b)), compare each cell's area with a
+# quadrature of the gnomonic area element, and compare the two-point flux with
+# the exact flux of a smooth function through faces where the grid is
+# orthogonal (the panel's two central lines), where it must converge at second
+# order.  On skewed faces a two-point flux is not consistent (its error stays
+# O(1) near the panel corners), so the panel has no manufactured-solution
+# convergence test like the box and the band.
+
+def _panel_unit(x, y):
+    v = np.stack(np.broadcast_arrays(np.ones_like(x), x, y), axis=-1)
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def _great_arc(a, b):
+    return np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), np.sum(a * b, axis=-1))
+
+
+@pytest.mark.parametrize("n_x,n_y", [(6, 6), (17, 9), (64, 64)])
+def test_panel_face_weights_are_edge_over_centre_distance(n_x, n_y):
+    p = W.panel_problem(n_x, n_y, 2)
+    t = operator_terms(p)
+    xf = np.linspace(-1.0, 1.0, n_x + 1)
+    yf = np.linspace(-1.0, 1.0, n_y + 1)
+    xc = 0.5 * (xf[1:] + xf[:-1])
+    yc = 0.5 * (yf[1:] + yf[:-1])
+    alpha = np.asarray(p.alpha_e)
+    mu_e = np.zeros((n_y, n_x))
+    mu_n = np.zeros((n_y, n_x))
+    for j in range(n_y):
+        for i in range(n_x):
+            centre = _panel_unit(xc[i], yc[j])
+            if i + 1 < n_x:     # east edge: x = xf[i+1], y from yf[j] to yf[j+1]
+                edge = _great_arc(_panel_unit(xf[i + 1], yf[j]), _panel_unit(xf[i + 1], yf[j + 1]))
+                mu_e[j, i] = edge / _great_arc(centre, _panel_unit(xc[i + 1], yc[j]))
+            if j + 1 < n_y:     # north edge: y = yf[j+1], x from xf[i] to xf[i+1]
+                edge = _great_arc(_panel_unit(xf[i], yf[j + 1]), _panel_unit(xf[i + 1], yf[j + 1]))
+                mu_n[j, i] = edge / _great_arc(centre, _panel_unit(xc[i], yc[j + 1]))
+    np.testing.assert_allclose(t.mu_e, alpha * mu_e, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(t.mu_n, np.asarray(p.alpha_n) * mu_n, rtol=1e-12, atol=0)
+
+
+def test_panel_cell_areas_match_quadrature_of_the_area_element():
+    # the gnomonic map (x, y) -> (1, x, y)/|(1, x, y)| has area element
+    # (1 + x^2 + y^2)^(-3/2) dx dy; 8-point Gauss-Legendre per cell and axis
+    n_x, n_y = 12, 7
+    t = operator_terms(W.panel_problem(n_x, n_y, 2))
+    g, wg = np.polynomial.legendre.leggauss(8)
+    xf = np.linspace(-1.0, 1.0, n_x + 1)
+    yf = np.linspace(-1.0, 1.0, n_y + 1)
+    for j in range(n_y):
+        for i in range(n_x):
+            hx, hy = xf[i + 1] - xf[i], yf[j + 1] - yf[j]
+            x = xf[i] + 0.5 * hx * (g + 1.0)
+            y = yf[j] + 0.5 * hy * (g + 1.0)
+            X, Y = np.meshgrid(x, y)
+            q = 0.25 * hx * hy * np.einsum("a,b,ab->", wg, wg, (1.0 + X * X + Y * Y) ** -1.5)
+            assert abs(t.area[j, i] - q) <= 1e-13 * q, (j, i, t.area[j, i], q)
+
+
+def _smooth_on_sphere(v):
+    """A smooth function of the 3-D point and its 3-D gradient."""
+    X, Y, Z = v[..., 0], v[..., 1], v[..., 2]
+    u = np.sin(2 * Y + 0.5) * np.cos(1.5 * Z) + Y * Z + 0.3 * X * X
+    grad = np.stack([0.6 * X,
+                     2 * np.cos(2 * Y + 0.5) * np.cos(1.5 * Z) + Z,
+                     -1.5 * np.sin(2 * Y + 0.5) * np.sin(1.5 * Z) + Y], axis=-1)
+    return u, grad
+
+
+def _exact_face_flux(a, b, towards):
+    """Integral over the great-circle edge from a to b of grad u . N, N the
+    unit normal of the edge within the sphere, oriented towards ``towards``.
+    N = a x b / |a x b| is the same at every point of the edge and tangent to
+    the sphere there, so the 3-D gradient of any extension gives grad u . N."""
+    nrm = np.cross(a, b)
+    nrm /= np.linalg.norm(nrm)
+    if nrm @ towards < 0:
+        nrm = -nrm
+    theta = _great_arc(a, b)
+    tang = b - (a @ b) * a
+    tang /= np.linalg.norm(tang)
+    g, wg = np.polynomial.legendre.leggauss(12)
+    s = 0.5 * theta * (g + 1.0)
+    pts = np.cos(s)[:, None] * a + np.sin(s)[:, None] * tang
+    _, grad = _smooth_on_sphere(pts)
+    return 0.5 * theta * float(wg @ (grad @ nrm))
+
+
+def _central_line_flux_error(n):
+    p = W.panel_problem(n, n, 2)
+    t = operator_terms(p)
+    mu_e = t.mu_e / np.asarray(p.alpha_e)
+    mu_n = t.mu_n / np.asarray(p.alpha_n)
+    f = np.linspace(-1.0, 1.0, n + 1)
+    c = 0.5 * (f[1:] + f[:-1])
+    m = n // 2 - 1                       # faces on x = 0 (east of column m) and on y = 0 (north of row m)
+    errs, scale = [], []
+    for k in range(n):
+        uP, _ = _smooth_on_sphere(_panel_unit(c[m], c[k]))
+        uE, _ = _smooth_on_sphere(_panel_unit(c[m + 1], c[k]))
+        exact = _exact_face_flux(_panel_unit(0.0, f[k]), _panel_unit(0.0, f[k + 1]), np.array([0.0, 1.0, 0.0]))
+        errs.append(mu_e[k, m] * (uE - uP) - exact)
+        scale.append(abs(exact))
+        uP, _ = _smooth_on_sphere(_panel_unit(c[k], c[m]))
+        uN, _ = _smooth_on_sphere(_panel_unit(c[k], c[m + 1]))
+        exact = _exact_face_flux(_panel_unit(f[k], 0.0), _panel_unit(f[k + 1], 0.0), np.array([0.0, 0.0, 1.0]))
+        errs.append(mu_n[m, k] * (uN - uP) - exact)
+        scale.append(abs(exact))
+    return np.abs(errs).max() / max(scale)
+
+
+def test_panel_two_point_flux_is_second_order_on_the_orthogonal_central_lines():
+    e = [_central_line_flux_error(n) for n in (8, 16, 32, 64)]
+    ratios = [e[i] / e[i + 1] for i in range(3)]
+    assert all(3.5 < q < 4.5 for q in ratios), (e, ratios)
+    assert e[-1] < 1e-3
