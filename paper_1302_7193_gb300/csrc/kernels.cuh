@@ -1119,6 +1119,127 @@ __device__ __forceinline__ void spmv_tile_compute(const OpView<float>& op, const
     }
 }
 
+// Values a staged z tile lacks: neighbours across a periodic edge.  The
+// bulk copy fills cells outside the grid with zeros, so a block on an edge
+// loads the wrapped neighbours of its own cells (levels k0 .. k0+kn-1) from
+// global memory into registers before its copies land, and writes them into
+// the tile's halo (or, in a ragged last tile, into the cell just past the
+// grid) once they have.  A face on a Neumann edge has weight 0, so its halo
+// cell may keep the zero.  Thread (tx, ty) takes the x-wrap cells of level tx
+// (< LZ) in row ty, and the y-wrap cells of column tx at levels ty, ty + BYT, ...
+template <int LZ, int BYT>
+struct WrapPatch {
+    static constexpr int NY = (LZ + BYT - 1) / BYT;
+    float xw, xe, ys[NY], yn[NY];
+    bool any;            // block-uniform: the tile has a wrapped neighbour
+    int i0, j0, nxv, nyv, kn;
+    bool west, east, south, north;
+
+    __device__ __forceinline__ void load(const OpView<float>& op, const float* __restrict__ zr, int i0_, int j0_,
+                                         int k0, int kn_, int tx, int ty) {
+        i0 = i0_;
+        j0 = j0_;
+        kn = kn_;
+        nxv = min(BX, op.nx - i0);
+        nyv = min(BYT, op.ny - j0);
+        west = i0 == 0;
+        east = i0 + BX >= op.nx;
+        south = op.periodic_y && j0 == 0;
+        north = op.periodic_y && j0 + BYT >= op.ny;
+        any = west || east || south || north;
+        if (!any) return;
+        const long long pl = op.plane, nx = op.nx;
+        if (tx < kn && ty < nyv) {
+            const float* lev = zr + (long long)(k0 + tx) * pl + (long long)(j0 + ty) * nx;
+            if (west) xw = ldro(lev + (nx - 1));
+            if (east) xe = ldro(lev);
+        }
+        if (tx < nxv) {
+#pragma unroll
+            for (int m = 0; m < NY; ++m) {
+                const int t = ty + m * BYT;
+                if (t < kn) {
+                    const float* lev = zr + (long long)(k0 + t) * pl + (i0 + tx);
+                    if (south) ys[m] = ldro(lev + (long long)(op.ny - 1) * nx);
+                    if (north) yn[m] = ldro(lev);
+                }
+            }
+        }
+    }
+
+    // zs: the tile [LZ+2][BYT+2][BX+2*TMA_HALO_X], level t of the chunk at t+1
+    __device__ __forceinline__ void store(float* zs, int tx, int ty) const {
+        constexpr int ZX = BX + 2 * TMA_HALO_X, ZP = ZX * (BYT + 2);
+        if (tx < kn && ty < nyv) {
+            float* row = zs + (tx + 1) * ZP + (ty + 1) * ZX + TMA_HALO_X;
+            if (west) row[-1] = xw;
+            if (east) row[nxv] = xe;
+        }
+        if (tx < nxv) {
+#pragma unroll
+            for (int m = 0; m < NY; ++m) {
+                const int t = ty + m * BYT;
+                if (t < kn) {
+                    float* lev = zs + (t + 1) * ZP + TMA_HALO_X + tx;
+                    if (south) lev[0] = ys[m];
+                    if (north) lev[(nyv + 1) * ZX] = yn[m];
+                }
+            }
+        }
+    }
+};
+
+// The SpMV arithmetic of one thread on a staged tile whose halo holds every
+// neighbour (WrapPatch applied), in spmv_column<float>'s order of operations:
+// zs holds levels k0-1 .. k0+LZ of the tile with halo, us/ps/qs levels k0 ..
+// k0+LZ-1 of the block's own columns; tw[t], td[t], tm[t] are wv, dk and mass
+// at level k0 + t (tw[-1] too when k0 > 0); u, p, q point at level 0 of the
+// right-hand side.  sigma = <p, q> of the chunk is summed in plain FP32 (error
+// <= LZ u sum_k |p_k q_k|) and added to the compensated accumulator once.
+template <int LZ, int BYT>
+__device__ __forceinline__ void spmv_tile_compute_p(const OpView<float>& op, const Col<float>& col, int tx, int ty,
+                                                    int k0, int kn, const float* zs, const float* us,
+                                                    const float* ps, const float* qs, const float* tw,
+                                                    const float* td, const float* tm, float* __restrict__ u,
+                                                    float* __restrict__ p, float* __restrict__ q, float alpha,
+                                                    float beta, Acc<float>& sig) {
+    using TT = SpmvTmaTile<LZ, BYT>;
+    const long long pl = op.plane;
+    float* __restrict__ ub = u + col.c + (long long)k0 * pl;
+    float* __restrict__ pb = p + col.c + (long long)k0 * pl;
+    float* __restrict__ qb = q + col.c + (long long)k0 * pl;
+    constexpr int ZX = TT::ZX, ZP = TT::ZX * TT::ZY;
+    const int c0 = (ty + 1) * ZX + (tx + TMA_HALO_X);
+    const int v0 = ty * BX + tx;
+    const bool top = k0 + kn == op.nz;          // the chunk holds the top level: no flux above it
+    float zc = zs[ZP + c0];
+    float fprev = (k0 > 0) ? tw[-1] * (zs[c0] - zc) : 0.f;
+    float sc = 0.f;
+#pragma unroll
+    for (int t = 0; t < LZ; ++t) {
+        if (t < kn) {
+            const float* zl = zs + (t + 1) * ZP;
+            const float zu = (top && t + 1 == kn) ? zc : zl[ZP + c0];
+            const float pk = ps[t * BX * BYT + v0];
+            ub[t * pl] = fmaf(alpha, pk, us[t * BX * BYT + v0]);
+            const float pn = fmaf(beta, pk, zc);
+            pb[t * pl] = pn;
+            const float f = tw[t] * (zc - zu);
+            float hz = col.me * (zc - zl[c0 + 1]);
+            hz = fmaf(col.mw, zc - zl[c0 - 1], hz);
+            hz = fmaf(col.mn, zc - zl[c0 + ZX], hz);
+            hz = fmaf(col.ms, zc - zl[c0 - ZX], hz);
+            const float az = fmaf(td[t], hz, col.area * fmaf(tm[t], zc, f - fprev));
+            const float qn = fmaf(beta, qs[t * BX * BYT + v0], az);
+            qb[t * pl] = qn;
+            sc = fmaf(pn, qn, sc);
+            fprev = f;
+            zc = zu;
+        }
+    }
+    sig.add(sc);
+}
+
 template <int LZ, int BYT>
 __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma(
     OpView<float> op, const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
@@ -1127,6 +1248,7 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma(
     double* __restrict__ partials, unsigned* __restrict__ counters, int nblocks, int nchunks) {
     using TT = SpmvTmaTile<LZ, BYT>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ float tb[3][LZ + 1];         // wv at k0-1 .. k0+LZ-1, dk and mass at k0 .. k0+LZ-1
     // bulk tensor copies land on 128-byte aligned addresses
     float* zs = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));   // [ZZ][ZY][ZX]
     float* us = zs + TT::ZN;                // [LZ][BYT][32]
@@ -1137,43 +1259,49 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma(
     const int ch = blockIdx.z - rhs * nchunks;
     SolveState* st = states + rhs;
     if (st->done) return;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BYT;
     const int k0 = ch * LZ;
     const int kn = min(LZ, op.nz - k0);
     const int lev0 = rhs * op.nz + k0;      // level coordinate of the chunk in the folded arrays
     const uint32_t b = smem_u32(bar);
-    if (tx == 0 && ty == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b), "r"(1) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (tid == 0) mbar_init(b);
     __syncthreads();
-    if (tx == 0 && ty == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(TT::BYTES) : "memory");
+    if (tid == 0) {
+        mbar_expect(b, TT::BYTES);
         tma_load_3d(smem_u32(zs), &tm_z, i0 - TMA_HALO_X, j0 - 1, lev0 - 1, b);
         tma_load_3d(smem_u32(us), &tm_u, i0, j0, lev0, b);
         tma_load_3d(smem_u32(ps), &tm_p, i0, j0, lev0, b);
         tma_load_3d(smem_u32(qs), &tm_q, i0, j0, lev0, b);
     }
+    // while the copies are in flight: level tables, column geometry, wrapped neighbours
+    if (tid < 3 * (LZ + 1)) {
+        const int a = tid / (LZ + 1), t = tid - a * (LZ + 1);
+        const int k = k0 - 1 + t;
+        const float* src = a == 0 ? op.wv : (a == 1 ? op.dk : op.mass);
+        const int ko = a == 0 ? k : k + 1;  // dk, mass: entry t is level k0 + t
+        tb[a][t] = (ko >= 0 && ko < op.nz) ? ldro(src + ko) : 0.f;
+    }
     const float alpha = (float)st->alpha;
     const float beta = (float)st->beta;
     const Col<float> col = make_col(op, i0 + tx, j0 + ty);
     const bool act = col.valid && kn > 0;
-    // neighbours inside the staged tile (not wrapped, not clamped)
-    const bool in_e = col.ce == col.c + 1, in_w = col.cw == col.c - 1;
-    const bool in_n = col.cn == col.c + op.nx, in_s = col.cs == col.c - op.nx;
+    const long long base = (long long)rhs * op.vol;
+    WrapPatch<LZ, BYT> wp;
+    wp.load(op, z + base, i0, j0, k0, kn, tx, ty);
     const bool landed = mbar_wait0(b, 1 << 22);
+    if (landed) wp.store(zs, tx, ty);
+    __syncthreads();
     Acc<float> sig[1];
     if (!landed) {
         // the copies did not complete in time: record it (the last block ends
         // the solve), wait (bounded) for them to land before the block's
         // shared memory is released, and add nothing to sigma
-        if (tx == 0 && ty == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT
+        if (tid == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT
         mbar_wait0(b, 1 << 22);
     } else if (act) {
-        const long long base = (long long)rhs * op.vol;
-        spmv_tile_compute<LZ, BYT>(op, col, tx, ty, k0, kn, zs, us, ps, qs, z + base, u + base, p + base, q + base,
-                                   alpha, beta, in_e, in_w, in_n, in_s, sig[0]);
+        spmv_tile_compute_p<LZ, BYT>(op, col, tx, ty, k0, kn, zs, us, ps, qs, &tb[0][1], tb[1], tb[2], u + base,
+                                     p + base, q + base, alpha, beta, sig[0]);
     }
     double v[1];
     const int bid = (ch * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -1185,8 +1313,16 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma(
 // The same SpMV sweep as a persistent two-stage pipeline: blockIdx.y = right-
 // hand side; a block walks the (tile, chunk) items i = blockIdx.x, +gridDim.x,
 // ... and keeps the copies of its next item in flight (second stage, second
-// mbarrier) while it computes the current one.
+// mbarrier) while it computes the current one.  The level tables of all n_z
+// levels sit in shared memory after the two stages; the grid-level reduction
+// runs once per block instead of once per item.
 // ---------------------------------------------------------------------------
+template <int LZ, int BYT>
+__host__ __device__ constexpr size_t spmv_tma2_smem(int nz) {
+    return 2 * ((size_t)SpmvTmaTile<LZ, BYT>::ZN + 3 * SpmvTmaTile<LZ, BYT>::VN) * 4 + (size_t)(3 * nz + 4) * 4 + 16 +
+           128;
+}
+
 template <int LZ, int BYT>
 __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
     OpView<float> op, const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
@@ -1197,7 +1333,11 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
     constexpr int STAGE = TT::ZN + 3 * TT::VN;          // floats per stage (a multiple of 32)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* sbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 2 * STAGE);
+    const int nz = op.nz;
+    float* tbw = sbase + 2 * STAGE;                     // wv[0 .. nz-1] at tbw[1 ..], tbw[0] = 0
+    float* tbd = tbw + nz + 1;
+    float* tbm = tbd + nz;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 2 * STAGE + ((3 * nz + 4) & ~3));
     const int rhs = blockIdx.y;
     SolveState* st = states + rhs;
     if (st->done) return;
@@ -1208,10 +1348,16 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
         mbar_init(bar0);
         mbar_init(bar1);
     }
+    for (int k = tid; k < nz; k += BX * BYT) {
+        tbw[k + 1] = ldro(op.wv + k);
+        tbd[k] = ldro(op.dk + k);
+        tbm[k] = ldro(op.mass + k);
+    }
+    if (tid == 0) tbw[0] = 0.f;
     __syncthreads();
     auto issue = [&](int item, int stage) {
         const int ch = item % nchunks, tile = item / nchunks;
-        const int i0 = (tile % gx) * BX, j0 = (tile / gx) * BYT, lev0 = rhs * op.nz + ch * LZ;
+        const int i0 = (tile % gx) * BX, j0 = (tile / gx) * BYT, lev0 = rhs * nz + ch * LZ;
         float* zs = sbase + stage * STAGE;
         const uint32_t bar = stage ? bar1 : bar0;
         mbar_expect(bar, TT::BYTES);
@@ -1220,9 +1366,14 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
         tma_load_3d(smem_u32(zs + TT::ZN + TT::VN), &tm_p, i0, j0, lev0, bar);
         tma_load_3d(smem_u32(zs + TT::ZN + 2 * TT::VN), &tm_q, i0, j0, lev0, bar);
     };
-    if (tid == 0) {
-        if ((int)blockIdx.x < nitems) issue(blockIdx.x, 0);
-        if ((int)(blockIdx.x + gridDim.x) < nitems) issue(blockIdx.x + gridDim.x, 1);
+    uint32_t pending = 0;
+    if ((int)blockIdx.x < nitems) {
+        if (tid == 0) issue(blockIdx.x, 0);
+        pending |= 1u;
+    }
+    if ((int)(blockIdx.x + gridDim.x) < nitems) {
+        if (tid == 0) issue(blockIdx.x + gridDim.x, 1);
+        pending |= 2u;
     }
     const float alpha = (float)st->alpha;
     const float beta = (float)st->beta;
@@ -1233,39 +1384,42 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
     int n = 0;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++n) {
         const int stage = n & 1;
-        bool landed = false;
-        if (ok) landed = mbar_wait(stage ? bar1 : bar0, stage ? par1 : par0, 1 << 22);
+        const int ch = item % nchunks, tile = item / nchunks;
+        const int i0 = (tile % gx) * BX, j0 = (tile / gx) * BYT, k0 = ch * LZ;
+        const int kn = min(LZ, nz - k0);
+        WrapPatch<LZ, BYT> wp;
+        wp.load(op, z + base, i0, j0, k0, kn, tx, ty);
+        const Col<float> col = make_col(op, i0 + tx, j0 + ty);
+        bool landed = mbar_wait(stage ? bar1 : bar0, stage ? par1 : par0, 1 << 22);
         landed = __syncthreads_and(landed ? 1 : 0) != 0;
-        if (landed) {
-            if (stage) par1 ^= 1u; else par0 ^= 1u;
-        }
-        if (ok && !landed) {
+        if (!landed) {
             if (tid == 0) atomicExch(&st->status, 6);   // PCG_TIMEOUT
             ok = false;
+            break;
         }
-        if (ok) {
-            const int ch = item % nchunks, tile = item / nchunks;
-            const int i0 = (tile % gx) * BX, j0 = (tile / gx) * BYT, k0 = ch * LZ;
-            const int kn = min(LZ, op.nz - k0);
-            const Col<float> col = make_col(op, i0 + tx, j0 + ty);
-            if (col.valid && kn > 0) {
-                const bool in_e = col.ce == col.c + 1, in_w = col.cw == col.c - 1;
-                const bool in_n = col.cn == col.c + op.nx, in_s = col.cs == col.c - op.nx;
-                const float* zs = sbase + stage * STAGE;
-                spmv_tile_compute<LZ, BYT>(op, col, tx, ty, k0, kn, zs, zs + TT::ZN, zs + TT::ZN + TT::VN,
-                                           zs + TT::ZN + 2 * TT::VN, z + base, u + base, p + base, q + base, alpha,
-                                           beta, in_e, in_w, in_n, in_s, sig[0]);
-            }
+        if (stage) par1 ^= 1u; else par0 ^= 1u;
+        pending &= ~(1u << stage);
+        float* zs = sbase + stage * STAGE;
+        if (wp.any) {
+            wp.store(zs, tx, ty);
+            __syncthreads();
         }
-        __syncthreads();            // the stage has been read: refill it
-        if (tid == 0 && ok && item + 2 * (int)gridDim.x < nitems) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(item + 2 * gridDim.x, stage);
+        if (col.valid && kn > 0)
+            spmv_tile_compute_p<LZ, BYT>(op, col, tx, ty, k0, kn, zs, zs + TT::ZN, zs + TT::ZN + TT::VN,
+                                         zs + TT::ZN + 2 * TT::VN, tbw + 1 + k0, tbd + k0, tbm + k0, u + base,
+                                         p + base, q + base, alpha, beta, sig[0]);
+        // the stage has been read (and patched) by the threads: order that
+        // before the bulk copies that refill it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (item + 2 * (int)gridDim.x < nitems) {
+            if (tid == 0) issue(item + 2 * gridDim.x, stage);
+            pending |= 1u << stage;
         }
     }
     if (!ok) {
-        mbar_wait(bar0, par0, 1 << 22);
-        mbar_wait(bar1, par1, 1 << 22);
+        if (pending & 1u) mbar_wait(bar0, par0, 1 << 22);
+        if (pending & 2u) mbar_wait(bar1, par1, 1 << 22);
     }
     double v[1];
     if (grid_sum_acc<1>(sig, partials + (long long)rhs * gridDim.x * 2, counters + rhs, gridDim.x, blockIdx.x, v))
@@ -1289,19 +1443,134 @@ struct PrecTmaTile {
     static constexpr size_t SMEM = 4 * (size_t)VN * 4 + 16 + 128;   // 2 stages x (r, q), 2 mbarriers, alignment
 };
 
+// Per-level tables of the chunked preconditioner when every column has the
+// same factors (cls_mode 0, n_z <= 8 LZ): 1/D, E, e = E/D and the carry
+// weights of each level's LZ-level chunk, C (forward: 1 - prod of (1 - e)
+// from the chunk's first level up) and Q (backward: from the chunk's last
+// level down).  Each block builds them from the FP32 factors with exactly
+// the operations prec_chunked_body repeats per column and pass, so the solve
+// is bitwise that of prec_chunked_body at a fraction of the instructions.
 template <int LZ>
+struct PrecTab {
+    float g[8 * LZ], E[8 * LZ], e[8 * LZ], C[8 * LZ], Q[8 * LZ];
+};
+
+template <int LZ>
+__device__ __forceinline__ void prec_tab_build(const OpView<float>& op, PrecTab<LZ>& tb, int tid, int nthr) {
+    const int nz = op.nz;
+    for (int k = tid; k < nz; k += nthr) {
+        const float g = ldro(op.fg + k), E = ldro(op.fe + k);   // one factor set: ncls == 1
+        tb.g[k] = g;
+        tb.E[k] = E;
+        tb.e[k] = E * g;
+    }
+    __syncthreads();
+    const int nch = (nz + LZ - 1) / LZ;
+    if (tid < nch) {
+        const int k0 = tid * LZ, kn = min(LZ, nz - k0);
+        float cp = k0 > 0 ? tb.e[k0 - 1] : 0.f;
+        tb.C[k0] = cp;
+        for (int t = 1; t < kn; ++t) {
+            cp = fmaf(tb.e[k0 + t - 1], 1.f - cp, cp);
+            tb.C[k0 + t] = cp;
+        }
+        float dp = tb.e[k0 + kn - 1];
+        tb.Q[k0 + kn - 1] = dp;
+        for (int t = kn - 2; t >= 0; --t) {
+            dp = fmaf(tb.e[k0 + t], 1.f - dp, dp);
+            tb.Q[k0 + t] = dp;
+        }
+    }
+    __syncthreads();
+}
+
+// prec_chunked_body on a staged tile with the tables above: the chunk's r and
+// q at rsrc[t R 32], qsrc[t R 32]; FULL: the chunk has LZ levels.  Holds two
+// block barriers, like prec_chunked_body.
+template <int LZ, int R, bool FULL>
+__device__ __forceinline__ void prec_tab_body(const OpView<float>& op, const PrecTab<LZ>& tb, const Col<float>& col,
+                                              int lane, int ch, int nch, int w0, float* __restrict__ r,
+                                              float* __restrict__ z, float alpha, Acc<float> (&acc)[2],
+                                              float (*sh_y)[32], float (*sh_c)[32], float (*sh_z)[32],
+                                              float (*sh_d)[32], const float* rsrc, const float* qsrc) {
+    const int k0 = ch * LZ;
+    const int kn = FULL ? LZ : min(LZ, op.nz - k0);
+    const bool act = col.valid && kn > 0;
+    const long long pl = op.plane;
+    float* __restrict__ rb = r + col.c + (long long)k0 * pl;
+    float* __restrict__ zb = z + col.c + (long long)k0 * pl;
+    float yv[LZ];
+    float yl = 0.f;
+    if (act) {
+        const float e_in = k0 > 0 ? tb.e[k0 - 1] : 0.f;
+        float rr_c = 0.f;
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            if (FULL || t < kn) {
+                const float rn = fmaf(-alpha, qsrc[t * R * 32], rsrc[t * R * 32]);
+                rb[t * pl] = rn;
+                rr_c = fmaf(rn, rn, rr_c);
+                const float ep = t == 0 ? e_in : tb.e[k0 + t - 1];
+                yl = fmaf(-ep, yl, rn) + yl;
+                yv[t] = yl;
+            }
+        }
+        acc[0].add(rr_c);
+    }
+    sh_y[w0 + ch][lane] = yl;
+    sh_c[w0 + ch][lane] = act ? tb.C[k0 + kn - 1] : 0.f;
+    __syncthreads();
+    float Y = 0.f;
+    for (int cc = 0; cc < ch; ++cc) Y = fmaf(-sh_c[w0 + cc][lane], Y, sh_y[w0 + cc][lane]) + Y;
+    float zl = 0.f;
+    if (act) {
+        float kap_c = 0.f;
+#pragma unroll
+        for (int t = 0; t < LZ; ++t) {
+            if (FULL || t < kn) {
+                const float y = fmaf(-tb.C[k0 + t], Y, yv[t]) + Y;
+                yv[t] = y;
+                kap_c = fmaf(tb.g[k0 + t] * y, y, kap_c);
+            }
+        }
+        acc[1].add(kap_c);
+#pragma unroll
+        for (int t = LZ - 1; t >= 0; --t) {
+            if (FULL || t < kn) {
+                zl = fmaf(tb.g[k0 + t], fmaf(-tb.E[k0 + t], zl, yv[t]), zl);
+                yv[t] = zl;
+            }
+        }
+    }
+    sh_z[w0 + ch][lane] = zl;
+    sh_d[w0 + ch][lane] = act ? tb.Q[k0] : 0.f;
+    __syncthreads();
+    float Z = 0.f;
+    for (int cc = nch - 1; cc > ch; --cc) Z = fmaf(-sh_d[w0 + cc][lane], Z, sh_z[w0 + cc][lane]) + Z;
+    if (act) {
+#pragma unroll
+        for (int t = LZ - 1; t >= 0; --t)
+            if (FULL || t < kn) zb[t * pl] = fmaf(-tb.Q[k0 + t], Z, yv[t]) + Z;
+    }
+}
+
+// RT > 0: one factor set for all columns, tables (PrecTab) and items of RT rows
+// known at compile time; RT == 0: any factor classes, prec_chunked_body.
+template <int LZ, int RT>
 __global__ __launch_bounds__(256, 2) void k_sweep_prec_tma(
     OpView<float> op, const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_q,
     float* __restrict__ r, const float* __restrict__ q, float* __restrict__ z, SolveState* __restrict__ states,
     double* __restrict__ partials, unsigned* __restrict__ counters, int R, int nch, int gx, int nitems) {
     using TT = PrecTmaTile<LZ>;
     __shared__ float sh_y[MAXW][32], sh_c[MAXW][32], sh_z[MAXW][32], sh_d[MAXW][32];
+    __shared__ PrecTab<(RT > 0 ? LZ : 1)> tb[1];
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* sbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 4 * TT::VN);
     const int rhs = blockIdx.y;
     SolveState* st = states + rhs;
     if (st->done) return;
+    if (RT > 0) R = RT;
     const float alpha = (float)st->alpha;
     const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
     const int row = w / nch, ch = w - row * nch;
@@ -1324,6 +1593,7 @@ __global__ __launch_bounds__(256, 2) void k_sweep_prec_tma(
         if ((int)blockIdx.x < nitems) issue(blockIdx.x, 0);
         if ((int)(blockIdx.x + gridDim.x) < nitems) issue(blockIdx.x + gridDim.x, 1);
     }
+    if constexpr (RT > 0) prec_tab_build<LZ>(op, tb[0], tid, 256);
     const long long vb = (long long)rhs * op.vol;
     Acc<float> acc[2];
     uint32_t par0 = 0, par1 = 0;
@@ -1344,8 +1614,17 @@ __global__ __launch_bounds__(256, 2) void k_sweep_prec_tma(
         const int j = (ok && row < R) ? (item / gx) * R + row : op.ny;   // op.ny: no column (barriers only)
         const Col<float> col = make_col(op, (item % gx) * 32 + lane, j);
         const float* rs = sbase + stage * 2 * TT::VN + ((ch * LZ) * R + row) * 32 + lane;
-        prec_chunked_body<float, LZ>(op, col, lane, ch, nch, row * nch, r + vb, q + vb, z + vb, alpha, acc, sh_y,
-                                     sh_c, sh_z, sh_d, rs, rs + TT::VN, R * 32);
+        if constexpr (RT > 0) {
+            if (ch * LZ + LZ <= op.nz)
+                prec_tab_body<LZ, RT, true>(op, tb[0], col, lane, ch, nch, row * nch, r + vb, z + vb, alpha, acc,
+                                            sh_y, sh_c, sh_z, sh_d, rs, rs + TT::VN);
+            else
+                prec_tab_body<LZ, RT, false>(op, tb[0], col, lane, ch, nch, row * nch, r + vb, z + vb, alpha, acc,
+                                             sh_y, sh_c, sh_z, sh_d, rs, rs + TT::VN);
+        } else {
+            prec_chunked_body<float, LZ>(op, col, lane, ch, nch, row * nch, r + vb, q + vb, z + vb, alpha, acc, sh_y,
+                                         sh_c, sh_z, sh_d, rs, rs + TT::VN, R * 32);
+        }
         __syncthreads();            // the stage has been read: refill it
         if (tid == 0 && ok && item + 2 * (int)gridDim.x < nitems) issue(item + 2 * gridDim.x, stage);
     }

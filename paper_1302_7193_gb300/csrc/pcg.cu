@@ -78,10 +78,11 @@ struct pcg_ctx {
     // ... and of u, p, q, z for the pipelined TMA SpMV sweep (8-level chunks)
     CUtensorMap tm2_u, tm2_p, tm2_q, tm2_z;
     bool tma2_ready = false;
-    int spmv2_G = 1, spmv2_nch = 1;
+    int spmv2_G = 1, spmv2_nch = 1, spmv2_gx = 1, spmv2_gy = 1;
     int prec32 = 0;                       // FP32 preconditioner sweep: 0 column/chunked, 2 TMA pipeline
     bool prec_tma_ready = false;
     int prec_R = 1, prec_gx = 1, prec_items = 0, prec_G = 1;
+    int prec_generic = 0;                 // 1: the TMA preconditioner sweep without per-level tables
     dim3 grid_t, block_t;
     int nblk_t = 0;
     double *hb = nullptr, *hx = nullptr;  // device staging for pcg_solve_host
@@ -95,7 +96,8 @@ struct pcg_ctx {
     dim3 grid, block;
     // chunked sweeps (levels split across threads): launch shapes
     int chunked32 = 0, chunked64 = 0, lz_a = 16, lz_b = 16, nch_b = 1;
-    int spmv32 = 0, spmv64 = 0;          // SpMV sweep variant: 0 per column, 1 chunked, 2 chunked + smem tile, 3 TMA
+    int spmv32 = 0, spmv64 = 0;          // SpMV sweep variant: 0 per column, 1 chunked, 2 chunked + smem tile, 3 TMA,
+                                          // 4 persistent two-stage TMA
     // minimum resident blocks asked of the compiler for the chunked FP32 sweeps;
     // 3 for the preconditioner sweep (85-register cap, no spills) measured
     // 9-13 % faster than the uncapped 108 registers at 256^2, 1024^2 and the shell
@@ -452,15 +454,41 @@ bool encode_map(pcg_t h, CUtensorMap* m, float* base, unsigned bx, unsigned by, 
 
 constexpr int TMA_LZ = 16, TMA_BY = 8;
 using SpmvTile = pcg::SpmvTmaTile<TMA_LZ, TMA_BY>;
-constexpr int TMA2_LZ = 8;
-using SpmvTile2 = pcg::SpmvTmaTile<TMA2_LZ, TMA_BY>;
-constexpr size_t SPMV2_SMEM = 2 * ((size_t)SpmvTile2::ZN + 3 * SpmvTile2::VN) * 4 + 16 + 128;
+// persistent pipelined SpMV sweep: 16-level chunks of 32 x 4-column tiles
+constexpr int TMA2_LZ = 16, TMA2_BY = 4;
+size_t spmv2_smem(int nz) { return pcg::spmv_tma2_smem<TMA2_LZ, TMA2_BY>(nz); }
 
 int ensure_ws32(pcg_t h) {
     if (h->u32) return PCG_OK;
     int rc;
     for (float** p : {&h->u32, &h->r32, &h->z32, &h->p32, &h->q32})
         if ((rc = dmalloc(h, p, (size_t)h->ntot))) return rc;
+    if (h->spmv32 == 4) {
+        const unsigned zx = BX + 2 * pcg::TMA_HALO_X;
+        const size_t smem = spmv2_smem(h->nz);
+        int occ = 0, dev = 0, sms = 1;
+        cudaError_t ea = cudaFuncSetAttribute(pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ea == cudaSuccess)
+            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY>,
+                                                               BX * TMA2_BY, smem);
+        if (ea == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        h->spmv2_nch = (h->nz + TMA2_LZ - 1) / TMA2_LZ;
+        h->spmv2_gx = (h->nx + BX - 1) / BX;
+        h->spmv2_gy = (h->ny + TMA2_BY - 1) / TMA2_BY;
+        const long long nitems = (long long)h->spmv2_gx * h->spmv2_gy * h->spmv2_nch;
+        h->spmv2_G = (int)std::max(1LL, std::min(nitems, (long long)sms * std::max(occ, 1)));
+        h->tma2_ready = ea == cudaSuccess && occ >= 1 && nitems < (1LL << 31) &&
+                        encode_map(h, &h->tm2_u, h->u32, BX, TMA2_BY, TMA2_LZ) &&
+                        encode_map(h, &h->tm2_p, h->p32, BX, TMA2_BY, TMA2_LZ) &&
+                        encode_map(h, &h->tm2_q, h->q32, BX, TMA2_BY, TMA2_LZ) &&
+                        encode_map(h, &h->tm2_z, h->z32, zx, TMA2_BY + 2, TMA2_LZ + 2);
+        if (!h->tma2_ready) {
+            cudaGetLastError();
+            h->spmv32 = 3;      // the single-stage TMA sweep
+        }
+    }
     if (h->spmv32 == 3) {
         // the TMA SpMV sweep: maps of the workspace vectors; fall back to the
         // chunked sweep when the driver cannot encode them
@@ -479,33 +507,16 @@ int ensure_ws32(pcg_t h) {
                                                    (int)SpmvTile::SMEM)) == cudaSuccess;
         if (!h->tma_ready) h->spmv32 = (h->chunked32 && h->plane * (long long)h->nrhs < (1LL << 19)) ? 1 : 0;
     }
-    if (h->spmv32 == 4) {
-        const unsigned zx = BX + 2 * pcg::TMA_HALO_X;
-        int occ = 0, dev = 0, sms = 1;
-        cudaError_t ea = cudaFuncSetAttribute(pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA_BY>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPMV2_SMEM);
-        if (ea == cudaSuccess)
-            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA_BY>,
-                                                               BX * TMA_BY, SPMV2_SMEM);
-        if (ea == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        h->spmv2_nch = (h->nz + TMA2_LZ - 1) / TMA2_LZ;
-        const int nitems = h->grid_t.x * h->grid_t.y * h->spmv2_nch;
-        h->spmv2_G = std::max(1, std::min(nitems, sms * std::max(occ, 1)));
-        h->tma2_ready = ea == cudaSuccess && occ >= 1 && h->tma_by == TMA_BY &&
-                        encode_map(h, &h->tm2_u, h->u32, BX, TMA_BY, TMA2_LZ) &&
-                        encode_map(h, &h->tm2_p, h->p32, BX, TMA_BY, TMA2_LZ) &&
-                        encode_map(h, &h->tm2_q, h->q32, BX, TMA_BY, TMA2_LZ) &&
-                        encode_map(h, &h->tm2_z, h->z32, zx, TMA_BY + 2, TMA2_LZ + 2);
-        if (!h->tma2_ready) h->spmv32 = (h->chunked32 && h->plane * (long long)h->nrhs < (1LL << 19)) ? 1 : 0;
-    }
     if (h->prec32 == 2) {
         const unsigned lev = (unsigned)(((h->nz + h->lz_a - 1) / h->lz_a) * h->lz_a);
         int occ = 0;
-        cudaError_t ea = cudaFuncSetAttribute(pcg::k_sweep_prec_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)pcg::PrecTmaTile<16>::SMEM);
+        cudaError_t ea = cudaSuccess;
+        for (auto fn : {pcg::k_sweep_prec_tma<16, 0>, pcg::k_sweep_prec_tma<16, 1>, pcg::k_sweep_prec_tma<16, 2>,
+                        pcg::k_sweep_prec_tma<16, 4>, pcg::k_sweep_prec_tma<16, 8>})
+            if (ea == cudaSuccess)
+                ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcg::PrecTmaTile<16>::SMEM);
         if (ea == cudaSuccess)
-            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg::k_sweep_prec_tma<16>, 256,
+            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg::k_sweep_prec_tma<16, 1>, 256,
                                                                pcg::PrecTmaTile<16>::SMEM);
         int dev = 0, sms = 1;
         if (ea == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess)
@@ -533,9 +544,16 @@ void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, 
         if (h->prec32 == 2 && h->prec_tma_ready && r == h->r32 && q == h->q32 && z == h->z32) {
             const dim3 grid(h->prec_G, h->nrhs, 1), block(BX, 8, 1);
             const int nch = (h->nz + h->lz_a - 1) / h->lz_a;
-            pcg::k_sweep_prec_tma<16><<<grid, block, pcg::PrecTmaTile<16>::SMEM, s>>>(
-                v, h->tm_pr, h->tm_pq, r, q, z, st, h->partials, h->counters, h->prec_R, nch, h->prec_gx,
-                h->prec_items);
+            // one factor set for all columns: per-level carry tables (bitwise the same solve)
+#define PCG_PREC_TMA(RT)                                                                                     \
+    pcg::k_sweep_prec_tma<16, RT><<<grid, block, pcg::PrecTmaTile<16>::SMEM, s>>>(                           \
+        v, h->tm_pr, h->tm_pq, r, q, z, st, h->partials, h->counters, h->prec_R, nch, h->prec_gx, h->prec_items)
+            if (h->cls_mode != 0 || h->prec_generic) PCG_PREC_TMA(0);
+            else if (h->prec_R == 1) PCG_PREC_TMA(1);
+            else if (h->prec_R == 2) PCG_PREC_TMA(2);
+            else if (h->prec_R == 4) PCG_PREC_TMA(4);
+            else PCG_PREC_TMA(8);
+#undef PCG_PREC_TMA
             return;
         }
     }
@@ -570,9 +588,10 @@ void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, 
                                                                                 h->counters, h->nblk_b, h->nch_b)
     if constexpr (sizeof(T) == 4) {
         if (mode == 4 && h->tma2_ready && u == h->u32 && p == h->p32 && q == h->q32 && z == h->z32) {
-            pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA_BY><<<dim3(h->spmv2_G, h->nrhs, 1), h->block_t, SPMV2_SMEM, s>>>(
-                v, h->tm2_u, h->tm2_p, h->tm2_q, h->tm2_z, u, p, q, z, st, h->partials, h->counters, h->grid_t.x,
-                h->grid_t.y, h->spmv2_nch);
+            pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY><<<dim3(h->spmv2_G, h->nrhs, 1), dim3(BX, TMA2_BY, 1),
+                                                       spmv2_smem(h->nz), s>>>(
+                v, h->tm2_u, h->tm2_p, h->tm2_q, h->tm2_z, u, p, q, z, st, h->partials, h->counters, h->spmv2_gx,
+                h->spmv2_gy, h->spmv2_nch);
             return;
         }
         if (mode == 3 && h->tma_ready && u == h->u32 && p == h->p32 && q == h->q32 && z == h->z32) {
@@ -1252,9 +1271,10 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->nblk_t = (int)(h->grid_t.x * h->grid_t.y) * h->nch_b;
     const bool tma_ok = h->lz_b == TMA_LZ && h->nx % 4 == 0 && (long long)h->nrhs * h->nch_b <= 65535 &&
                         (long long)h->nz * h->nrhs < (1LL << 31);
-    // the TMA sweep wherever it applies: 65536 columns 72 us, 2^20 columns
-    // 923 us per sweep at 128 levels (3.3 and 4.1 TB/s)
-    if (tma_ok) h->spmv32 = 3;
+    // the persistent two-stage TMA sweep wherever it applies: 54 us at
+    // 256^2 x 128, 648 us at 1024^2 x 128, 4.50 ms for 16 rhs of 1440 x 640 x 64
+    // (4.3, 5.8, 5.9 TB/s), against 58 us, 832 us and 5.11 ms single-stage
+    if (tma_ok) h->spmv32 = 4;
     // TMA-pipelined FP32 preconditioner sweep: items of prec_R rows of 32
     // columns (prec_R x chunks <= 8 warps), same eligibility plus the chunked form
     {
@@ -1265,13 +1285,15 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
         const bool ptma_ok = h->chunked32 && h->lz_a == 16 && nch_p <= 8 && h->nx % 4 == 0 && h->nrhs <= 65535 &&
                              (long long)h->nz * h->nrhs < (1LL << 31);
         h->prec32 = ptma_ok ? 2 : 0;   // 256x256x128: 52.9 -> 50.8 us; 512x512x64: 93.8 -> 85.2 us
-        if (const char* pv = std::getenv("PCG_PREC")) {            // experiments: chunked|tma
+        if (const char* pv = std::getenv("PCG_PREC")) {            // experiments: chunked|tma|tma-generic
             if (!std::strcmp(pv, "chunked")) h->prec32 = 0;
             if (!std::strcmp(pv, "tma")) h->prec32 = ptma_ok ? 2 : 0;
+            if (!std::strcmp(pv, "tma-generic")) {                   // no per-level tables (tests)
+                h->prec32 = ptma_ok ? 2 : 0;
+                h->prec_generic = 1;
+            }
         }
     }
-    // PCG_SPMV=tma2 (persistent two-stage pipeline, 8-level chunks) measured
-    // 2-4 % slower than the single-stage sweep at every size and is opt-in only.
     if (const char* sv = std::getenv("PCG_SPMV")) {            // experiments: column|chunked|tile|tma|tma2
         const int m = !std::strcmp(sv, "tile") ? 2 : (!std::strcmp(sv, "chunked") ? 1 :
                       (!std::strcmp(sv, "tma") ? 3 : (!std::strcmp(sv, "tma2") ? 4 : 0)));

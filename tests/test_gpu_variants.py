@@ -1,7 +1,7 @@
 """Parity of every sweep variant against the oracle.
 
 The solver picks one kernel per sweep at creation (one thread per column,
-chunked columns, TMA-staged tiles, TMA pipeline); the PCG_* environment
+chunked columns, TMA-staged tiles, persistent TMA pipelines); the PCG_* environment
 variables force the others.  Each variant must reproduce the oracle's
 Algorithm 1 iterates (FP64, fixed iteration count, 1e-10) and the oracle's
 converged solution through the mixed-precision refinement (1e-8), on grids
@@ -23,6 +23,8 @@ CASES = [
     ("latlon72x32x16", W.latlon_problem(72, 32, 16)),
     ("panel40x36x24", W.panel_problem(40, 36, 24)),
     ("box64x64x40", W.box_problem(64, 64, 40, 0.004)),
+    ("box44x30x20", W.box_problem(44, 30, 20, 0.01)),      # ragged tiles in x, y and z
+    ("box4x6x5", W.box_problem(4, 6, 5, 0.01)),            # one tile wrapping onto itself
 ]
 
 FP64_VARIANTS = {
@@ -38,9 +40,10 @@ FP32_VARIANTS = {
     "spmv-column": {"PCG_SPMV": "column"},
     "spmv-chunked": {"PCG_SPMV": "chunked"},
     "spmv-tile": {"PCG_SPMV": "tile"},
-    "spmv-tma2": {"PCG_SPMV": "tma2"},
-    "spmv-tma-8rows": {"PCG_TMA_BY": "8"},
+    "spmv-tma-single-stage": {"PCG_SPMV": "tma"},
+    "spmv-tma-single-stage-8rows": {"PCG_SPMV": "tma", "PCG_TMA_BY": "8"},
     "prec-chunked": {"PCG_PREC": "chunked"},
+    "prec-tma-chunked": {"PCG_PREC": "tma"},
     "all-column": {"PCG_KERNELS": "column"},
 }
 
@@ -112,3 +115,26 @@ def test_multi_rhs_tma_sweeps_match_single(torch_cuda):
             x1 = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
             s1.solve(torch.from_numpy(b.ravel().copy()).cuda(), x1, tol=1e-9, maxit=20000)
             assert np.array_equal(x1.cpu().numpy(), xb[i]), i
+
+
+@pytest.mark.parametrize("p", [W.box_problem(96, 32, 128, 0.004), W.box_problem(64, 64, 40, 0.004),
+                               W.box_problem(64, 32, 32, 0.01), W.box_problem(32, 24, 16, 0.01)],
+                         ids=["nz128-R1", "nz40-R2-ragged", "nz32-R4", "nz16-R8"])
+def test_prec_tables_match_generic_sweep_bitwise(torch_cuda, monkeypatch, p):
+    """With one factor set for all columns (uniform box), the FP32
+    preconditioner sweep reads the chunk-carry weights from per-level tables
+    instead of recomputing them per column; the tables are built with the same
+    FP32 operations, so the mixed solve must equal the generic sweep's bitwise
+    (items of 1, 2, 4 and 8 rows; a ragged last chunk)."""
+    import paper_1302_7193_gb300 as pkg
+    torch = torch_cuda
+    b = torch.from_numpy(W.rhs_for(p, seed=6).ravel().copy()).cuda()
+    xs = []
+    for env in ({}, {"PCG_PREC": "tma-generic"}):
+        _set(monkeypatch, env)
+        with pkg.Solver(p, precision="mixed") as s:
+            x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+            st = s.solve(b, x, tol=1e-10, maxit=20000)
+            assert st.status == 0, st
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1])
