@@ -195,25 +195,31 @@ int pcg_precond_f32(pcg_t h, const float* r, float* z);
 int pcg_time_sweeps(pcg_t h, const double* b, int precision, int passes, double* ms_prec, double* ms_spmv);
 
 /* z = M^{-1} r like pcg_precond, for a caller that must not allocate device
- * memory when it calls: for instance while it is capturing a CUDA graph, where
- * cudaMalloc is not allowed, inside a real-time loop that cannot take an
- * allocation's latency, or when all device memory belongs to another
- * allocator.  There is no counterpart in the paper; it exists for those
- * callers.  No handle is needed and nothing is allocated: the operator
- * tables and Thomas factors go into one fixed 4 MiB device array owned by
- * the library (every GPU that loads the library holds it until exit), so
- * the grid must satisfy 3 n_z + n_y + 2 n_x n_y + 3 n_z c <= 524288 with
- * c = 1 (box, alpha NULL), n_y (latlon, alpha NULL) or n_x n_y (alpha
- * given); larger grids return PCG_ERR_INVALID_ARG with the sizes in
- * pcg_last_error(NULL).  grid, coeffs: host descriptions as for pcg_create
- * (read during the call); r, z: FP64 device pointers, nrhs vectors, not
- * overlapping.  stream: cudaStream_t (NULL = default stream); the work is
- * asynchronous on it.  The first call on each device looks up the array's
- * device address; make that first call before any stream capture.  Every
- * call rewrites the whole array, so calls whose work overlaps on the GPU
- * (other streams, other host threads) race on it; a call is also not
- * thread-safe on the host.  Errors: PCG_ERR_INVALID_ARG, PCG_ERR_CUDA (text
- * in pcg_last_error(NULL)). */
+ * memory when it calls: a real-time loop that cannot take the latency (or the
+ * implicit synchronisation) of a cudaMalloc, or a host whose device memory
+ * all belongs to another allocator (a framework's caching allocator, a fixed
+ * budget), where a library-side cudaMalloc would fail or fragment it.  Such a
+ * caller cannot create a handle at that point, since pcg_create allocates.
+ * There is no counterpart in the paper; it exists for those callers.
+ * Nothing is allocated: the operator tables and Thomas factors go into one
+ * fixed 4 MiB device array owned by the library (every GPU that loads the
+ * library holds it until exit), so the grid must satisfy
+ *     3 n_z + a + 2 n_x n_y + 3 n_z c <= 524288,
+ * a = n_y (box, latlon) or n_x n_y (cubed panel), c = 1 (box, alpha NULL),
+ * n_y (latlon, alpha NULL) or n_x n_y (alpha given, or the cubed panel);
+ * larger grids return PCG_ERR_INVALID_ARG with the sizes in
+ * pcg_last_error(NULL).  grid, coeffs: host descriptions as for pcg_create,
+ * any of the three geometries (read during the call); r, z: FP64 device
+ * pointers, nrhs vectors, not overlapping.  stream: cudaStream_t (NULL =
+ * default stream).  The tables are computed on the host into one static host
+ * buffer of the library and copied to the device array by cudaMemcpyAsync on
+ * `stream` (a copy from pageable memory returns once the buffer has been
+ * read); the factor and solve kernels follow on the same stream.  The first
+ * call on each device looks up the array's device address (with that device
+ * current).  Every call rewrites the whole array and the staging buffer, so
+ * calls whose work overlaps on the GPU (other streams) race on the array, and
+ * calls from several host threads at once race on the staging buffer.
+ * Errors: PCG_ERR_INVALID_ARG, PCG_ERR_CUDA (text in pcg_last_error(NULL)). */
 int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const double* r, double* z, void* stream);
 
 /* ---- served batch (continuous batching of many solves) ------------------ */

@@ -33,6 +33,9 @@ using pcg::SolveState;
 namespace {
 
 thread_local std::string g_create_error = "no error";
+// text that pcg_last_error(NULL) returns when it is not g_create_error (set by
+// the allocation-free entry point, cleared by every other null-handle failure)
+thread_local const char* g_null_error = nullptr;
 
 struct DevTables {
     void* base = nullptr;       // one allocation for all tables of one precision
@@ -177,7 +180,12 @@ struct pcg_ctx {
 namespace {
 
 int fail(pcg_t h, int code, const std::string& msg) {
-    if (h) h->err = msg; else g_create_error = msg;
+    if (h) {
+        h->err = msg;
+    } else {
+        g_create_error = msg;
+        g_null_error = nullptr;
+    }
     return code;
 }
 
@@ -209,23 +217,33 @@ struct HostTables {
     std::vector<double> mass, wv, dk, area, mue, mun;
 };
 
-int build_tables_core(const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t, std::string& err,
-                      double& total_mass) {
-    auto bad = [&](const char* m) { err = m; return PCG_ERR_INVALID_ARG; };
+// Where the tables go: n_z values each of mass, wv, dk; area_len values of
+// area (n_y, or n_x n_y for the panel); n_x n_y values each of mue, mun.
+struct TableOut {
+    double *mass, *wv, *dk, *area, *mue, *mun;
+};
+
+// Number of area values of a geometry: one per latitude (or box) row, one
+// per column on the panel.
+size_t table_area_len(const pcg_grid_t* g) {
+    return g->geometry == PCG_GEOM_CUBED_PANEL ? (size_t)g->n_x * g->n_y : (size_t)g->n_y;
+}
+
+// Fill the tables of grid g and coefficients c into caller-supplied arrays.
+// Allocates nothing; on invalid input returns PCG_ERR_INVALID_ARG with a
+// static message in *err.  total_mass = sum over cells of |T| a_k.
+int tables_into(const pcg_grid_t* g, const pcg_coeffs_t* c, const TableOut& t, const char** err,
+                double* total_mass) {
+    auto bad = [&](const char* m) { *err = m; return PCG_ERR_INVALID_ARG; };
     const int nx = g->n_x, ny = g->n_y, nz = g->n_z;
     const double* z = g->z_iface;
     const double* beta = c->beta_iface;
-    t.mass.assign(nz, 0.0);
-    t.wv.assign(nz, 0.0);
-    t.dk.assign(nz, 0.0);
-    t.area.assign(ny, 0.0);
-    t.mue.assign((size_t)nx * ny, 0.0);
-    t.mun.assign((size_t)nx * ny, 0.0);
     for (int k = 0; k <= nz; ++k) {
         if (!std::isfinite(z[k]) || !std::isfinite(beta[k])) return bad("non-finite z_iface or beta_iface");
         if (k > 0 && !(z[k] > z[k - 1])) return bad("z_iface must be strictly increasing");
     }
     auto centre = [&](int k) { return 0.5 * (z[k] + z[k + 1]); };
+    const size_t nxy = (size_t)nx * ny;
     if (g->geometry == PCG_GEOM_BOX) {
         if (!(g->lx > 0.0) || !(g->ly > 0.0)) return bad("box extents must be positive");
         const double hx = g->lx / nx, hy = g->ly / ny;
@@ -236,7 +254,7 @@ int build_tables_core(const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t,
             t.wv[k] = (k + 1 < nz) ? beta[k + 1] / (centre(k + 1) - centre(k)) : 0.0;
         }
         for (int j = 0; j < ny; ++j) t.area[j] = hx * hy;
-        for (size_t idx = 0; idx < (size_t)nx * ny; ++idx) {
+        for (size_t idx = 0; idx < nxy; ++idx) {
             const double ae = c->alpha_e ? c->alpha_e[idx] : 1.0;
             const double an = c->alpha_n ? c->alpha_n[idx] : 1.0;
             t.mue[idx] = ae * (hy / hx);
@@ -290,7 +308,6 @@ int build_tables_core(const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t,
             t.dk[k] = r1 - r0;
             t.wv[k] = (k + 1 < nz) ? beta[k + 1] * r1 * r1 / (centre(k + 1) - centre(k)) : 0.0;
         }
-        t.area.assign((size_t)nx * ny, 0.0);
         auto xf = [&](int i) { return -1.0 + 2.0 * i / nx; };
         auto yf = [&](int j) { return -1.0 + 2.0 * j / ny; };
         auto xc = [&](int i) { return 0.5 * (xf(i) + xf(i + 1)); };
@@ -310,11 +327,29 @@ int build_tables_core(const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t,
         return bad("unknown geometry");
     }
     // sum over all cells of |T_j| a_k = sum_i (A 1)_i, the Galerkin coarse operator on the constant vector
+    const size_t na = table_area_len(g);
     double sa = 0.0, sm = 0.0;
-    for (double a : t.area) sa += a;
+    for (size_t j = 0; j < na; ++j) sa += t.area[j];
     for (int k = 0; k < nz; ++k) sm += t.mass[k];
-    total_mass = (t.area.size() == (size_t)ny ? (double)nx : 1.0) * sa * sm;
+    *total_mass = (na == (size_t)ny ? (double)nx : 1.0) * sa * sm;
     return PCG_OK;
+}
+
+int build_tables_core(const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t, std::string& err,
+                      double& total_mass) {
+    const int nz = g->n_z;
+    const size_t nxy = (size_t)g->n_x * g->n_y;
+    t.mass.assign(nz, 0.0);
+    t.wv.assign(nz, 0.0);
+    t.dk.assign(nz, 0.0);
+    t.area.assign(table_area_len(g), 0.0);
+    t.mue.assign(nxy, 0.0);
+    t.mun.assign(nxy, 0.0);
+    const char* msg = nullptr;
+    const int rc = tables_into(g, c, TableOut{t.mass.data(), t.wv.data(), t.dk.data(), t.area.data(), t.mue.data(),
+                                              t.mun.data()}, &msg, &total_mass);
+    if (rc) err = msg;
+    return rc;
 }
 
 int build_tables(pcg_t h, const pcg_grid_t* g, const pcg_coeffs_t* c, HostTables& t) {
@@ -1305,6 +1340,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
 
     auto bail = [&](int rc) {
         g_create_error = h->err;
+        g_null_error = nullptr;
         pcg_destroy(h);
         return rc;
     };
@@ -1476,7 +1512,7 @@ size_t pcg_device_bytes(pcg_t h) { return h ? h->bytes : 0; }
 
 long long pcg_kernel_launches(pcg_t h) { return h ? h->launches : 0; }
 
-const char* pcg_last_error(pcg_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+const char* pcg_last_error(pcg_t h) { return h ? h->err.c_str() : (g_null_error ? g_null_error : g_create_error.c_str()); }
 
 void pcg_destroy(pcg_t h) {
     if (!h) return;
@@ -1516,14 +1552,14 @@ void pcg_destroy(pcg_t h) {
 // Line preconditioner without any allocation.
 //
 // For callers that must not allocate device memory at the point of the call:
-// code running while a CUDA stream is being captured into a graph (where a
-// cudaMalloc is not allowed), real-time loops that cannot afford an
-// allocation's latency or synchronisation, and hosts whose device memory is
-// owned entirely by another allocator (a framework's caching allocator or a
-// fixed budget) so that a library-side cudaMalloc would fail or fragment it.
-// Such callers cannot create a handle at that point, because pcg_create
-// allocates.  pcg_precond_noalloc applies the same preconditioner as
-// pcg_precond, keeping its operator tables and Thomas factors in the
+// real-time loops that cannot afford an allocation's latency or the
+// synchronisation a cudaMalloc/cudaFree may imply, and hosts whose device
+// memory is owned entirely by another allocator (a framework's caching
+// allocator or a fixed budget), so that a library-side cudaMalloc would fail
+// or fragment it.  Such callers cannot create a handle at that point, because
+// pcg_create allocates.  pcg_precond_noalloc applies the same preconditioner
+// as pcg_precond: the operator tables come from the same host routine
+// (tables_into) and the factors from the same kernel (k_factors), kept in the
 // fixed-size device array below, which every GPU that loads this library
 // holds until the process exits.
 // ---------------------------------------------------------------------------
@@ -1535,9 +1571,11 @@ __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 double g_noalloc_stage[kNoAllocDoubles];              // host staging of the tables (same layout)
 constexpr int kNoAllocMaxDevices = 64;
 double* g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};   // device address of the scratch, per device
+thread_local char g_noalloc_msg[320];                 // error text of this thread's last failed call
 
 int noalloc_fail(int code, const char* msg) {
-    g_create_error = msg;
+    std::snprintf(g_noalloc_msg, sizeof g_noalloc_msg, "pcg_precond_noalloc: %s", msg);
+    g_null_error = g_noalloc_msg;
     return code;
 }
 
@@ -1548,19 +1586,26 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
     if (!grid || !coeffs || !r || !z) return noalloc_fail(PCG_ERR_INVALID_ARG, "grid, coeffs, r and z are required");
     if (grid->n_x < 1 || grid->n_y < 1 || grid->n_z < 1 || grid->nrhs < 1)
         return noalloc_fail(PCG_ERR_INVALID_ARG, "n_x, n_y, n_z and nrhs must be >= 1");
+    if (grid->nrhs > 65535) return noalloc_fail(PCG_ERR_INVALID_ARG, "nrhs must be <= 65535");
     if (!grid->z_iface || !coeffs->beta_iface) return noalloc_fail(PCG_ERR_INVALID_ARG, "z_iface and beta_iface are required");
     if (!(coeffs->lambda2 >= 0.0) || !std::isfinite(coeffs->lambda2))
         return noalloc_fail(PCG_ERR_INVALID_ARG, "lambda2 must be finite and >= 0");
+    const int geo = grid->geometry;
+    if (geo != PCG_GEOM_BOX && geo != PCG_GEOM_LATLON && geo != PCG_GEOM_CUBED_PANEL)
+        return noalloc_fail(PCG_ERR_INVALID_ARG, "unknown geometry");
     const int nx = grid->n_x, ny = grid->n_y, nz = grid->n_z;
     const size_t nxy = (size_t)nx * ny;
+    // factor classes exactly as pcg_create chooses them
     const bool field = coeffs->alpha_e || coeffs->alpha_n;
-    const int cls_mode = field ? 2 : (grid->geometry == PCG_GEOM_LATLON ? 1 : 0);
+    const int cls_mode = (field || geo == PCG_GEOM_CUBED_PANEL) ? 2 : (geo == PCG_GEOM_LATLON ? 1 : 0);
     const size_t ncls = cls_mode == 0 ? 1 : (cls_mode == 1 ? (size_t)ny : nxy);
-    const size_t need = 3 * (size_t)nz + ny + 2 * nxy + 3 * (size_t)nz * ncls;
+    const size_t na = table_area_len(grid);
+    const size_t ntab = 3 * (size_t)nz + na + 2 * nxy;
+    const size_t need = ntab + 3 * (size_t)nz * ncls;
     if (need > kNoAllocDoubles) {
-        static char msg[256];
+        char msg[256];
         std::snprintf(msg, sizeof msg,
-                      "pcg_precond_noalloc: this grid needs %zu doubles of tables, the fixed scratch holds %zu "
+                      "this grid needs %zu doubles of tables and factors, the fixed scratch holds %zu "
                       "(use pcg_create and pcg_precond)", need, kNoAllocDoubles);
         return noalloc_fail(PCG_ERR_INVALID_ARG, msg);
     }
@@ -1576,56 +1621,15 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
         g_noalloc_dev_ptr[dev] = (double*)p;
     }
     double* d = g_noalloc_dev_ptr[dev];
-    // tables (Section 3.1 geometry, as in pcg_create) into the static staging buffer
+    // tables (Section 3.1 geometry) into the static host staging buffer, by
+    // the routine pcg_create uses
     double* hs = g_noalloc_stage;
-    double *mass = hs, *wv = hs + nz, *dk = hs + 2 * nz, *area = hs + 3 * nz, *mue = area + ny, *mun = mue + nxy;
-    const double* zi = grid->z_iface;
-    const double* beta = coeffs->beta_iface;
-    for (int k = 0; k <= nz; ++k) {
-        if (!std::isfinite(zi[k]) || !std::isfinite(beta[k])) return noalloc_fail(PCG_ERR_INVALID_ARG, "non-finite z_iface or beta_iface");
-        if (k > 0 && !(zi[k] > zi[k - 1])) return noalloc_fail(PCG_ERR_INVALID_ARG, "z_iface must be strictly increasing");
-    }
-    auto centre = [&](int k) { return 0.5 * (zi[k] + zi[k + 1]); };
-    if (grid->geometry == PCG_GEOM_BOX) {
-        if (!(grid->lx > 0.0) || !(grid->ly > 0.0)) return noalloc_fail(PCG_ERR_INVALID_ARG, "box extents must be positive");
-        const double hx = grid->lx / nx, hy = grid->ly / ny;
-        for (int k = 0; k < nz; ++k) {
-            const double dz = zi[k + 1] - zi[k];
-            mass[k] = coeffs->lambda2 * dz;
-            dk[k] = dz;
-            wv[k] = (k + 1 < nz) ? beta[k + 1] / (centre(k + 1) - centre(k)) : 0.0;
-        }
-        for (int j = 0; j < ny; ++j) area[j] = hx * hy;
-        for (size_t idx = 0; idx < nxy; ++idx) {
-            mue[idx] = (coeffs->alpha_e ? coeffs->alpha_e[idx] : 1.0) * (hy / hx);
-            mun[idx] = (coeffs->alpha_n ? coeffs->alpha_n[idx] : 1.0) * (hx / hy);
-        }
-    } else if (grid->geometry == PCG_GEOM_LATLON) {
-        const double pi = 3.14159265358979323846;
-        if (!(grid->lat0 > -0.5 * pi && grid->lat1 < 0.5 * pi && grid->lat0 < grid->lat1))
-            return noalloc_fail(PCG_ERR_INVALID_ARG, "latitude band must satisfy -pi/2 < lat0 < lat1 < pi/2");
-        const double dlon = 2.0 * pi / nx, dlat = (grid->lat1 - grid->lat0) / ny;
-        for (int k = 0; k < nz; ++k) {
-            const double r0 = zi[k], r1 = zi[k + 1];
-            mass[k] = coeffs->lambda2 * ((r1 - r0) * (r1 * r1 + r1 * r0 + r0 * r0)) / 3.0;
-            dk[k] = r1 - r0;
-            wv[k] = (k + 1 < nz) ? beta[k + 1] * r1 * r1 / (centre(k + 1) - centre(k)) : 0.0;
-        }
-        for (int j = 0; j < ny; ++j) {
-            const double ln = grid->lat0 + (j + 1) * dlat, lc = grid->lat0 + (j + 0.5) * dlat;
-            area[j] = dlon * 2.0 * std::cos(lc) * std::sin(0.5 * dlat);
-            for (int i = 0; i < nx; ++i) {
-                const size_t idx = (size_t)j * nx + i;
-                mue[idx] = (coeffs->alpha_e ? coeffs->alpha_e[idx] : 1.0) * dlat / (std::cos(lc) * dlon);
-                mun[idx] = (j + 1 < ny) ? (coeffs->alpha_n ? coeffs->alpha_n[idx] : 1.0) * std::cos(ln) * dlon / dlat : 0.0;
-            }
-        }
-    } else {
-        return noalloc_fail(PCG_ERR_INVALID_ARG, "unknown geometry");
-    }
+    const TableOut tout{hs, hs + nz, hs + 2 * nz, hs + 3 * nz, hs + 3 * nz + na, hs + 3 * nz + na + nxy};
+    const char* msg = nullptr;
+    double total_mass = 0.0;
+    if (tables_into(grid, coeffs, tout, &msg, &total_mass)) return noalloc_fail(PCG_ERR_INVALID_ARG, msg);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t ntab = 3 * (size_t)nz + ny + 2 * nxy;
-    // pageable source: the call returns once the staging buffer has been consumed
+    // a copy from pageable host memory returns once the staging buffer has been read
     e = cudaMemcpyAsync(d, hs, ntab * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return noalloc_fail(PCG_ERR_CUDA, cudaGetErrorString(e));
     OpView<double> v;
@@ -1638,9 +1642,10 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
     v.wv = d + nz;
     v.dk = d + 2 * nz;
     v.area = d + 3 * nz;
-    v.mue = v.area + ny;
+    v.mue = v.area + na;
     v.mun = v.mue + nxy;
-    v.periodic_y = grid->geometry == PCG_GEOM_BOX ? 1 : 0;
+    // the panel's edge faces carry weight 0, so its axes are walked as if periodic (as in pcg_create)
+    v.periodic_y = geo == PCG_GEOM_LATLON ? 0 : 1;
     double* fg = d + ntab;
     double* fe = fg + (size_t)nz * ncls;
     double* fc = fe + (size_t)nz * ncls;
@@ -1649,7 +1654,7 @@ extern "C" int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* c
     v.fc = fc;
     v.cls_mode = cls_mode;
     v.ncls = (int)ncls;
-    v.area_percol = 0;
+    v.area_percol = geo == PCG_GEOM_CUBED_PANEL ? 1 : 0;
     v.amass = nullptr;
     v.awv = nullptr;
     v.arow_step = 0;

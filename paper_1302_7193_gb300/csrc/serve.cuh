@@ -97,7 +97,12 @@ struct pcg_server {
 namespace {
 
 int sfail(pcg_server_t s, int code, const std::string& msg) {
-    if (s) s->err = msg; else g_create_error = msg;
+    if (s) {
+        s->err = msg;
+    } else {
+        g_create_error = msg;
+        g_null_error = nullptr;
+    }
     return code;
 }
 
@@ -433,6 +438,7 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
     }
     auto bail = [&](int rc) {
         g_create_error = s->err;
+        g_null_error = nullptr;
         pcg_server_destroy(s);
         return rc;
     };

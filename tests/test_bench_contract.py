@@ -2,7 +2,8 @@
 machine without a GPU: one line with the arm's metric, unit and workload,
 the timed oracle described in cpu_baseline, and an e2e object with no
 host-device traffic.  The oracle runs a bounded sample (one step of a few
-Algorithm-1 passes of the full 256 x 256 x 128 problem)."""
+Algorithm-1 passes of the full 256 x 256 x 128 problem); ms_per_step and
+steps describe those timed passes, and value scales them to solves/s."""
 import json
 import os
 import subprocess
@@ -22,7 +23,15 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference"
     assert d["metric"] == "PCG solves/s" and d["unit"] == "solves/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
-    assert abs(d["ms_per_step"] - 1000.0 / d["value"]) <= 1e-6 * d["ms_per_step"]
+    # ms_per_step is the step actually timed (a bounded sample of passes);
+    # the solves/s value scales the measured time per pass to a whole solve
+    t = d["timed"]
+    assert t["passes_per_step"] >= 1 and len(t["ms_per_step"]) == 1
+    assert abs(d["ms_per_step"] - t["passes_per_step"] * t["ms_per_pass"]) <= 1e-6 * d["ms_per_step"]
+    with open(os.path.join(ROOT, "tests", "golden", "medium_box_oracle.json")) as f:
+        iters = json.load(f)["iterations"]
+    assert abs(d["value"] - 1000.0 / (t["ms_per_pass"] * iters)) <= 1e-9 * d["value"]
+    assert d["extrapolated_solves_per_s"] == d["value"]
     assert d["dtype"] == "f64" and d["data"] == "synthetic" and d["vs_baseline"] is None
     assert d["config"]["workload"] == "box256x256x128_fp64_tol1e-8"
     cb = d["cpu_baseline"]
