@@ -315,6 +315,40 @@ __device__ __forceinline__ bool grid_sum_acc(Acc<float> (&a)[N], double* partial
     return tid == 0;
 }
 
+// The block-level part of grid_sum_acc alone: the block's compensated FP32
+// sums merged in the same order, converted to FP64 and written by thread 0
+// to dst[0 .. N-1].  Holds one block barrier; the cross-block sum is left to
+// a later kernel (the served batch's per-request scalar step).
+template <int N>
+__device__ __forceinline__ void block_partials(Acc<float> (&a)[N], double* dst) {
+    __shared__ float shs[N][MAXW], shc[N][MAXW];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        float s = a[n].s, c = a[n].c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+            const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+            pair_add(s, c, s2, c2);
+        }
+        if ((tid & 31) == 0) {
+            shs[n][tid >> 5] = s;
+            shc[n][tid >> 5] = c;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            float s = shs[n][0], c = shc[n][0];
+            for (int w = 1; w < nw; ++w) pair_add(s, c, shs[n][w], shc[n][w]);
+            dst[n] = (double)s + (double)c;
+        }
+    }
+}
+
 template <int N>
 __device__ __forceinline__ bool grid_sum_acc(Acc<double> (&a)[N], double* partials, unsigned* counter, int nblocks,
                                              int bid, double (&out)[N]) {

@@ -79,6 +79,8 @@ struct pcg_server {
     int2* h_items = nullptr;            // pinned mirror
     int* h_nitems = nullptr;            // pinned [2]
     int* d_one = nullptr;
+    int* d_inner = nullptr;             // [max_slots]: 1 while the slot's request is in its inner phase
+    int* h_inner = nullptr;             // pinned mirror
     unsigned* d_fetch = nullptr;        // [epochs_per_launch][2]: next item of each epoch's two launches
     int items_cap = 0;
     bool items_dirty = true;
@@ -149,7 +151,7 @@ size_t request_bytes(const pcg_grid_t& g, int cls_mode) {
     const ServeItems it = serve_items(g);
     const size_t nparts = std::max(ntiles, (size_t)std::max(it.nprec, it.nspmv));
     return align_up(ntab * 8) + align_up(ntab * 4) + 2 * align_up(vol * 8) + 5 * align_up(vol * 4) +
-           align_up(nparts * 4 * 8) + align_up(6 * sizeof(CUtensorMap)) + 256;
+           align_up(nparts * 4 * 8) + align_up(6 * sizeof(CUtensorMap)) + align_up(5 * nz * 4) + 256;
 }
 
 int admit(pcg_server_t s, ServeReq* q) {
@@ -194,6 +196,8 @@ int admit(pcg_server_t s, ServeReq* q) {
     m += align_up((size_t)std::max(q->ntiles, std::max(q->nprec, q->nspmv)) * 4 * 8);
     q->tmaps = (CUtensorMap*)m;             // 256-byte aligned like every carved region
     m += align_up(6 * sizeof(CUtensorMap));
+    float* ptab = (float*)m;
+    m += align_up(5 * nz * 4);
     q->counter = (unsigned*)m;
     // tables: same carving as a solver handle
     auto carve = [&](auto& op, auto* base) {
@@ -222,6 +226,9 @@ int admit(pcg_server_t s, ServeReq* q) {
     pcg::k_factors<<<(unsigned)((ncls + 127) / 128), 128, 0, st>>>(q->op64, (double*)q->op64.fg, (double*)q->op64.fe,
                                                                     nullptr);
     pcg::k_to_float<<<256, 256, 0, st>>>(t64, t32, (long long)ntab);
+    // one factor set and chunked preconditioner items: the chunk-carry tables
+    const bool tab = cls_mode == 0 && !q->colmode && nz % pcg::SERVE_LZ == 0 && q->rows <= 4;
+    if (tab) pcg::k_build_prec_tab<<<1, 256, 0, st>>>(q->op32, ptab);
     SRV_CK(s, cudaMemcpyAsync(q->bd, q->b.data(), vol * 8, cudaMemcpyHostToDevice, st));
     SRV_CK(s, cudaMemsetAsync(q->xd, 0, vol * 8, st));
     SRV_CK(s, cudaMemsetAsync(q->counter, 0, sizeof(unsigned), st));
@@ -269,6 +276,7 @@ int admit(pcg_server_t s, ServeReq* q) {
     hs.nspmv = q->nspmv;
     hs.tmaps = q->tmaps;
     hs.prec_tma = q->prec_tma;
+    hs.ptab = (tab && q->prec_tma) ? ptab : nullptr;
     SRV_CK(s, cudaMemcpyAsync(s->d_slots + slot, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
     pcg::k_init_state<<<1, 32, 0, st>>>(s->d_states + 2 * slot, 2, 0.0, 0, nullptr);
     s->launches += 1;
@@ -383,6 +391,9 @@ int rebuild_items(pcg_server_t s) {
     }
     s->h_nitems[0] = (int)na;
     s->h_nitems[1] = (int)nb;
+    for (int i = 0; i < s->max_slots; ++i) s->h_inner[i] = (s->slot_req[i] && s->slot_req[i]->phase == RQ_INNER) ? 1 : 0;
+    SRV_CK(s, cudaMemcpyAsync(s->d_inner, s->h_inner, sizeof(int) * (size_t)s->max_slots, cudaMemcpyHostToDevice,
+                              s->stream));
     SRV_CK(s, cudaMemcpyAsync(s->d_items, ha, sizeof(int2) * (size_t)std::max<long long>(na, 1),
                               cudaMemcpyHostToDevice, s->stream));
     SRV_CK(s, cudaMemcpyAsync(s->d_items + s->items_cap, hb, sizeof(int2) * (size_t)std::max<long long>(nb, 1),
@@ -404,8 +415,10 @@ int capture_epochs(pcg_server_t s) {
         else
             pcg::k_serve_prec<2><<<s->blocks_prec, dim3(BX, 8, 1), pcg::SERVE_PREC_SMEM, s->cap_stream>>>(
                 s->d_slots, s->d_items, s->d_nitems, s->d_fetch + 2 * e);
-        pcg::k_serve_spmv<<<s->blocks_spmv, dim3(BX, pcg::SERVE_BY, 1), ServeSpmvTile::SMEM, s->cap_stream>>>(
+        pcg::k_serve_scalars<0><<<s->max_slots, 256, 0, s->cap_stream>>>(s->d_slots, s->d_inner);
+        pcg::k_serve_spmv<<<s->blocks_spmv, dim3(BX, pcg::SERVE_BY, 1), pcg::SERVE_SPMV_SMEM, s->cap_stream>>>(
             s->d_slots, s->d_items + s->items_cap, s->d_nitems + 1, s->d_fetch + 2 * e + 1);
+        pcg::k_serve_scalars<1><<<s->max_slots, 256, 0, s->cap_stream>>>(s->d_slots, s->d_inner);
     }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
     if (e != cudaSuccess) return sfail(s, PCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -459,19 +472,22 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
         {(void**)&s->d_items, 2 * sizeof(int2) * (size_t)s->items_cap},
         {(void**)&s->d_nitems, 2 * sizeof(int)},
         {(void**)&s->d_one, sizeof(int)},
+        {(void**)&s->d_inner, sizeof(int) * (size_t)max_slots},
         {(void**)&s->d_fetch, 2 * sizeof(unsigned) * (size_t)std::max(s->epochs_per_launch, 1)},
     };
     for (auto& a : dev_allocs)
         if ((e = cudaMalloc(a.p, a.b)) != cudaSuccess) { *a.p = nullptr; s->err = "cudaMalloc failed"; return bail(PCG_ERR_OOM); }
     if ((e = cudaMallocHost((void**)&s->h_states, sizeof(SolveState) * 2 * max_slots)) != cudaSuccess ||
         (e = cudaMallocHost((void**)&s->h_items, 2 * sizeof(int2) * (size_t)s->items_cap)) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&s->h_nitems, 2 * sizeof(int))) != cudaSuccess) {
+        (e = cudaMallocHost((void**)&s->h_nitems, 2 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&s->h_inner, sizeof(int) * (size_t)max_slots)) != cudaSuccess) {
         s->err = "cudaMallocHost failed";
         return bail(PCG_ERR_OOM);
     }
     const int one = 1;
     if ((e = cudaMemcpy(s->d_one, &one, sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(s->d_nitems, 0, 2 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(s->d_inner, 0, sizeof(int) * (size_t)max_slots)) != cudaSuccess ||
         (e = cudaMemset(s->d_slots, 0, sizeof(pcg::ServeSlot) * max_slots)) != cudaSuccess) {
         s->err = cudaGetErrorString(e);
         return bail(PCG_ERR_CUDA);
@@ -482,7 +498,7 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
     if (const char* e5 = std::getenv("PCG_SERVE_PREC_TMA")) s->no_prec_tma = std::atoi(e5) == 0 ? 1 : 0;   // experiments
     // persistent grids: as many blocks as are resident on every SM at once
     if ((e = cudaFuncSetAttribute(pcg::k_serve_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)ServeSpmvTile::SMEM)) != cudaSuccess) {
+                                  (int)pcg::SERVE_SPMV_SMEM)) != cudaSuccess) {
         s->err = cudaGetErrorString(e);
         return bail(PCG_ERR_CUDA);
     }
@@ -500,7 +516,7 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<2>, BX * 8, pcg::SERVE_PREC_SMEM);
     if (eo != cudaSuccess || occ_a < 1) occ_a = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, pcg::k_serve_spmv, BX * pcg::SERVE_BY,
-                                                      ServeSpmvTile::SMEM) != cudaSuccess || occ_b < 1)
+                                                      pcg::SERVE_SPMV_SMEM) != cudaSuccess || occ_b < 1)
         occ_b = 1;
     s->blocks_prec = sms * occ_a;
     s->blocks_spmv = sms * occ_b;
@@ -584,7 +600,7 @@ int pcg_serve_step(pcg_server_t s, int max_epochs, int* n_active, int* n_pending
         if (done_epochs >= max_epochs) break;
         if (s->items_dirty && (rc = rebuild_items(s)) != PCG_OK) return rc;
         SRV_CK(s, cudaGraphLaunch(s->graph, s->stream));
-        s->launches += 2LL * s->epochs_per_launch;
+        s->launches += 4LL * s->epochs_per_launch;   // two sweeps and their scalar steps per epoch
         s->epochs += s->epochs_per_launch;
         done_epochs += s->epochs_per_launch;
         SRV_CK(s, cudaMemcpyAsync(s->h_states, s->d_states, sizeof(SolveState) * 2 * s->max_slots,
@@ -667,9 +683,9 @@ void pcg_server_destroy(pcg_server_t s) {
     cudaStreamSynchronize(s->stream);
     if (s->graph) cudaGraphExecDestroy(s->graph);
     for (void* p : {(void*)s->d_slots, (void*)s->d_states, (void*)s->d_items, (void*)s->d_nitems, (void*)s->d_one,
-                    (void*)s->d_fetch})
+                    (void*)s->d_inner, (void*)s->d_fetch})
         if (p) cudaFree(p);
-    for (void* p : {(void*)s->h_states, (void*)s->h_items, (void*)s->h_nitems})
+    for (void* p : {(void*)s->h_states, (void*)s->h_items, (void*)s->h_nitems, (void*)s->h_inner})
         if (p) cudaFreeHost(p);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
