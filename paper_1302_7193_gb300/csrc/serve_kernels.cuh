@@ -69,6 +69,39 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
+// The served preconditioner's less common item kinds, kept out of line so
+// that their register needs do not weigh on the tabulated path: columns of
+// more than 128 levels (one thread per column) and items without the carry
+// tables (staged, or read directly from r and q).
+__device__ __noinline__ void serve_prec_column(const ServeSlot& s, int bx, int jb, int lane, int w, float alpha,
+                                               Acc<float> (&acc)[2]) {
+    const Col<float> col = make_col(s.op, bx * 32 + lane, jb * 8 + w);
+    if (col.valid) prec_column<float>(s.op, col, s.r + col.c, s.q + col.c, s.z + col.c, alpha, acc[0], acc[1]);
+}
+
+__device__ __noinline__ void serve_prec_generic(const ServeSlot& s, const Col<float>& col, int lane, int ch, int row,
+                                                float alpha, Acc<float> (&acc)[2], float (*sh_y)[32],
+                                                float (*sh_c)[32], float (*sh_z)[32], float (*sh_d)[32],
+                                                const float* rs) {
+    if (rs)
+        prec_chunked_body<float, SERVE_LZ>(s.op, col, lane, ch, s.nch, row * s.nch, s.r, s.q, s.z, alpha, acc, sh_y,
+                                           sh_c, sh_z, sh_d, rs, rs + SERVE_PVN, s.rows * 32);
+    else
+        prec_chunked_body<float, SERVE_LZ>(s.op, col, lane, ch, s.nch, row * s.nch, s.r, s.q, s.z, alpha, acc, sh_y,
+                                           sh_c, sh_z, sh_d);
+}
+
+// The tabulated chunked solve of one staged item, one function per item
+// height, each with its own register allocation.
+template <int R>
+__device__ __noinline__ void serve_prec_tab(const ServeSlot& s, const PrecTab<SERVE_LZ>& tb, const Col<float>& col,
+                                            int lane, int ch, int row, float alpha, Acc<float> (&acc)[2],
+                                            float (*sh_y)[32], float (*sh_c)[32], float (*sh_z)[32],
+                                            float (*sh_d)[32], const float* rs) {
+    prec_tab_body<SERVE_LZ, R, true>(s.op, tb, col, lane, ch, s.nch, row * s.nch, s.r, s.z, alpha, acc, sh_y, sh_c,
+                                     sh_z, sh_d, rs, rs + SERVE_PVN);
+}
+
 // Items are taken in arrival order from `fetch` (zeroed before the launch):
 // thread 0 draws an item when it refills a stage, so a block's stages hold its
 // items in the order drawn, and once one of them is past the end of the list
@@ -153,8 +186,7 @@ __global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __res
             const int bx = wk.y % s.gx, jb = wk.y / s.gx;
             Acc<float> acc[2];
             if (s.colmode) {
-                const Col<float> col = make_col(s.op, bx * 32 + lane, jb * 8 + w);
-                if (col.valid) prec_column<float>(s.op, col, s.r + col.c, s.q + col.c, s.z + col.c, alpha, acc[0], acc[1]);
+                serve_prec_column(s, bx, jb, lane, w, alpha, acc);
             } else {
                 // warp w: row w / nch of the item, chunk w % nch; warps past
                 // rows * nch (and an item whose copies did not land) only take
@@ -175,21 +207,15 @@ __global__ __launch_bounds__(256, MINB) void k_serve_prec(const ServeSlot* __res
                     __syncthreads();
                     const float* rs = sbase + g * 2 * SERVE_PVN + ((ch * SERVE_LZ) * s.rows + row) * 32 + lane;
                     if (s.rows == 1)
-                        prec_tab_body<SERVE_LZ, 1, true>(s.op, tb, col, lane, ch, s.nch, row * s.nch, s.r, s.z, alpha,
-                                                         acc, sh_y, sh_c, sh_z, sh_d, rs, rs + SERVE_PVN);
+                        serve_prec_tab<1>(s, tb, col, lane, ch, row, alpha, acc, sh_y, sh_c, sh_z, sh_d, rs);
                     else if (s.rows == 2)
-                        prec_tab_body<SERVE_LZ, 2, true>(s.op, tb, col, lane, ch, s.nch, row * s.nch, s.r, s.z, alpha,
-                                                         acc, sh_y, sh_c, sh_z, sh_d, rs, rs + SERVE_PVN);
+                        serve_prec_tab<2>(s, tb, col, lane, ch, row, alpha, acc, sh_y, sh_c, sh_z, sh_d, rs);
                     else
-                        prec_tab_body<SERVE_LZ, 4, true>(s.op, tb, col, lane, ch, s.nch, row * s.nch, s.r, s.z, alpha,
-                                                         acc, sh_y, sh_c, sh_z, sh_d, rs, rs + SERVE_PVN);
-                } else if (was_staged) {
-                    const float* rs = sbase + g * 2 * SERVE_PVN + ((ch * SERVE_LZ) * s.rows + row) * 32 + lane;
-                    prec_chunked_body<float, SERVE_LZ>(s.op, col, lane, ch, s.nch, row * s.nch, s.r, s.q, s.z, alpha,
-                                                       acc, sh_y, sh_c, sh_z, sh_d, rs, rs + SERVE_PVN, s.rows * 32);
+                        serve_prec_tab<4>(s, tb, col, lane, ch, row, alpha, acc, sh_y, sh_c, sh_z, sh_d, rs);
                 } else {
-                    prec_chunked_body<float, SERVE_LZ>(s.op, col, lane, ch, s.nch, row * s.nch, s.r, s.q, s.z, alpha,
-                                                       acc, sh_y, sh_c, sh_z, sh_d);
+                    const float* rs = was_staged
+                        ? sbase + g * 2 * SERVE_PVN + ((ch * SERVE_LZ) * s.rows + row) * 32 + lane : nullptr;
+                    serve_prec_generic(s, col, lane, ch, row, alpha, acc, sh_y, sh_c, sh_z, sh_d, rs);
                 }
             }
             block_partials<2>(acc, s.partials + 2LL * wk.y);
