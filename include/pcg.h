@@ -194,6 +194,14 @@ int pcg_precond_f32(pcg_t h, const float* r, float* z);
  * workspace; blocks until done.  Errors: PCG_ERR_INVALID_ARG, PCG_ERR_CUDA. */
 int pcg_time_sweeps(pcg_t h, const double* b, int precision, int passes, double* ms_prec, double* ms_spmv);
 
+/* Benchmark helper: as pcg_time_sweeps, but the `passes` passes run back to
+ * back as in a solve (no event between the sweeps; the FP32 sweeps of
+ * PCG_MIXED overlap their neighbours' start and end as in the solve's
+ * graphs), and the mean device time of one pass (preconditioner sweep plus
+ * SpMV sweep) is returned in *ms_per_pass.  Blocks until done.  Errors:
+ * PCG_ERR_INVALID_ARG, PCG_ERR_CUDA. */
+int pcg_time_passes(pcg_t h, const double* b, int precision, int passes, double* ms_per_pass);
+
 /* z = M^{-1} r like pcg_precond, for a caller that must not allocate device
  * memory when it calls: a real-time loop that cannot take the latency (or the
  * implicit synchronisation) of a cudaMalloc, or a host whose device memory

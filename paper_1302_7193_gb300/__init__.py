@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "not_converge
 
 EXPORTED = (
     "pcg_create", "pcg_solve", "pcg_solve_host", "pcg_rhs_stats", "pcg_apply_A", "pcg_precond",
-    "pcg_apply_A_f32", "pcg_precond_f32", "pcg_time_sweeps", "pcg_sync", "pcg_device_bytes", "pcg_kernel_launches",
+    "pcg_apply_A_f32", "pcg_precond_f32", "pcg_time_sweeps", "pcg_time_passes", "pcg_sync", "pcg_device_bytes", "pcg_kernel_launches",
     "pcg_last_error", "pcg_destroy", "pcg_precond_noalloc",
     "pcg_server_create", "pcg_serve_submit", "pcg_serve_step", "pcg_serve_poll", "pcg_serve_info",
     "pcg_server_last_error", "pcg_server_destroy",
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = I
     lib.pcg_time_sweeps.argtypes = [P, P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.pcg_time_sweeps.restype = I
+    lib.pcg_time_passes.argtypes = [P, P, I, I, ctypes.POINTER(D)]
+    lib.pcg_time_passes.restype = I
     lib.pcg_sync.argtypes = [P]
     lib.pcg_sync.restype = I
     lib.pcg_device_bytes.argtypes = [P]
@@ -279,6 +281,13 @@ class Solver:
         self._check(self.lib.pcg_time_sweeps(self.h, _dptr(b, "f64", self.n), prec, int(passes),
                                              ctypes.byref(a), ctypes.byref(c)))
         return a.value, c.value
+
+    def pcg_time_passes(self, b, precision: str = "fp64", passes: int = 20) -> float:
+        """Mean device ms of one pass (both sweeps) with the passes back to back."""
+        a = ctypes.c_double()
+        prec = {"fp64": PCG_FP64, "mixed": PCG_MIXED}[precision]
+        self._check(self.lib.pcg_time_passes(self.h, _dptr(b, "f64", self.n), prec, int(passes), ctypes.byref(a)))
+        return a.value
 
     def pcg_sync(self):
         self._check(self.lib.pcg_sync(self.h))

@@ -1094,6 +1094,16 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
 }
 
+// Programmatic dependent launch: a sweep launched with programmatic stream
+// serialization may start while the sweep before it drains.  Everything it
+// does before pdl_wait() must not read what earlier sweeps wrote; pdl_wait()
+// returns once the previous grid has completed and its writes are visible
+// (at once when the launch had no such dependency).  pdl_trigger() lets the
+// next sweep launch; it comes after pdl_wait(), so a sweep two launches back
+// is always complete when a sweep starts.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <int LZ, int BYT>
 struct SpmvTmaTile {
     static constexpr int ZX = BX + 2 * TMA_HALO_X, ZY = BYT + 2, ZZ = LZ + 2;
@@ -1374,10 +1384,10 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
     uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 2 * STAGE + ((3 * nz + 4) & ~3));
     const int rhs = blockIdx.y;
     SolveState* st = states + rhs;
-    if (st->done) return;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int nitems = gx * gy * nchunks;
     const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
+    // prologue on data no sweep writes (it may overlap the previous sweep)
     if (tid == 0) {
         mbar_init(bar0);
         mbar_init(bar1);
@@ -1389,6 +1399,9 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
     }
     if (tid == 0) tbw[0] = 0.f;
     __syncthreads();
+    pdl_wait();
+    pdl_trigger();
+    if (st->done) return;
     auto issue = [&](int item, int stage) {
         const int ch = item % nchunks, tile = item / nchunks;
         const int i0 = (tile % gx) * BX, j0 = (tile / gx) * BYT, lev0 = rhs * nz + ch * LZ;
@@ -1603,18 +1616,23 @@ __global__ __launch_bounds__(256, 2) void k_sweep_prec_tma(
     uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 4 * TT::VN);
     const int rhs = blockIdx.y;
     SolveState* st = states + rhs;
-    if (st->done) return;
     if (RT > 0) R = RT;
-    const float alpha = (float)st->alpha;
     const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
     const int row = w / nch, ch = w - row * nch;
     const uint32_t bytes = 2u * 32u * (uint32_t)R * (uint32_t)(nch * LZ) * 4u;
     const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
+    // prologue on data no sweep writes (it may overlap the previous sweep):
+    // the barriers and, with one factor set, the carry tables
     if (tid == 0) {
         mbar_init(bar0);
         mbar_init(bar1);
     }
     __syncthreads();
+    if constexpr (RT > 0) prec_tab_build<LZ>(op, tb[0], tid, 256);
+    pdl_wait();
+    pdl_trigger();
+    if (st->done) return;
+    const float alpha = (float)st->alpha;
     const int lev0 = rhs * op.nz;
     auto issue = [&](int item, int stage) {
         const uint32_t bar = stage ? bar1 : bar0;
@@ -1627,7 +1645,6 @@ __global__ __launch_bounds__(256, 2) void k_sweep_prec_tma(
         if ((int)blockIdx.x < nitems) issue(blockIdx.x, 0);
         if ((int)(blockIdx.x + gridDim.x) < nitems) issue(blockIdx.x + gridDim.x, 1);
     }
-    if constexpr (RT > 0) prec_tab_build<LZ>(op, tb[0], tid, 256);
     const long long vb = (long long)rhs * op.vol;
     Acc<float> acc[2];
     uint32_t par0 = 0, par1 = 0;

@@ -86,6 +86,7 @@ struct pcg_ctx {
     bool prec_tma_ready = false;
     int prec_R = 1, prec_gx = 1, prec_items = 0, prec_G = 1;
     int prec_generic = 0;                 // 1: the TMA preconditioner sweep without per-level tables
+    int pdl = 1;                          // FP32 TMA sweeps launched with programmatic dependencies (PCG_PDL=0: off)
     dim3 grid_t, block_t;
     int nblk_t = 0;
     double *hb = nullptr, *hx = nullptr;  // device staging for pcg_solve_host
@@ -568,12 +569,34 @@ int ensure_ws32(pcg_t h) {
     return PCG_OK;
 }
 
+// Launch a kernel, with programmatic stream serialization when pdl is set
+// (the kernel then overlaps the end of the previous one in the stream up to
+// its pdl_wait(); only kernels that call it may be launched this way).
+template <typename... KArgs, typename... Args>
+void launch_pdl(bool pdl, void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args... args) {
+    if (!pdl) {
+        kern<<<g, b, smem, s>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Launch the preconditioner sweep / SpMV sweep in the variant chosen at creation.
 template <typename T>
 bool use_chunked(pcg_t h) { return sizeof(T) == 4 ? h->chunked32 != 0 : h->chunked64 != 0; }
 
 template <typename T>
-void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, SolveState* st) {
+void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, SolveState* st, bool pdl = false) {
     const bool chunked = use_chunked<T>(h);
     if constexpr (sizeof(T) == 4) {
         if (h->prec32 == 2 && h->prec_tma_ready && r == h->r32 && q == h->q32 && z == h->z32) {
@@ -581,8 +604,8 @@ void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, 
             const int nch = (h->nz + h->lz_a - 1) / h->lz_a;
             // one factor set for all columns: per-level carry tables (bitwise the same solve)
 #define PCG_PREC_TMA(RT)                                                                                     \
-    pcg::k_sweep_prec_tma<16, RT><<<grid, block, pcg::PrecTmaTile<16>::SMEM, s>>>(                           \
-        v, h->tm_pr, h->tm_pq, r, q, z, st, h->partials, h->counters, h->prec_R, nch, h->prec_gx, h->prec_items)
+    launch_pdl(pdl, pcg::k_sweep_prec_tma<16, RT>, grid, block, pcg::PrecTmaTile<16>::SMEM, s, v, h->tm_pr,      \
+               h->tm_pq, r, (const T*)q, z, st, h->partials, h->counters, h->prec_R, nch, h->prec_gx, h->prec_items)
             if (h->cls_mode != 0 || h->prec_generic) PCG_PREC_TMA(0);
             else if (h->prec_R == 1) PCG_PREC_TMA(1);
             else if (h->prec_R == 2) PCG_PREC_TMA(2);
@@ -616,17 +639,17 @@ void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, 
 }
 
 template <typename T>
-void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, T* z, SolveState* st) {
+void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, T* z, SolveState* st,
+                 bool pdl = false) {
     const int mode = sizeof(T) == 4 ? h->spmv32 : h->spmv64;
 #define PCG_SPMV_CH(LZ, TILE, MB)                                                                            \
     pcg::k_sweep_spmv_chunked<T, LZ, TILE, MB><<<h->grid_b, h->block_b, 0, s>>>(v, u, p, q, z, st, h->partials,  \
                                                                                 h->counters, h->nblk_b, h->nch_b)
     if constexpr (sizeof(T) == 4) {
         if (mode == 4 && h->tma2_ready && u == h->u32 && p == h->p32 && q == h->q32 && z == h->z32) {
-            pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY><<<dim3(h->spmv2_G, h->nrhs, 1), dim3(BX, TMA2_BY, 1),
-                                                       spmv2_smem(h->nz), s>>>(
-                v, h->tm2_u, h->tm2_p, h->tm2_q, h->tm2_z, u, p, q, z, st, h->partials, h->counters, h->spmv2_gx,
-                h->spmv2_gy, h->spmv2_nch);
+            launch_pdl(pdl, pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY>, dim3(h->spmv2_G, h->nrhs, 1),
+                       dim3(BX, TMA2_BY, 1), spmv2_smem(h->nz), s, v, h->tm2_u, h->tm2_p, h->tm2_q, h->tm2_z, u, p, q,
+                       (const T*)z, st, h->partials, h->counters, h->spmv2_gx, h->spmv2_gy, h->spmv2_nch);
             return;
         }
         if (mode == 3 && h->tma_ready && u == h->u32 && p == h->p32 && q == h->q32 && z == h->z32) {
@@ -881,8 +904,8 @@ int capture_passes(pcg_t h, OpView<T> v, T* u, T* r, T* z, T* p, T* q, SolveStat
                 continue;
             }
         }
-        launch_prec<T>(h, h->cap_stream, v, r, q, z, st);
-        launch_spmv<T>(h, h->cap_stream, v, u, p, q, z, st);
+        launch_prec<T>(h, h->cap_stream, v, r, q, z, st, h->pdl != 0);
+        launch_spmv<T>(h, h->cap_stream, v, u, p, q, z, st, h->pdl != 0);
     }
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess) return fail(h, PCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -1281,6 +1304,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->nblk_a = (int)(h->grid_a.x * h->grid_a.y);
     h->lz_b = 16;
     if (const char* e = std::getenv("PCG_SPMV_LZ")) h->lz_b = std::atoi(e) == 8 ? 8 : 16;
+    if (const char* e = std::getenv("PCG_PDL")) h->pdl = std::atoi(e) ? 1 : 0;
     if (const char* e = std::getenv("PCG_PREC_MINB")) h->prec_minb = std::atoi(e);
     if (const char* e = std::getenv("PCG_SPMV_MINB")) h->spmv_minb = std::atoi(e);
     h->nch_b = (h->nz + h->lz_b - 1) / h->lz_b;
@@ -1499,6 +1523,56 @@ int pcg_time_sweeps(pcg_t h, const double* b, int precision, int passes, double*
     for (auto& e : ev) cudaEventDestroy(e);
     *ms_prec = tp / passes;
     *ms_spmv = ts / passes;
+    return PCG_OK;
+}
+
+int pcg_time_passes(pcg_t h, const double* b, int precision, int passes, double* ms_per_pass) {
+    if (!h) return fail(nullptr, PCG_ERR_INVALID_ARG, "handle is NULL");
+    if (!b || !ms_per_pass || passes < 1) return fail(h, PCG_ERR_INVALID_ARG, "b, ms_per_pass and passes >= 1 required");
+    if (precision != PCG_FP64 && precision != PCG_MIXED) return fail(h, PCG_ERR_INVALID_ARG, "unknown precision");
+    int rc;
+    if ((rc = ensure_ws64(h))) return rc;
+    if (precision == PCG_MIXED && (rc = ensure_ws32(h))) return rc;
+    cudaStream_t s = h->stream;
+    const OpView<double> v = h->view64();
+    const OpView<float> v32 = h->view32();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PCG_CK(h, cudaEventCreate(&e0));
+    PCG_CK(h, cudaEventCreate(&e1));
+    PCG_CK(h, cudaMemsetAsync(h->z64, 0, sizeof(double) * h->ntot, s));   // x0 = 0
+    pcg::k_init_state<<<(h->nrhs + 63) / 64, 64, 0, s>>>(h->st, h->nrhs, 0.0, passes, nullptr);
+    if (precision == PCG_FP64) {
+        pcg::k_residual<double><<<h->grid, h->block, 0, s>>>(v, b, h->z64, h->u64, h->r64, h->st, h->partials,
+                                                            h->counters, h->nblocks, 0);
+        PCG_CK(h, cudaMemsetAsync(h->p64, 0, sizeof(double) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->q64, 0, sizeof(double) * h->ntot, s));
+    } else {
+        pcg::k_residual<float><<<h->grid, h->block, 0, s>>>(v, b, h->z64, nullptr, h->r32, h->st, h->partials,
+                                                           h->counters, h->nblocks, 3);
+        pcg::k_init_state<<<(h->nrhs + 63) / 64, 64, 0, s>>>(h->st_in, h->nrhs, 0.0, passes, nullptr);
+        PCG_CK(h, cudaMemsetAsync(h->u32, 0, sizeof(float) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->p32, 0, sizeof(float) * h->ntot, s));
+        PCG_CK(h, cudaMemsetAsync(h->q32, 0, sizeof(float) * h->ntot, s));
+    }
+    PCG_CK(h, cudaGetLastError());
+    PCG_CK(h, cudaEventRecord(e0, s));
+    for (int i = 0; i < passes; ++i) {
+        if (precision == PCG_FP64) {
+            launch_prec<double>(h, s, v, h->r64, h->q64, h->z64, h->st);
+            launch_spmv<double>(h, s, v, h->u64, h->p64, h->q64, h->z64, h->st);
+        } else {
+            launch_prec<float>(h, s, v32, h->r32, h->q32, h->z32, h->st_in, h->pdl != 0);
+            launch_spmv<float>(h, s, v32, h->u32, h->p32, h->q32, h->z32, h->st_in, h->pdl != 0);
+        }
+    }
+    PCG_CK(h, cudaEventRecord(e1, s));
+    PCG_CK(h, cudaGetLastError());
+    PCG_CK(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    PCG_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_pass = ms / passes;
     return PCG_OK;
 }
 
