@@ -292,7 +292,8 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def serve_measure(dev, pkg, W, torch, seconds: float, mix: str = "paper", compare: bool = True):
+def serve_measure(dev, pkg, W, torch, seconds: float, mix: str = "paper", compare: bool = True,
+                  preconditioner: str = "line", arms=None):
     """Served batch: Poisson arrivals (200 requests/s, seed 1) of solves with
     random sizes {64..512}^2 x {32,64,128}, anisotropy 1e2-1e5 and lambda^2 in
     [1e-4, 1], tol 1e-8, mixed precision, admission bounded by 60 GB.  Each
@@ -300,8 +301,11 @@ def serve_measure(dev, pkg, W, torch, seconds: float, mix: str = "paper", compar
     retirement.  Right-hand sides are generated before the clock starts.
     compare: the same requests one at a time through pcg_solve_host (b from
     and x back to host memory like a served request, solver creation
-    included), FP64 and mixed, and mixed with b already on the device; the
-    served solutions are compared with the one-at-a-time FP64 ones."""
+    included), FP64, mixed, FP64 CG with the FP32 V-cycle, and mixed with b
+    already on the device (`arms` selects some of them); the served solutions
+    are compared with the one-at-a-time FP64 ones.  preconditioner: the
+    server's mode, "line" (batched sweeps of the mixed form) or
+    "multigrid-f32" (multigrid-preconditioned solves by a worker pool)."""
     import numpy as np
     scale = 1.0
     if mix == "small":
@@ -315,7 +319,8 @@ def serve_measure(dev, pkg, W, torch, seconds: float, mix: str = "paper", compar
     rhs = [W.rhs_for(r.problem, seed=r.rhs_seed) for r in reqs]
     rhs_keep = list(rhs) if compare else None
     stream = torch.cuda.current_stream(dev)
-    srv = pkg.Server(budget_bytes=60 * 10 ** 9, max_slots=256, stream=stream.cuda_stream)
+    srv = pkg.Server(budget_bytes=60 * 10 ** 9, max_slots=256, stream=stream.cuda_stream,
+                     preconditioner=preconditioner)
     # warm-up: one small request (graph capture, lazy module load)
     w = W.box_problem(64, 64, 32, 0.001, lambda2=0.1)
     wid = srv.submit(w, W.rhs_for(w, seed=5), tol=1e-8)
@@ -351,20 +356,22 @@ def serve_measure(dev, pkg, W, torch, seconds: float, mix: str = "paper", compar
     line = {"metric": "PCG solves/s", "value": len(done) / elapsed, "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic", "workload": "serve",
             "config": {"arrivals": "Poisson 200/s, seed 1" if scale == 1.0 else "Poisson 2000/s, seed 1",
-                       "mix": mix, "seconds_of_arrivals": seconds, "requests": len(reqs), "budget_gb": 60,
+                       "server": preconditioner, "mix": mix, "seconds_of_arrivals": seconds, "requests": len(reqs), "budget_gb": 60,
                        "max_slots": 256, "tol": 1e-8, "mean_unknowns": unknowns / max(1, len(done))},
             "completed": len(done), "converged": ok, "elapsed_s": elapsed,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
-            "inner_epochs": epochs, "fp32_inner_gbs_algorithmic": inner_bytes / elapsed / 1e9,
+            "inner_epochs": epochs,
+            "fp32_inner_gbs_algorithmic": inner_bytes / elapsed / 1e9 if preconditioner == "line" else None,
             "worst_relres_true": max(st.relres_true for _, _, st, _ in done),
             "met_tol_or_floor": sum(1 for _, r, st, _ in done
                                     if st.relres_true < r.tol or st.relres_true <= 2.0 * st.relres_floor),
             "clocks": clocks}
     if compare:
         served_x = {idx: x for idx, _, _, x in done}
-        arms = [("fp64", "host"), ("mixed", "host"), ("mixed", "device")]
-        worst = 0.0
+        if arms is None:
+            arms = [("fp64", "host"), ("mixed", "host"), ("multigrid-f32", "host"), ("mixed", "device")]
+        worst = None
         for prec, where in arms:
             t = 0.0
             its = 0
@@ -373,12 +380,21 @@ def serve_measure(dev, pkg, W, torch, seconds: float, mix: str = "paper", compar
                     bh = np.ascontiguousarray(bnp.ravel())
                     xh = np.zeros_like(bh)
                     t1 = time.perf_counter()
-                    with pkg.Solver(r.problem, precision=prec, stream=stream.cuda_stream) as s1:
+                    kw = {"preconditioner": prec} if prec == "multigrid-f32" else {"precision": prec}
+                    with pkg.Solver(r.problem, stream=stream.cuda_stream, **kw) as s1:
                         st = s1.solve_host(bh, xh, tol=r.tol, maxit=200000)
+                        # multigrid: restarted from x until the true residual meets tol or
+                        # twice the rounding floor, at most four solves (as the server does)
+                        n_solves = 1
+                        while (prec == "multigrid-f32" and st.status == 0 and st.relres_true >= r.tol
+                               and st.relres_true > 2.0 * st.relres_floor and n_solves < 4):
+                            its += st.iterations
+                            st = s1.solve_host(bh, xh, tol=r.tol, maxit=200000)
+                            n_solves += 1
                     t += time.perf_counter() - t1
                     if prec == "fp64" and idx in served_x:
                         xs = np.asarray(served_x[idx]).ravel()
-                        worst = max(worst, float(np.linalg.norm(xs - xh) / np.linalg.norm(xh)))
+                        worst = max(worst or 0.0, float(np.linalg.norm(xs - xh) / np.linalg.norm(xh)))
                 else:
                     bt = torch.from_numpy(bnp.ravel()).to(dev)
                     x = torch.zeros_like(bt)
@@ -389,16 +405,19 @@ def serve_measure(dev, pkg, W, torch, seconds: float, mix: str = "paper", compar
                     torch.cuda.synchronize(dev)
                     t += time.perf_counter() - t1
                 its += st.iterations
-            line[f"sequential_{prec}_{where}"] = {"solves_per_s": len(reqs) / t, "seconds": t, "iterations": its}
-        line["served_speedup_vs_sequential_fp64_host"] = line["value"] / line["sequential_fp64_host"]["solves_per_s"]
-        line["served_speedup_vs_sequential_mixed_host"] = line["value"] / line["sequential_mixed_host"]["solves_per_s"]
-        line["served_vs_sequential_fp64_max_relerr"] = worst
+            line[f"sequential_{prec.replace('-', '_')}_{where}"] = {"solves_per_s": len(reqs) / t, "seconds": t,
+                                                                   "iterations": its}
+        for key in ("fp64_host", "mixed_host", "multigrid_f32_host"):
+            if f"sequential_{key}" in line:
+                line[f"served_speedup_vs_sequential_{key}"] = line["value"] / line[f"sequential_{key}"]["solves_per_s"]
+        if worst is not None:
+            line["served_vs_sequential_fp64_max_relerr"] = worst
     return line
 
 
 def run_serve(args, dev, pkg, W, torch):
-    print(json.dumps(serve_measure(dev, pkg, W, torch, args.serve_seconds, args.serve_mix, args.serve_compare)),
-          flush=True)
+    print(json.dumps(serve_measure(dev, pkg, W, torch, args.serve_seconds, args.serve_mix, args.serve_compare,
+                                   preconditioner=args.serve_prec)), flush=True)
 
 
 def run_paper_panel(args, dev, pkg, W, torch):
@@ -651,6 +670,9 @@ def main():
                     help="serve: seconds of arrivals (200 req/s); the default benchmark line uses 0.5")
     ap.add_argument("--serve-mix", choices=["paper", "small"], default="paper",
                     help="serve: the full request mix, or only requests of at most 128 x 128 x 64 at 10x the rate")
+    ap.add_argument("--serve-prec", choices=["line", "multigrid-f32"], default="line",
+                    help="serve: the server's mode, batched line-preconditioned mixed solves or multigrid-preconditioned "
+                         "FP64 solves by a worker pool")
     ap.add_argument("--serve-compare", action="store_true",
                     help="serve: also solve the same requests one at a time with the FP64 and mixed solvers")
     ap.add_argument("--profile-vcycle", choices=["fp64", "fp32"], default=None,
@@ -909,7 +931,16 @@ def main():
     extras = {}
     if rank == 0 and world == 1 and not args.quick:
         extras["box1024"] = large_config_measure(dev, pkg, W, torch, "box1024", hbm_peak)
-        extras["serve"] = serve_measure(dev, pkg, W, torch, 0.5, "paper", compare=True)
+        extras["serve"] = serve_measure(dev, pkg, W, torch, 0.5, "paper", compare=True,
+                                        arms=[("fp64", "host"), ("mixed", "host"), ("mixed", "device")])
+        # the same requests served with the multigrid preconditioner (worker pool), against one-at-a-time
+        # multigrid solves; the other one-at-a-time arms are the line server's
+        smg = serve_measure(dev, pkg, W, torch, 0.5, "paper", compare=True, preconditioner="multigrid-f32",
+                            arms=[("multigrid-f32", "host")])
+        for key in ("sequential_fp64_host", "sequential_mixed_host"):
+            smg[key] = extras["serve"][key]
+            smg["served_speedup_vs_" + key] = smg["value"] / smg[key]["solves_per_s"]
+        extras["serve_multigrid"] = smg
         extras["shell_batch"] = large_config_measure(dev, pkg, W, torch, "shell-batch", hbm_peak,
                                                      same_accuracy=False)
 

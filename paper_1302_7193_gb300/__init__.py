@@ -333,10 +333,13 @@ def problem_structs(problem, nrhs: int = 1):
 
 
 class Server:
-    """One pcg_server_t: a served batch of mixed-precision solves."""
+    """One pcg_server_t: served solves, either batched line-preconditioned
+    mixed-precision solves (preconditioner="line") or multigrid-preconditioned
+    FP64 CG solves by a pool of worker threads (preconditioner="multigrid-f32")."""
 
     def __init__(self, budget_bytes: int, max_slots: int = 64, inner_tol: float = 0.0, inner_maxit: int = 0,
-                 max_outer: int = 0, epochs_per_launch: int = 0, stream: Optional[int] = None):
+                 max_outer: int = 0, epochs_per_launch: int = 0, stream: Optional[int] = None,
+                 preconditioner: str = "line"):
         self.lib = load_library()
         if stream is None:
             try:
@@ -344,8 +347,9 @@ class Server:
                 stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
             except Exception:
                 stream = 0
+        pc = {"line": PCG_PREC_LINE, "multigrid-f32": PCG_PREC_MULTIGRID_F32}[preconditioner]
         o = pcg_opts_t(PCG_MIXED, float(inner_tol), int(inner_maxit), int(max_outer), int(epochs_per_launch),
-                       ctypes.c_void_p(stream or 0))
+                       ctypes.c_void_p(stream or 0), pc)
         h = ctypes.c_void_p()
         rc = self.lib.pcg_server_create(ctypes.c_size_t(int(budget_bytes)), int(max_slots), ctypes.byref(o),
                                         ctypes.byref(h))

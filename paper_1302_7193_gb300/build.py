@@ -18,6 +18,7 @@ SOURCES = [os.path.join(HERE, "csrc", "pcg.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "kernels.cuh"), os.path.join(HERE, "csrc", "serve.cuh"),
                   os.path.join(HERE, "csrc", "multigrid.cuh"),
                   os.path.join(HERE, "csrc", "single_reduction.cuh"), os.path.join(HERE, "csrc", "serve_kernels.cuh"),
+                  os.path.join(HERE, "csrc", "serve_mg.cuh"),
                   os.path.join(ROOT, "include", "pcg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -40,7 +41,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     tmp = LIB + ".tmp"
-    cmd = [nvcc_path(), "-shared", "-Xcompiler", "-fPIC", *ARCH, "-O3", "-lineinfo", "-std=c++17",
+    cmd = [nvcc_path(), "-shared", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", *ARCH, "-O3", "-lineinfo", "-std=c++17",
            "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)

@@ -17,7 +17,10 @@
 // retires requests that converged (their x is copied out and their memory
 // returned) and admits waiting requests into the freed slots, so new
 // requests join the work of the ones already on the GPU.
+#include <condition_variable>
 #include <deque>
+#include <mutex>
+#include <thread>
 #include <type_traits>
 #include <unordered_map>
 
@@ -51,6 +54,7 @@ struct ServeReq {
     double bb = 0.0, last_rr = 0.0, floor_rel = 0.0;
     int sweeps = 0, inner_its = 0, status = PCG_NOT_CONVERGED, stag = 0;
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    pcg_stats_t mg_stats{};                  // multigrid mode: the solve's statistics
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
@@ -94,6 +98,14 @@ struct pcg_server {
     long long epochs = 0, launches = 0, retired = 0;
     int trace = 0;                      // PCG_TRACE=1: refinement history per request on stderr
     std::string err = "no error";
+    // multigrid mode (opts->preconditioner == PCG_PREC_MULTIGRID_F32, serve_mg.cuh): worker threads
+    int mode = 0;                       // 0: batched line-preconditioned mixed solves; 1: multigrid workers
+    int device = 0;
+    std::vector<std::thread> workers;
+    std::mutex mu;                      // mode 1: guards pending, reqs, the requests' phases, used, busy
+    std::condition_variable cv_work, cv_done;
+    bool stopping = false;
+    int busy = 0;                       // mode 1: requests being solved
 };
 
 namespace {
@@ -430,6 +442,8 @@ int capture_epochs(pcg_server_t s) {
 
 }  // namespace
 
+#include "serve_mg.cuh"
+
 extern "C" {
 
 int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts, pcg_server_t* out) {
@@ -455,12 +469,31 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
         pcg_server_destroy(s);
         return rc;
     };
-    s->slot_req.assign(max_slots, nullptr);
-    s->h_slots.assign(max_slots, pcg::ServeSlot{});
-    s->items_cap = 1 << 21;
     cudaError_t e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) { s->err = cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
+    s->device = dev;
+    const int pc = opts ? opts->preconditioner : PCG_PREC_LINE;
+    if (pc != PCG_PREC_LINE && pc != PCG_PREC_MULTIGRID_F32) {
+        s->err = "served solves take the line preconditioner or PCG_PREC_MULTIGRID_F32";
+        return bail(PCG_ERR_INVALID_ARG);
+    }
+    if (pc == PCG_PREC_MULTIGRID_F32) {
+        // multigrid mode: up to 16 requests solved at once, one worker thread and stream each
+        s->mode = 1;
+        const int nw = std::min(max_slots, 16);
+        try {
+            for (int i = 0; i < nw; ++i) s->workers.emplace_back(mg_worker, s);
+        } catch (...) {
+            s->err = "could not start the worker threads";
+            return bail(PCG_ERR_OOM);
+        }
+        *out = s;
+        return PCG_OK;
+    }
+    s->slot_req.assign(max_slots, nullptr);
+    s->h_slots.assign(max_slots, pcg::ServeSlot{});
+    s->items_cap = 1 << 21;
     if ((e = cudaDeviceGetDefaultMemPool(&s->pool, dev)) != cudaSuccess) { s->err = cudaGetErrorString(e); return bail(PCG_ERR_CUDA); }
     if ((e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
         s->err = cudaGetErrorString(e);
@@ -541,11 +574,10 @@ int pcg_serve_submit(pcg_server_t s, const pcg_grid_t* grid, const pcg_coeffs_t*
         if (rc) return sfail(s, rc, err);
     }
     const int cls_mode = serve_cls_mode(*grid, coeffs->alpha_e || coeffs->alpha_n);
-    const size_t need = request_bytes(*grid, cls_mode);
+    const size_t need = s->mode == 1 ? mg_request_bytes(*grid) : request_bytes(*grid, cls_mode);
     if (need > s->budget) return sfail(s, PCG_ERR_OOM, "request needs more device memory than the server's budget");
     ServeReq* q = new (std::nothrow) ServeReq();
     if (!q) return sfail(s, PCG_ERR_OOM, "host allocation failed");
-    q->id = s->next_id++;
     q->grid = *grid;
     const size_t nz = grid->n_z, nxy = (size_t)grid->n_x * grid->n_y;
     q->z_iface.assign(grid->z_iface, grid->z_iface + nz + 1);
@@ -556,6 +588,18 @@ int pcg_serve_submit(pcg_server_t s, const pcg_grid_t* grid, const pcg_coeffs_t*
     q->b.assign(b_host, b_host + nxy * nz);
     q->tol = tol;
     q->t_submit = now_ms();
+    if (s->mode == 1) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            q->id = s->next_id++;
+            s->pending.push_back(q);
+            s->reqs[q->id] = q;
+        }
+        s->cv_work.notify_all();
+        *req_id = q->id;
+        return PCG_OK;
+    }
+    q->id = s->next_id++;
     s->pending.push_back(q);
     s->reqs[q->id] = q;
     *req_id = q->id;
@@ -564,6 +608,15 @@ int pcg_serve_submit(pcg_server_t s, const pcg_grid_t* grid, const pcg_coeffs_t*
 
 int pcg_serve_step(pcg_server_t s, int max_epochs, int* n_active, int* n_pending) {
     if (!s) return sfail(nullptr, PCG_ERR_INVALID_ARG, "server is NULL");
+    if (s->mode == 1) {
+        // the workers advance on their own: wait (at most a millisecond) for one to finish a request
+        std::unique_lock<std::mutex> lk(s->mu);
+        const long long before = s->retired;
+        s->cv_done.wait_for(lk, std::chrono::milliseconds(1), [&] { return s->retired != before; });
+        if (n_active) *n_active = s->busy;
+        if (n_pending) *n_pending = (int)s->pending.size();
+        return PCG_OK;
+    }
     if (!s->graph) {
         int rc = capture_epochs(s);
         if (rc) return rc;
@@ -637,6 +690,22 @@ int pcg_serve_step(pcg_server_t s, int max_epochs, int* n_active, int* n_pending
 
 int pcg_serve_poll(pcg_server_t s, uint64_t req_id, double* x_host, pcg_stats_t* stats) {
     if (!s) return sfail(nullptr, PCG_ERR_INVALID_ARG, "server is NULL");
+    if (s->mode == 1) {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(req_id);
+        if (it == s->reqs.end()) return sfail(s, PCG_ERR_INVALID_ARG, "unknown request id");
+        ServeReq* q = it->second;
+        if (q->phase != RQ_DONE) return PCG_PENDING;
+        s->reqs.erase(it);
+        lk.unlock();
+        if (x_host && !q->x.empty()) std::memcpy(x_host, q->x.data(), q->x.size() * sizeof(double));
+        if (stats) {
+            *stats = q->mg_stats;
+            stats->elapsed_ms = q->t_done - q->t_submit;
+        }
+        delete q;
+        return PCG_OK;
+    }
     auto it = s->reqs.find(req_id);
     if (it == s->reqs.end()) return sfail(s, PCG_ERR_INVALID_ARG, "unknown request id");
     ServeReq* q = it->second;
@@ -661,6 +730,14 @@ int pcg_serve_poll(pcg_server_t s, uint64_t req_id, double* x_host, pcg_stats_t*
 
 int pcg_serve_info(pcg_server_t s, int* n_active, int* n_pending, size_t* used_bytes, long long* epochs) {
     if (!s) return sfail(nullptr, PCG_ERR_INVALID_ARG, "server is NULL");
+    if (s->mode == 1) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (n_active) *n_active = s->busy;
+        if (n_pending) *n_pending = (int)s->pending.size();
+        if (used_bytes) *used_bytes = s->used;
+        if (epochs) *epochs = 0;
+        return PCG_OK;
+    }
     int act = 0;
     for (ServeReq* q : s->slot_req) if (q) ++act;
     if (n_active) *n_active = act;
@@ -674,6 +751,17 @@ const char* pcg_server_last_error(pcg_server_t s) { return s ? s->err.c_str() : 
 
 void pcg_server_destroy(pcg_server_t s) {
     if (!s) return;
+    if (s->mode == 1) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stopping = true;
+        }
+        s->cv_work.notify_all();
+        for (auto& t : s->workers) t.join();   // a worker finishes the request it is solving first
+        for (auto& kv : s->reqs) delete kv.second;
+        delete s;
+        return;
+    }
     cudaStreamSynchronize(s->stream);
     for (auto& kv : s->reqs) {
         ServeReq* q = kv.second;

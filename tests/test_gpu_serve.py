@@ -11,6 +11,9 @@
 * Admission respects the device-byte budget; a request larger than the budget
   is refused at submission; a request with a non-finite right-hand side ends
   in breakdown without disturbing the others.
+* The multigrid mode (FP64 CG with the FP32 V-cycle, a worker pool) matches
+  the oracle, gives a request the same result alone and in a mix, keeps more
+  than one solve in flight and respects the budget.
 """
 import numpy as np
 import pytest
@@ -140,3 +143,72 @@ def test_every_preconditioner_path_in_one_mix(pkg):
             rid = srv.submit(*mix[k], tol=1e-10)
             x_alone, st_alone = _drain(srv, [rid])[rid]
         assert np.array_equal(x_alone, res[ids[k]][0]), probs[k].name
+
+
+# ---------------------------------------------------------------------------
+# Multigrid mode: each request solved by FP64 CG with the FP32 V-cycle, by a
+# pool of worker threads with a stream each.
+# ---------------------------------------------------------------------------
+
+def _mg_bytes(p):
+    return 96 * p.n_cells + (1 << 20)
+
+
+def test_multigrid_server_matches_oracle_and_alone(pkg):
+    # tol 1e-12 as the oracle's: at the mix's strongest anisotropy a stop at 1e-10
+    # leaves the near-constant mode about 1e-8 off
+    mix = _mix()
+    with pkg.Server(budget_bytes=1 << 30, max_slots=8, preconditioner="multigrid-f32") as srv:
+        ids = [srv.submit(q, bq, tol=1e-12) for q, bq in mix[:5]]
+        srv.step(8)
+        ids += [srv.submit(q, bq, tol=1e-12) for q, bq in mix[5:]]      # arrive while the others run
+        res = _drain(srv, list(ids))
+    for (p, b), rid in list(zip(mix, ids))[:4]:
+        x, st = res[rid]
+        assert st.status == 0 and 0 < st.iterations < 200, st
+        ref = pcg_interleaved(FluxOperator(p), LinePreconditioner(assemble_csr(p), p), b, eps=1e-12, maxiter=20000)
+        err = np.linalg.norm(x - ref.x.ravel()) / np.linalg.norm(ref.x)
+        assert err < 1e-8, (p.name, err)
+    probe = 3
+    with pkg.Server(budget_bytes=1 << 30, max_slots=1, preconditioner="multigrid-f32") as srv:
+        rid = srv.submit(*mix[probe], tol=1e-12)
+        x_alone, st_alone = _drain(srv, [rid])[rid]
+    assert st_alone.iterations == res[ids[probe]][1].iterations
+    assert np.array_equal(x_alone, res[ids[probe]][0])
+
+
+def test_multigrid_server_overlaps_and_bounds_admission(pkg):
+    p = W.box_problem(128, 128, 64, 0.002, lambda2=0.01)
+    per = _mg_bytes(p)
+    with pkg.Server(budget_bytes=int(2.5 * per), max_slots=16, preconditioner="multigrid-f32") as srv:
+        ids = [srv.submit(p, W.rhs_for(p, seed=s), tol=1e-8) for s in range(6)]
+        peak, out = 0, {}
+        for _ in range(100000):
+            for i in list(ids):
+                got = srv.poll(i, want_x=False)
+                if got is not None:
+                    out[i] = got
+                    ids.remove(i)
+            if not ids:
+                break
+            active, pending = srv.step(4)
+            peak = max(peak, active)
+            assert srv.info()["used_bytes"] <= 2.5 * per
+        assert not ids and peak == 2              # two solves in flight at once, never three
+        assert all(st.status == 0 for _, st in out.values())
+        # restarted until the true residual meets tol or twice its FP64 rounding floor
+        assert all(st.relres_true < 1e-8 or st.relres_true <= 2.0 * st.relres_floor for _, st in out.values())
+
+
+def test_multigrid_server_refuses_oversize_and_other_preconditioners(pkg):
+    with pkg.Server(budget_bytes=64 << 20, max_slots=4, preconditioner="multigrid-f32") as srv:
+        big = W.box_problem(256, 256, 64, 0.01)
+        with pytest.raises(pkg.PCGError) as e:
+            srv.submit(big, np.zeros(big.n_cells))
+        assert e.value.code == pkg.PCG_ERR_OOM
+    import ctypes
+    lib = pkg.load_library()
+    o = pkg.pcg_opts_t(pkg.PCG_MIXED, 0.0, 0, 0, 0, ctypes.c_void_p(0), pkg.PCG_PREC_MULTIGRID)
+    h = ctypes.c_void_p()
+    rc = lib.pcg_server_create(ctypes.c_size_t(1 << 30), 4, ctypes.byref(o), ctypes.byref(h))
+    assert rc == pkg.PCG_ERR_INVALID_ARG and not h.value
