@@ -233,26 +233,41 @@ int pcg_precond_noalloc(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, cons
 /* ---- served batch (continuous batching of many solves) ------------------ */
 
 /* Create a server that solves many independent problems of different grids,
- * coefficients and right-hand sides together in the mixed-precision form
- * (FP32 inner Algorithm 1 inside FP64 refinement, as pcg_solve with
- * PCG_MIXED).  budget_bytes bounds the device memory of admitted requests
- * (tables, FP64 x and b, five FP32 inner vectors; about 36 bytes per unknown);
- * max_slots bounds how many are admitted at once (<= 4096).  opts (may be
- * NULL): inner_tol, inner_maxit, max_outer as for pcg_create;
- * passes_per_launch = epochs per CUDA-graph launch (default 8); stream.
+ * coefficients and right-hand sides together.  budget_bytes bounds the
+ * device memory of admitted requests; max_slots bounds how many are admitted
+ * at once (<= 4096).  opts (may be NULL) selects one of two modes by
+ * opts->preconditioner:
+ *  - PCG_PREC_LINE (default): the mixed-precision form (FP32 inner
+ *    Algorithm 1 inside FP64 refinement, as pcg_solve with PCG_MIXED), the
+ *    inner iterations of all admitted requests advancing together in
+ *    persistent batched sweeps; about 36 bytes per unknown (tables, FP64 x
+ *    and b, five FP32 inner vectors).  inner_tol, inner_maxit, max_outer as
+ *    for pcg_create; passes_per_launch = epochs per CUDA-graph launch
+ *    (default 8); stream = the stream of the batched work.
+ *  - PCG_PREC_MULTIGRID_F32: FP64 CG preconditioned by the FP32 V-cycle (as
+ *    pcg_solve on a handle created with it), each request on a handle of its
+ *    own, solved by one of min(max_slots, 16) worker threads with a stream
+ *    each, so up to that many solves run at once and overlap on the device;
+ *    a solve is restarted from x until the true residual is below tol or
+ *    within twice the FP64 rounding floor (at most four solves;
+ *    stats.outer_sweeps counts them).  About 96 bytes per unknown.
+ * Other preconditioner values return PCG_ERR_INVALID_ARG.
  * Errors: PCG_ERR_INVALID_ARG, PCG_ERR_OOM, PCG_ERR_CUDA. */
 int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts, pcg_server_t* out);
 
 /* Queue one solve (nrhs must be 1).  grid, coeffs, b_host (n_z*n_y*n_x
  * values, layout as everywhere) are copied; tol as for pcg_solve with
- * PCG_MIXED.  The request is admitted by a later pcg_serve_step when a slot
- * and the byte budget allow (first in, first out).  A request larger than
+ * PCG_MIXED.  The request is admitted when a slot and the byte budget allow
+ * (first in, first out): by a later pcg_serve_step in the batched mode, by a
+ * free worker in the multigrid mode.  A request larger than
  * the whole budget fails here with PCG_ERR_OOM; invalid geometry with
  * PCG_ERR_INVALID_ARG.  *req_id identifies the request. */
 int pcg_serve_submit(pcg_server_t s, const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const double* b_host,
                      double tol, uint64_t* req_id);
 
-/* Advance the served batch: admit waiting requests, run the FP64
+/* Multigrid mode: the workers advance on their own; pcg_serve_step waits
+ * at most a millisecond for a request to finish and reports the counts.
+ * Batched mode: advance the served batch: admit waiting requests, run the FP64
  * refinement steps that are due, and run inner PCG epochs (one epoch = one
  * pass of Algorithm 1 for every request in its inner phase, executed by
  * persistent kernels over the work list of (request, 32x4-column tile)
@@ -276,7 +291,8 @@ int pcg_serve_info(pcg_server_t s, int* n_active, int* n_pending, size_t* used_b
  * pcg_server_create on this thread when s is NULL). */
 const char* pcg_server_last_error(pcg_server_t s);
 
-/* Free all device and host memory of the server, finished or not. */
+/* Free all device and host memory of the server, finished or not (in the
+ * multigrid mode after the solves in flight have finished). */
 void pcg_server_destroy(pcg_server_t s);
 
 /* Block the host until all work enqueued on the handle's stream is done. */
