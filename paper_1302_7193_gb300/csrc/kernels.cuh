@@ -817,6 +817,16 @@ __device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col
         }
     }
     const T e_in = (act && k0 > 0) ? ldro(fe - fs) * ldro(fg - fs) : T(0);
+    // ZMODE 2 updates z in place: its old values are read with the chunk's
+    // other loads (the thread owns them), not one by one after each store
+    T zo[ZMODE == 2 ? LZ : 1];
+    if constexpr (ZMODE == 2) {
+        if (act) {
+#pragma unroll
+            for (int t = 0; t < LZ; ++t)
+                if (t < kn) zo[t] = zb[t * pl];
+        }
+    }
     // updated residual, ||r||^2, local forward sweep with zero carry-in.
     // ||r||^2 and kappa are sums of non-negative terms: each chunk sums its
     // LZ terms directly (relative error <= (LZ - 1) u) and adds the chunk sum
@@ -890,7 +900,7 @@ __device__ __forceinline__ void prec_chunked_body(const OpView<T>& op, const Col
                 const T m = fma(-dp, Z, yv[t]) + Z;
                 if constexpr (ZMODE == 0) zb[t * pl] = m;
                 else if constexpr (ZMODE == 1) zb[t * pl] = omega * m;
-                else zb[t * pl] = fma(omega, m, zb[t * pl]);
+                else zb[t * pl] = fma(omega, m, zo[t]);
             }
         }
     }

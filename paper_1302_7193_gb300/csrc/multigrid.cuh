@@ -348,18 +348,25 @@ __global__ void k_mg_convert(const TA* __restrict__ a, TB* __restrict__ b, long 
     for_each_elem(vol, nrhs, st, [&](long long c, int) { b[c] = (TB)a[c]; });
 }
 
-// r <- r - alpha q (Algorithm 1 line 2, the preconditioner itself applied separately)
-__global__ void k_mg_rupdate(double* __restrict__ r, const double* __restrict__ q, long long vol, int nrhs,
-                             const SolveState* __restrict__ st) {
-    for_each_elem(vol, nrhs, st, [&](long long c, int rhs) { r[c] = fma(-st[rhs].alpha, q[c], r[c]); });
+// r <- r - alpha q (Algorithm 1 line 2, the preconditioner itself applied
+// separately); rf, if not null, receives r rounded to FP32 (the input of an
+// FP32 V-cycle).
+__global__ void k_mg_rupdate(double* __restrict__ r, const double* __restrict__ q, float* __restrict__ rf,
+                             long long vol, int nrhs, const SolveState* __restrict__ st) {
+    for_each_elem(vol, nrhs, st, [&](long long c, int rhs) {
+        const double v = fma(-st[rhs].alpha, q[c], r[c]);
+        r[c] = v;
+        if (rf) rf[c] = (float)v;
+    });
 }
 
 // <r, r> and <r, z> of every right-hand side; the last block applies the
 // stopping test and forms beta (Algorithm 1 lines 3-4, as k_sweep_prec).
+// With zf (an FP32 V-cycle's output) z is first widened from it and stored.
 __global__ __launch_bounds__(NT) void k_mg_dots(OpView<double> op, const double* __restrict__ r,
-                                                const double* __restrict__ z, SolveState* __restrict__ states,
-                                                double* __restrict__ partials, unsigned* __restrict__ counters,
-                                                int nblocks) {
+                                                double* __restrict__ z, const float* __restrict__ zf,
+                                                SolveState* __restrict__ states, double* __restrict__ partials,
+                                                unsigned* __restrict__ counters, int nblocks) {
     const int rhs = blockIdx.z;
     SolveState* st = states + rhs;
     if (st->done) return;
@@ -370,13 +377,260 @@ __global__ __launch_bounds__(NT) void k_mg_dots(OpView<double> op, const double*
         for (int k = 0; k < op.nz; ++k) {
             const long long o = base + (long long)k * op.plane;
             const double rk = r[o];
+            double zk;
+            if (zf) {
+                zk = (double)zf[o];
+                z[o] = zk;
+            } else {
+                zk = z[o];
+            }
             acc[0].add_prod(rk, rk);
-            acc[1].add_prod(rk, z[o]);
+            acc[1].add_prod(rk, zk);
         }
     }
     double v[2];
     if (grid_sum_acc<2>(acc, partials + (long long)rhs * nblocks * 2, counters + rhs, nblocks, bid2(), v))
         prec_epilogue(st, v[0], v[1]);
+}
+
+// ---------------------------------------------------------------------------
+// The coarse end of the V-cycle in one launch.
+//
+// On the smallest levels every step of the cycle is a short chain of
+// dependent work on a few thousand cells, and a launch per step costs
+// several microseconds of fill, first loads and drain whatever the level's
+// size.  k_mg_tail runs the levels lt .. L-1 -- the downward smoothing and
+// restriction, the coarsest level, the prolongation and the upward smoothing
+// back to lt -- in one thread block per right-hand side, with the levels'
+// vectors held in shared memory (r and z of every level, one residual
+// scratch of the largest) and a block barrier between dependent steps.  It
+// reads r of level lt from global memory at the start and writes z of level
+// lt back at the end.  Every step does the arithmetic of the kernel it
+// replaces in the same order (the chunked line solve of k_mg_lsolve_chunked,
+// the flux-form residual of k_mg_resid, the four-cell sums of k_mg_restrict
+// and k_mg_prolong), so the cycle's result does not depend on where the
+// tail starts.
+// ---------------------------------------------------------------------------
+constexpr int TAIL_MAXL = 8;
+constexpr int TAIL_WARPS = 8;   // 256 threads: the chunked line solve's registers
+
+template <typename T>
+struct TailArgs {
+    OpView<T> op[TAIL_MAXL];          // levels lt .. L-1
+    long long off_r[TAIL_MAXL];       // r of each level in the dynamic shared memory (elements)
+    long long off_z[TAIL_MAXL];       // z of each level
+    long long off_t;                  // residual scratch (the largest level's size)
+    const T* r_in;                    // r of level lt in global memory (right-hand side k at + k vol)
+    T* z_out;                         // z of level lt in global memory
+    int nlev;
+    int nu;                           // smoothing sweeps before and after the coarse correction
+    int ncoarse;                      // sweeps on a coarsest level of more than one column
+    T omega;
+};
+
+// A z at level k of one column, zl = z at level k: the expression of
+// k_mg_resid, fprev the vertical flux from below (0 at k = 0), replaced by
+// the flux to level k + 1.
+template <typename T>
+__device__ __forceinline__ T tail_az(const OpView<T>& op, const Col<T>& col, const T* zl, int k, T& fprev) {
+    const int pl = (int)op.plane;
+    const T zc = zl[col.c];
+    const T zu = k + 1 < op.nz ? zl[pl + col.c] : zc;
+    const T f = ldro(op.wv + k) * (zc - zu);
+    T h = col.me * (zc - zl[col.ce]);
+    h = fma(col.mw, zc - zl[col.cw], h);
+    h = fma(col.mn, zc - zl[col.cn], h);
+    h = fma(col.ms, zc - zl[col.cs], h);
+    const T az = fma(ldro(op.dk + k), h, col.area * fma(ldro(op.mass + k), zc, f - fprev));
+    fprev = f;
+    return az;
+}
+
+// The flux into level k0 of a column from below, as k_mg_resid starts a part.
+template <typename T>
+__device__ __forceinline__ T tail_flux_below(const OpView<T>& op, const Col<T>& col, const T* z, int k0) {
+    const int pl = (int)op.plane;
+    return k0 > 0 ? ldro(op.wv + k0 - 1) * (z[(k0 - 1) * pl + col.c] - z[k0 * pl + col.c]) : T(0);
+}
+
+// The cell loops of the tail deal (column, level range) units over the
+// block: a column's levels are split into parts so that small levels still
+// give every thread work; a thread builds its column's geometry once and
+// walks the levels of its part.
+struct TailUnits {
+    int ncols, nz, parts, units;
+    __device__ __forceinline__ TailUnits(int ncols_, int nz_) : ncols(ncols_), nz(nz_) {
+        parts = max(1, min(nz, (TAIL_WARPS * 32) / ncols));
+        units = ncols * parts;
+    }
+    __device__ __forceinline__ void unit(int u, int& c, int& k0, int& k1) const {
+        const int part = u / ncols;
+        c = u - part * ncols;
+        k0 = part * nz / parts;
+        k1 = (part + 1) * nz / parts;
+    }
+};
+
+// Each kind of step below is one out-of-line function, called for every
+// level: the cycle runs each step only a few times, and inlined copies at
+// every call site would be fetched from beyond the instruction cache each
+// time.  The level's view is passed by value (its table pointers cannot
+// alias the step's stores).
+
+// z = (ZMODE 2 ? z : 0) + om M^{-1} rin on one level: rows of 32 consecutive
+// columns (flattened j n_x + i), each row taken by a group of nch warps (one
+// per 16-level chunk), the rows dealt round-robin over the block's groups.
+// Warps outside a group join the block barriers only.
+template <typename T, int ZMODE>
+__device__ __noinline__ void tail_smooth(const OpView<T> op, const T* rin, T* z, T om, T (*sh_y)[32],
+                                         T (*sh_c)[32], T (*sh_z)[32], T (*sh_d)[32]) {
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int nch = (op.nz + 15) / 16;
+    const int G = TAIL_WARPS / nch;
+    const bool in_grp = warp < G * nch;
+    const int grp = in_grp ? warp / nch : 0;
+    const int ch = in_grp ? warp - grp * nch : 0;
+    const int w0 = in_grp ? grp * nch : warp;
+    const int nch_c = in_grp ? nch : 1;
+    const int ncols = (int)op.plane, nrow = (ncols + 31) / 32;
+    const int rounds = (nrow + G - 1) / G;
+    for (int rd = 0; rd < rounds; ++rd) {
+        const int f = (rd * G + grp) * 32 + lane;
+        int i = op.nx, j = 0;   // no column
+        if (in_grp && f < ncols) {
+            j = f / op.nx;
+            i = f - j * op.nx;
+        }
+        const Col<T> col = make_col(op, i, j);
+        Acc<T> sums[2];
+        prec_chunked_body<T, 16, false, ZMODE>(op, col, lane, ch, nch_c, w0, const_cast<T*>(rin), rin, z, T(0), sums,
+                                               sh_y, sh_c, sh_z, sh_d, nullptr, nullptr, 0, om);
+    }
+}
+
+template <typename T>
+__device__ __noinline__ void tail_resid(const OpView<T> op, const T* r, const T* z, T* t) {
+    const TailUnits tu((int)op.plane, op.nz);
+    const int pl = (int)op.plane;
+    for (int u = threadIdx.y * 32 + threadIdx.x; u < tu.units; u += TAIL_WARPS * 32) {
+        int c, k0, k1;
+        tu.unit(u, c, k0, k1);
+        const int j = c / op.nx;
+        const Col<T> col = make_col(op, c - j * op.nx, j);
+        T fprev = tail_flux_below(op, col, z, k0);
+        for (int k = k0; k < k1; ++k) {
+            const T az = tail_az(op, col, z + k * pl, k, fprev);
+            t[k * pl + c] = r[k * pl + c] - az;
+        }
+    }
+}
+
+// rc = R (r - A z): the four fine residuals of a coarse cell summed in the
+// order of k_mg_restrict.
+template <typename T>
+__device__ __noinline__ void tail_resid_restrict(const OpView<T> op, const T* r, const T* z, T* rc) {
+    const int nxc = op.nx / 2, pl = (int)op.plane, plc = pl / 4;
+    const TailUnits tu(plc, op.nz);
+    for (int u = threadIdx.y * 32 + threadIdx.x; u < tu.units; u += TAIL_WARPS * 32) {
+        int cc, k0, k1;
+        tu.unit(u, cc, k0, k1);
+        const int jc = cc / nxc, ic = cc - jc * nxc;
+        const Col<T> c00 = make_col(op, 2 * ic, 2 * jc), c01 = make_col(op, 2 * ic + 1, 2 * jc);
+        const Col<T> c10 = make_col(op, 2 * ic, 2 * jc + 1), c11 = make_col(op, 2 * ic + 1, 2 * jc + 1);
+        T f00 = tail_flux_below(op, c00, z, k0), f01 = tail_flux_below(op, c01, z, k0);
+        T f10 = tail_flux_below(op, c10, z, k0), f11 = tail_flux_below(op, c11, z, k0);
+        for (int k = k0; k < k1; ++k) {
+            const T* zl = z + k * pl;
+            const T* rl = r + k * pl;
+            const T t00 = rl[c00.c] - tail_az(op, c00, zl, k, f00);
+            const T t01 = rl[c01.c] - tail_az(op, c01, zl, k, f01);
+            const T t10 = rl[c10.c] - tail_az(op, c10, zl, k, f10);
+            const T t11 = rl[c11.c] - tail_az(op, c11, zl, k, f11);
+            rc[k * plc + cc] = ((t00 + t01) + t10) + t11;
+        }
+    }
+}
+
+// zf += P zc
+template <typename T>
+__device__ __noinline__ void tail_prolong(const OpView<T> op, const T* zc, T* zf) {
+    const int nxc = op.nx / 2, pl = (int)op.plane, plc = pl / 4;
+    const TailUnits tu(pl, op.nz);
+    for (int u = threadIdx.y * 32 + threadIdx.x; u < tu.units; u += TAIL_WARPS * 32) {
+        int c, k0, k1;
+        tu.unit(u, c, k0, k1);
+        const int j = c / op.nx, i = c - j * op.nx;
+        const int cc = (j >> 1) * nxc + (i >> 1);
+        for (int k = k0; k < k1; ++k) zf[k * pl + c] += zc[k * plc + cc];
+    }
+}
+
+// Grid (nrhs), block (32, TAIL_WARPS), dynamic shared memory as laid out in
+// a.off_*.  The sequence of steps is that of the launches it replaces.
+template <typename T>
+__global__ __launch_bounds__(TAIL_WARPS * 32) void k_mg_tail(const __grid_constant__ TailArgs<T> a,
+                                                            const SolveState* __restrict__ st) {
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    __shared__ T sh_y[TAIL_WARPS][32], sh_c[TAIL_WARPS][32], sh_z[TAIL_WARPS][32], sh_d[TAIL_WARPS][32];
+    const int rhs = blockIdx.x;
+    if (st[rhs].done) return;
+    T* sm = reinterpret_cast<T*>(tail_smem);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int c = a.nlev - 1;
+    T* const tt = sm + a.off_t;
+    auto R = [&](int l) { return sm + a.off_r[l]; };
+    auto Z = [&](int l) { return sm + a.off_z[l]; };
+    auto smooth = [&](int l, const T* rin, T om, bool acc) {   // z = (acc ? z : 0) + om M^{-1} rin
+        const OpView<T> op = a.op[l];
+        if (acc)
+            tail_smooth<T, 2>(op, rin, Z(l), om, sh_y, sh_c, sh_z, sh_d);
+        else
+            tail_smooth<T, 1>(op, rin, Z(l), om, sh_y, sh_c, sh_z, sh_d);
+        __syncthreads();
+    };
+    auto resid = [&](int l) {                                  // t = r - A z
+        const OpView<T> op = a.op[l];
+        tail_resid(op, R(l), Z(l), tt);
+        __syncthreads();
+    };
+    auto smooth_more = [&](int l) {                            // z += omega M^{-1} (r - A z)
+        resid(l);
+        smooth(l, tt, a.omega, true);
+    };
+    {
+        const int v0 = (int)a.op[0].vol;
+        const T* src = a.r_in + (long long)rhs * v0;
+        T* dst = R(0);
+        for (int u = tid; u < v0; u += TAIL_WARPS * 32) dst[u] = ldro(src + u);
+        __syncthreads();
+    }
+    for (int l = 0; l < c; ++l) {
+        smooth(l, R(l), a.omega, false);
+        for (int k = 1; k < a.nu; ++k) smooth_more(l);
+        const OpView<T> op = a.op[l];
+        tail_resid_restrict(op, R(l), Z(l), R(l + 1));
+        __syncthreads();
+    }
+    if (a.op[c].plane == 1) {   // one column: its block solve with one refinement step
+        smooth(c, R(c), T(1), false);
+        resid(c);
+        smooth(c, tt, T(1), true);
+    } else {
+        smooth(c, R(c), a.omega, false);
+        for (int k = 1; k < a.ncoarse; ++k) smooth_more(c);
+    }
+    for (int l = c - 1; l >= 0; --l) {
+        const OpView<T> op = a.op[l];
+        tail_prolong(op, Z(l + 1), Z(l));
+        __syncthreads();
+        for (int k = 0; k < a.nu; ++k) smooth_more(l);
+    }
+    {
+        const int v0 = (int)a.op[0].vol;
+        T* dst = a.z_out + (long long)rhs * v0;
+        const T* src = Z(0);
+        for (int u = tid; u < v0; u += TAIL_WARPS * 32) dst[u] = src[u];
+    }
 }
 
 }  // namespace pcg

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -128,6 +129,8 @@ struct pcg_ctx {
     long long mg_few = 0;                 // chunked line solve below this many columns (0: by precision)
     int mg_resid_pb = 0;                  // k_mg_resid prefetch depth, 1, 2 or 4 levels (0: by precision)
     int mg_fuse = 1;                      // downward residual and restriction in one kernel
+    long long mg_tail_cols = 4096;        // levels of at most this many columns may run in k_mg_tail (0: none)
+    long long mg_tail_smem = 200 * 1024;  // dynamic shared memory k_mg_tail may use for the levels' vectors
     // PCG_ALG_SINGLE_REDUCTION: one k_sweep_sr per pass; r, s (q64), w double-buffered
     bool alg_sr = false;
     dim3 grid_sr;
@@ -728,9 +731,13 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
     int n = 0;
     // Each column's work is spread over several threads where a level has too
     // few columns to keep the SMs' loads in flight: the residual over level
-    // chunks (parts of a column), and, below a column count, the line solve in
-    // its chunked form (one warp per 16 levels) with the damped update as its store.
-    const long long few_cols = h->mg_few > 0 ? h->mg_few : (sizeof(V) == 4 ? 32768 : 16384);
+    // chunks (parts of a column), and the line solve in its chunked form (one
+    // warp per 16 levels) with the damped update as its store.  In FP32 the
+    // chunked form is the faster one on every level (it keeps more loads in
+    // flight and has no y round trip through memory); in FP64, bound by the
+    // FP64 pipe, its extra arithmetic makes it slower on large levels.
+    const long long few_cols =
+        h->mg_few > 0 ? h->mg_few : (sizeof(V) == 4 ? std::numeric_limits<long long>::max() : 16384);
     auto few = [&](pcg_t hl) { return hl->plane * (long long)hl->nrhs < few_cols && hl->nz <= 128; };
     auto ksplit = [&](pcg_t hl) {
         int ks = 1;
@@ -769,7 +776,21 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
         resid(l);
         smooth(l, T(l), omega, 1);
     };
-    for (int l = 0; l + 1 < L; ++l) {
+    // Levels lt .. L-1 (at most mg_tail_cols columns each, all solved in the
+    // chunked form, their r and z and one residual scratch within
+    // mg_tail_smem bytes) run in one k_mg_tail launch; lt = L: none.
+    int lt = L;
+    if (h->mg_tail_cols > 0 && h->nrhs <= 65535)
+        for (int l = L - 1; l >= 0 && L - l <= pcg::TAIL_MAXL; --l) {
+            pcg_t hl = H(l);
+            if (hl->plane > h->mg_tail_cols || !few(hl)) break;
+            long long elems = 0;
+            for (int m = l; m < L; ++m) elems += 2 * ((H(m)->vol + 3) / 4 * 4);
+            elems += (hl->vol + 3) / 4 * 4;
+            if (elems * (long long)sizeof(V) > h->mg_tail_smem) break;
+            lt = l;
+        }
+    for (int l = 0; l + 1 < L && l < lt; ++l) {
         smooth_first(l, omega);
         for (int k = 1; k < h->mg_nu; ++k) smooth_more(l);
         pcg_t hl = H(l), hc = H(l + 1);
@@ -793,7 +814,27 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
         ++n;
     }
     const int c = L - 1;
-    if (H(c)->plane == 1) {
+    if (lt < L) {
+        pcg::TailArgs<V> a{};
+        a.nlev = L - lt;
+        a.nu = h->mg_nu;
+        a.ncoarse = h->mg_coarse;
+        a.omega = omega;
+        a.r_in = R(lt);
+        a.z_out = Z(lt);
+        long long off = 0;
+        for (int l = lt; l < L; ++l) {
+            a.op[l - lt] = level_view<V>(H(l));
+            a.off_r[l - lt] = off;
+            off += (H(l)->vol + 3) / 4 * 4;
+            a.off_z[l - lt] = off;
+            off += (H(l)->vol + 3) / 4 * 4;
+        }
+        a.off_t = off;
+        off += (H(lt)->vol + 3) / 4 * 4;
+        pcg::k_mg_tail<V><<<dim3((unsigned)h->nrhs), dim3(32, pcg::TAIL_WARPS), (size_t)off * sizeof(V), s>>>(a, st);
+        ++n;
+    } else if (H(c)->plane == 1) {
         // one column: its block is all of A, solved with one step of
         // refinement (z += M^{-1} (r - A z)): without horizontal couplings the
         // block's condition number reaches 1e10 at strong anisotropy
@@ -804,7 +845,7 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
         smooth_first(c, omega);
         for (int k = 1; k < h->mg_coarse; ++k) smooth_more(c);
     }
-    for (int l = L - 2; l >= 0; --l) {
+    for (int l = std::min(L - 2, lt - 1); l >= 0; --l) {
         pcg_t hl = H(l);
         const CellLaunch cl = cell_launch(hl->nx, hl->ny, hl->nz, hl->nrhs);
         pcg::k_mg_prolong<V><<<cl.g, cl.b, 0, s>>>(Z(l + 1), Z(l), hl->nx, hl->ny, hl->nz, hl->nrhs, cl.nbi, st);
@@ -813,6 +854,21 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
     }
     return n;
 }
+
+// Opt k_mg_tail in to the shared memory its levels need (the block's
+// static arrays come on top); on failure the coarse levels run as separate
+// launches.
+template <typename V>
+bool tail_smem_ok(pcg_t h) {
+    if (cudaFuncSetAttribute(pcg::k_mg_tail<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->mg_tail_smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+bool tail_ready(pcg_t h) { return h->mg_f32 ? tail_smem_ok<float>(h) : tail_smem_ok<double>(h); }
 
 // Levels of the multigrid hierarchy: n_x, n_y halved while both are even
 // (down to one column), each level a handle of its own on the coarser grid
@@ -876,17 +932,16 @@ int build_hierarchy(pcg_t h, const pcg_grid_t* grid, const pcg_coeffs_t* coeffs)
 // z = B r; <r, r>, <r, z>, stopping test, beta; then the SpMV sweep.
 int launch_mg_pass(pcg_t h, cudaStream_t s) {
     const dim3 g = elem_grid(h->vol, h->nrhs);
-    pcg::k_mg_rupdate<<<g, 256, 0, s>>>(h->r64, h->q64, h->vol, h->nrhs, h->st);
+    // an FP32 cycle takes r rounded as it is updated, and its z is widened
+    // as the dot products read it
+    pcg::k_mg_rupdate<<<g, 256, 0, s>>>(h->r64, h->q64, h->mg_f32 ? h->mg_r0f : nullptr, h->vol, h->nrhs, h->st);
     int n = 1;
-    if (h->mg_f32) {
-        pcg::k_mg_convert<double, float><<<g, 256, 0, s>>>(h->r64, h->mg_r0f, h->vol, h->nrhs, h->st);
-        n += 2 + launch_vcycle<float>(h, s, h->st, h->mg_r0f, h->mg_z0f, h->mg_t0f);
-        pcg::k_mg_convert<float, double><<<g, 256, 0, s>>>(h->mg_z0f, h->z64, h->vol, h->nrhs, h->st);
-    } else {
+    if (h->mg_f32)
+        n += launch_vcycle<float>(h, s, h->st, h->mg_r0f, h->mg_z0f, h->mg_t0f);
+    else
         n += launch_vcycle<double>(h, s, h->st, h->r64, h->z64, h->mg_t0);
-    }
-    pcg::k_mg_dots<<<h->grid_c, h->block_c, 0, s>>>(h->view64(), h->r64, h->z64, h->st, h->partials, h->counters,
-                                                    h->nblk_c);
+    pcg::k_mg_dots<<<h->grid_c, h->block_c, 0, s>>>(h->view64(), h->r64, h->z64, h->mg_f32 ? h->mg_z0f : nullptr,
+                                                    h->st, h->partials, h->counters, h->nblk_c);
     launch_spmv<double>(h, s, h->view64(), h->u64, h->p64, h->q64, h->z64, h->st);
     return n + 2;
 }
@@ -1234,6 +1289,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if (const char* e = std::getenv("PCG_MG_FEW")) h->mg_few = std::atoll(e);                        // experiments
     if (const char* e = std::getenv("PCG_MG_RESID_PB")) h->mg_resid_pb = std::atoi(e);                // experiments
     if (const char* e = std::getenv("PCG_MG_FUSE")) h->mg_fuse = std::atoi(e) ? 1 : 0;                 // experiments
+    if (const char* e = std::getenv("PCG_MG_TAIL")) h->mg_tail_cols = std::atoll(e);                  // 0: no k_mg_tail
     h->rhs_stats.assign(h->nrhs, pcg_stats_t{});
     if (const char* tr = std::getenv("PCG_TRACE")) h->trace = std::atoi(tr);
     h->block = dim3(BX, BY, 1);
@@ -1387,6 +1443,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if (e != cudaSuccess) { h->h_st = nullptr; h->err = "cudaMallocHost failed"; return bail(PCG_ERR_OOM); }
     if ((rc = upload_tables(h, t))) return bail(rc);
     if (h->precond == PCG_PREC_MULTIGRID && (rc = build_hierarchy(h, grid, coeffs))) return bail(rc);
+    if (h->precond == PCG_PREC_MULTIGRID && h->mg_tail_cols > 0 && !tail_ready(h)) h->mg_tail_cols = 0;
     *out = h;
     return PCG_OK;
 }

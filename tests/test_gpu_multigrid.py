@@ -160,3 +160,48 @@ def test_mg_f32_batch_equals_single_bitwise(torch_cuda):
             st = s1.solve(_dev(torch, bs[r]), x1, tol=1e-9, maxit=500)
             assert st.iterations == stats[r].iterations
             assert np.array_equal(x1.cpu().numpy().reshape(p.shape), xb[r])
+
+
+@pytest.mark.parametrize("prec", ["multigrid", "multigrid-f32"])
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_coarse_levels_in_one_launch_bitwise(torch_cuda, monkeypatch, name, p, prec):
+    """The smallest levels run in one launch (k_mg_tail) by
+    default; PCG_MG_TAIL=0 runs them as separate launches.  Both do the same
+    arithmetic in the same order, so the V-cycles and the CG iterates built
+    on them agree bit for bit, and the single launch makes fewer launches."""
+    import paper_1302_7193_gb300 as pkg
+    torch = torch_cuda
+    r = np.random.default_rng(7).uniform(-1, 1, p.shape)
+    b = W.rhs_for(p, seed=2)
+    out = {}
+    for tail in ("4096", "0"):
+        monkeypatch.setenv("PCG_MG_TAIL", tail)
+        with pkg.Solver(p, preconditioner=prec) as s:
+            z = torch.empty(p.n_cells, dtype=torch.float64, device="cuda")
+            s.precond(_dev(torch, r), z)
+            x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+            st = s.solve(_dev(torch, b), x, tol=0.0, maxit=6)
+            out[tail] = (z.cpu().numpy(), x.cpu().numpy(), st.iterations, s.kernel_launches)
+    (z1, x1, it1, n1), (z0, x0, it0, n0) = out["4096"], out["0"]
+    assert np.array_equal(z1, z0)
+    assert it1 == it0 == 6 and np.array_equal(x1, x0)
+    assert n1 < n0, (n1, n0)
+
+
+def test_coarse_levels_in_one_launch_batched(torch_cuda, monkeypatch):
+    """Three right-hand sides, one block each, one of them stopped early:
+    the batched FP32 cycle inside CG equals the separate launches bit for bit."""
+    import paper_1302_7193_gb300 as pkg
+    torch = torch_cuda
+    p = W.box_problem(32, 16, 12, 0.01)
+    bs = W.batched_rhs(p, [0, 5, 9])
+    bs[1] *= 1e-3
+    xs = {}
+    for tail in ("4096", "0"):
+        monkeypatch.setenv("PCG_MG_TAIL", tail)
+        with pkg.Solver(p, nrhs=3, preconditioner="multigrid-f32") as s:
+            xb = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
+            s.solve(_dev(torch, bs), xb, tol=1e-9, maxit=500)
+            xs[tail] = (xb.cpu().numpy(), [s.pcg_rhs_stats(k).iterations for k in range(3)])
+    assert xs["4096"][1] == xs["0"][1]
+    assert np.array_equal(xs["4096"][0], xs["0"][0])
