@@ -394,6 +394,175 @@ __global__ __launch_bounds__(NT) void k_mg_dots(OpView<double> op, const double*
 }
 
 // ---------------------------------------------------------------------------
+// FP32 residuals on levels whose rows split into quads (n_x % 4 == 0; n_y is
+// even on every level but the coarsest).  A thread takes the four cells
+// i0 .. i0+3 of both rows of a row pair (2 jp, 2 jp + 1): the pair's own z
+// rows are each other's north and south neighbours, the east and west
+// neighbours at a quad's edges come from the adjacent lanes by shuffles
+// (loads only at the ends of rows and warps), and z, r move as float4.  Each
+// cell's arithmetic is that of k_mg_resid, in the same order.
+//   MODE 0: t = r - A z
+//   MODE 1: rc = R (r - A z), the four fine residuals of a coarse cell summed
+//           in the order of k_mg_restrict (t is not stored)
+// Grid (ceil(units / 128), 1, nrhs * ksplit), units = (n_y / 2) (n_x / 4);
+// blockIdx.z = rhs * ksplit + part, part taking levels
+// [part n_z / ksplit, (part + 1) n_z / ksplit).
+// ---------------------------------------------------------------------------
+struct Quad8 {         // z and r of a row pair's two quads at one level
+    float4 z0, z1;     // rows 2 jp, 2 jp + 1
+    float4 zs, zn;     // the row below 2 jp, the row above 2 jp + 1
+    float4 r0, r1;
+    float e0, w0, e1, w1;   // edge neighbours where no lane holds them
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float q4(const float4& v, int m) {
+    return m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
+}
+
+template <int MODE>
+__global__ __launch_bounds__(128) void k_mg_resid4(OpView<float> op, const float* __restrict__ r,
+                                                   const float* __restrict__ z, float* __restrict__ out,
+                                                   const SolveState* __restrict__ st, int ksplit) {
+    const int rhs = blockIdx.z / ksplit;
+    const int part = blockIdx.z - rhs * ksplit;
+    if (st[rhs].done) return;   // the same for the whole block
+    const int lane = threadIdx.x & 31;
+    const int nx = op.nx, ny = op.ny, nz = op.nz, nq = nx / 4;
+    const int units = (ny / 2) * nq;
+    const int u = blockIdx.x * 128 + threadIdx.x;
+    const bool valid = u < units;   // invalid threads still join the shuffles
+    const int jp = valid ? u / nq : 0;
+    const int q = valid ? u - jp * nq : 0;
+    const int j0 = 2 * jp, j1 = j0 + 1, i0 = 4 * q;
+    const int js = j0 > 0 ? j0 - 1 : (op.periodic_y ? ny - 1 : 0);
+    const int jn = j1 + 1 < ny ? j1 + 1 : (op.periodic_y ? 0 : j1);
+    const int ie = i0 + 4 < nx ? i0 + 4 : 0, iw = i0 > 0 ? i0 - 1 : nx - 1;
+    const bool e_shfl = q + 1 < nq && lane < 31, w_shfl = q > 0 && lane > 0;
+    const long long pl = op.plane, c0 = (long long)j0 * nx + i0, c1 = c0 + nx;
+    const long long cs = (long long)js * nx + i0, cn = (long long)jn * nx + i0;
+    const int nxc = nx / 2;
+    const long long plc = pl / 4;
+    const long long base = (long long)rhs * op.vol;
+    const float* __restrict__ zb = z + base;
+    const float* __restrict__ rb = r + base;
+    const int k0 = (int)((long long)part * nz / ksplit), k1 = (int)((long long)(part + 1) * nz / ksplit);
+    auto zq = [&](int k, long long c) -> float4 { return ld4(zb + (long long)k * pl + c); };   // a quad of z
+    auto zpt = [&](int k, int j, int i) -> float { return __ldg(zb + (long long)k * pl + (long long)j * nx + i); };
+    // the level's loads; own = false: only the own rows (the level above a part)
+    auto fetch = [&](int k, Quad8& v, bool own) {
+        if (!valid) return;
+        v.z0 = zq(k, c0);
+        v.z1 = zq(k, c1);
+        if (own) return;
+        v.zs = zq(k, cs);
+        v.zn = zq(k, cn);
+        v.r0 = ld4(rb + (long long)k * pl + c0);
+        v.r1 = ld4(rb + (long long)k * pl + c1);
+        if (!e_shfl) {
+            v.e0 = zpt(k, j0, ie);
+            v.e1 = zpt(k, j1, ie);
+        }
+        if (!w_shfl) {
+            v.w0 = zpt(k, j0, iw);
+            v.w1 = zpt(k, j1, iw);
+        }
+    };
+    // face weights of the eight cells, as make_col forms them (scalar loads:
+    // the tables are not aligned for vector loads)
+    float me[2][4], mw[2][4], mn[2][4], ms[2][4], ar[2][4];
+    {
+        const long long cr[2] = {c0, c1};
+        const int jr[2] = {j0, j1};
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                me[h][m] = valid ? ldro(op.mue + cr[h] + m) : 0.f;
+                mn[h][m] = valid ? ldro(op.mun + cr[h] + m) : 0.f;
+                ar[h][m] = valid ? ldro(op.area + (op.area_percol ? cr[h] + m : (long long)jr[h])) : 0.f;
+            }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float wsh = __shfl_up_sync(0xffffffffu, me[h][3], 1);
+            mw[h][0] = w_shfl ? wsh : (valid ? ldro(op.mue + (long long)jr[h] * nx + iw) : 0.f);
+#pragma unroll
+            for (int m = 1; m < 4; ++m) mw[h][m] = me[h][m - 1];
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            ms[0][m] = (valid && (op.periodic_y || j0 > 0)) ? ldro(op.mun + cs + m) : 0.f;
+            ms[1][m] = mn[0][m];
+        }
+    }
+    Quad8 cur{}, nxt{}, nn{};
+    float fp[2][4];   // vertical flux from below, per cell
+    fetch(k0, cur, false);
+    if (k0 + 1 < nz) fetch(k0 + 1, nxt, k0 + 1 >= k1);
+    if (k0 > 0) {
+        Quad8 lo{};
+        fetch(k0 - 1, lo, true);
+        const float wlo = ldro(op.wv + k0 - 1);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            fp[0][m] = wlo * (q4(lo.z0, m) - q4(cur.z0, m));
+            fp[1][m] = wlo * (q4(lo.z1, m) - q4(cur.z1, m));
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) fp[0][m] = fp[1][m] = 0.f;
+    }
+    for (int k = k0; k < k1; ++k) {
+        if (k + 2 < nz && k + 2 <= k1) fetch(k + 2, nn, k + 2 >= k1);
+        const float wvk = ldro(op.wv + k), dkk = ldro(op.dk + k), mk = ldro(op.mass + k);
+        const bool top = k + 1 >= nz;
+        float t[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 zr = h == 0 ? cur.z0 : cur.z1;
+            const float4 zup = h == 0 ? nxt.z0 : nxt.z1;
+            const float4 zno = h == 0 ? cur.z1 : cur.zn;   // north row
+            const float4 zso = h == 0 ? cur.zs : cur.z0;   // south row
+            const float4 rr = h == 0 ? cur.r0 : cur.r1;
+            const float esh = __shfl_down_sync(0xffffffffu, zr.x, 1);
+            const float wsh = __shfl_up_sync(0xffffffffu, zr.w, 1);
+            const float E = e_shfl ? esh : (h == 0 ? cur.e0 : cur.e1);
+            const float Wv = w_shfl ? wsh : (h == 0 ? cur.w0 : cur.w1);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float zcv = q4(zr, m);
+                const float zu = top ? zcv : q4(zup, m);
+                const float ze = m < 3 ? q4(zr, m + 1) : E;
+                const float zw = m > 0 ? q4(zr, m - 1) : Wv;
+                const float f = wvk * (zcv - zu);
+                float hh = me[h][m] * (zcv - ze);
+                hh = fmaf(mw[h][m], zcv - zw, hh);
+                hh = fmaf(mn[h][m], zcv - q4(zno, m), hh);
+                hh = fmaf(ms[h][m], zcv - q4(zso, m), hh);
+                const float az = fmaf(dkk, hh, ar[h][m] * fmaf(mk, zcv, f - fp[h][m]));
+                t[h][m] = q4(rr, m) - az;
+                fp[h][m] = f;
+            }
+        }
+        if (valid) {
+            if constexpr (MODE == 1) {
+                float2 v;
+                v.x = ((t[0][0] + t[0][1]) + t[1][0]) + t[1][1];
+                v.y = ((t[0][2] + t[0][3]) + t[1][2]) + t[1][3];
+                *reinterpret_cast<float2*>(out + (long long)rhs * (op.vol / 4) + (long long)k * plc +
+                                           (long long)jp * nxc + 2 * q) = v;
+            } else {
+                float* ob = out + base + (long long)k * pl;
+                *reinterpret_cast<float4*>(ob + c0) = make_float4(t[0][0], t[0][1], t[0][2], t[0][3]);
+                *reinterpret_cast<float4*>(ob + c1) = make_float4(t[1][0], t[1][1], t[1][2], t[1][3]);
+            }
+        }
+        cur = nxt;
+        nxt = nn;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The coarse end of the V-cycle in one launch.
 //
 // On the smallest levels every step of the cycle is a short chain of

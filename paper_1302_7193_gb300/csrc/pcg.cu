@@ -129,6 +129,7 @@ struct pcg_ctx {
     long long mg_few = 0;                 // chunked line solve below this many columns (0: by precision)
     int mg_resid_pb = 0;                  // k_mg_resid prefetch depth, 1, 2 or 4 levels (0: by precision)
     int mg_fuse = 1;                      // downward residual and restriction in one kernel
+    long long mg_quad = 16384;            // FP32 residuals on float4 quads of row pairs on levels of at least this many columns (0: none)
     long long mg_tail_cols = 4096;        // levels of at most this many columns may run in k_mg_tail (0: none)
     long long mg_tail_smem = 200 * 1024;  // dynamic shared memory k_mg_tail may use for the levels' vectors
     // PCG_ALG_SINGLE_REDUCTION: one k_sweep_sr per pass; r, s (q64), w double-buffered
@@ -746,8 +747,37 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
             ks *= 2;
         return ks;
     };
+    // FP32 levels whose rows split into quads, whose row count is even and
+    // that have at least mg_quad columns take the residual kernels on float4
+    // quads of row pairs (k_mg_resid4): fewer loads and instructions per cell
+    // where the level is large enough to be bound by them; on smaller levels
+    // the scalar kernels' thread per column keeps more loads in flight.
+    auto quad = [&](pcg_t hl) {
+        return sizeof(V) == 4 && h->mg_quad > 0 && hl->plane >= h->mg_quad && hl->nx % 4 == 0 && hl->ny % 2 == 0;
+    };
+    auto resid4 = [&](int l, int mode, V* out) {
+        if constexpr (sizeof(V) == 4) {
+            pcg_t hl = H(l);
+            const long long units = (long long)(hl->ny / 2) * (hl->nx / 4);
+            int ks = 1;
+            while (units * hl->nrhs * ks < h->mg_resid_threads / 4 && ks < 32 && hl->nz / (2 * ks) >= 4 &&
+                   (long long)hl->nrhs * ks * 2 <= 65535)
+                ks *= 2;
+            const dim3 g((unsigned)((units + 127) / 128), 1, (unsigned)(hl->nrhs * ks));
+            const pcg::OpView<float> v = level_view<V>(hl);
+            if (mode == 0)
+                pcg::k_mg_resid4<0><<<g, 128, 0, s>>>(v, R(l), Z(l), out, st, ks);
+            else
+                pcg::k_mg_resid4<1><<<g, 128, 0, s>>>(v, R(l), Z(l), out, st, ks);
+            ++n;
+        }
+    };
     auto resid = [&](int l) {                            // t = r - A z
         pcg_t hl = H(l);
+        if (quad(hl)) {
+            resid4(l, 0, T(l));
+            return;
+        }
         const int ks = ksplit(hl);
         const dim3 g(hl->grid_c.x, hl->grid_c.y, hl->grid_c.z * ks);
         const int pb = h->mg_resid_pb > 0 ? h->mg_resid_pb : (sizeof(V) == 4 ? 4 : 2);
@@ -794,6 +824,10 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
         smooth_first(l, omega);
         for (int k = 1; k < h->mg_nu; ++k) smooth_more(l);
         pcg_t hl = H(l), hc = H(l + 1);
+        if (quad(hl)) {                                  // the residual restricted as it is formed
+            resid4(l, 1, const_cast<V*>(R(l + 1)));
+            continue;
+        }
         if (h->mg_fuse && hl->ny / 2 <= 65535) {
             // the residual restricted as it is formed (t is not written)
             const int ks = ksplit(hl);
@@ -1290,6 +1324,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     if (const char* e = std::getenv("PCG_MG_RESID_PB")) h->mg_resid_pb = std::atoi(e);                // experiments
     if (const char* e = std::getenv("PCG_MG_FUSE")) h->mg_fuse = std::atoi(e) ? 1 : 0;                 // experiments
     if (const char* e = std::getenv("PCG_MG_TAIL")) h->mg_tail_cols = std::atoll(e);                  // 0: no k_mg_tail
+    if (const char* e = std::getenv("PCG_MG_QUAD")) h->mg_quad = std::atoll(e);                       // 0: no k_mg_resid4
     h->rhs_stats.assign(h->nrhs, pcg_stats_t{});
     if (const char* tr = std::getenv("PCG_TRACE")) h->trace = std::atoi(tr);
     h->block = dim3(BX, BY, 1);

@@ -162,46 +162,54 @@ def test_mg_f32_batch_equals_single_bitwise(torch_cuda):
             assert np.array_equal(x1.cpu().numpy().reshape(p.shape), xb[r])
 
 
+FUSED = {"PCG_MG_TAIL": "4096", "PCG_MG_QUAD": "1"}      # the fused kernels on every level that allows them
+SEPARATE = {"PCG_MG_TAIL": "0", "PCG_MG_QUAD": "0"}      # one launch per step, scalar residuals
+
+
 @pytest.mark.parametrize("prec", ["multigrid", "multigrid-f32"])
 @pytest.mark.parametrize("name,p", CASES, ids=IDS)
-def test_coarse_levels_in_one_launch_bitwise(torch_cuda, monkeypatch, name, p, prec):
-    """The smallest levels run in one launch (k_mg_tail) by
-    default; PCG_MG_TAIL=0 runs them as separate launches.  Both do the same
-    arithmetic in the same order, so the V-cycles and the CG iterates built
-    on them agree bit for bit, and the single launch makes fewer launches."""
+def test_fused_vcycle_matches_separate_launches_bitwise(torch_cuda, monkeypatch, name, p, prec):
+    """The smallest levels in one launch (k_mg_tail) and the FP32 residuals on
+    float4 quads of row pairs (k_mg_resid4, here on every level whose shape
+    allows it) against one launch per step with the scalar kernels
+    (PCG_MG_TAIL=0, PCG_MG_QUAD=0).  Both plans do the same arithmetic in the
+    same order, so the V-cycles and the CG iterates built on them agree bit
+    for bit, and the fused plan makes fewer launches."""
     import paper_1302_7193_gb300 as pkg
     torch = torch_cuda
     r = np.random.default_rng(7).uniform(-1, 1, p.shape)
     b = W.rhs_for(p, seed=2)
-    out = {}
-    for tail in ("4096", "0"):
-        monkeypatch.setenv("PCG_MG_TAIL", tail)
+    out = []
+    for plan in (FUSED, SEPARATE):
+        for k, v in plan.items():
+            monkeypatch.setenv(k, v)
         with pkg.Solver(p, preconditioner=prec) as s:
             z = torch.empty(p.n_cells, dtype=torch.float64, device="cuda")
             s.precond(_dev(torch, r), z)
             x = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
             st = s.solve(_dev(torch, b), x, tol=0.0, maxit=6)
-            out[tail] = (z.cpu().numpy(), x.cpu().numpy(), st.iterations, s.kernel_launches)
-    (z1, x1, it1, n1), (z0, x0, it0, n0) = out["4096"], out["0"]
+            out.append((z.cpu().numpy(), x.cpu().numpy(), st.iterations, s.kernel_launches))
+    (z1, x1, it1, n1), (z0, x0, it0, n0) = out
     assert np.array_equal(z1, z0)
     assert it1 == it0 == 6 and np.array_equal(x1, x0)
     assert n1 < n0, (n1, n0)
 
 
-def test_coarse_levels_in_one_launch_batched(torch_cuda, monkeypatch):
-    """Three right-hand sides, one block each, one of them stopped early:
-    the batched FP32 cycle inside CG equals the separate launches bit for bit."""
+def test_fused_vcycle_batched(torch_cuda, monkeypatch):
+    """Three right-hand sides, one of them stopped early: the batched FP32
+    cycle inside CG equals the separate launches bit for bit."""
     import paper_1302_7193_gb300 as pkg
     torch = torch_cuda
     p = W.box_problem(32, 16, 12, 0.01)
     bs = W.batched_rhs(p, [0, 5, 9])
     bs[1] *= 1e-3
-    xs = {}
-    for tail in ("4096", "0"):
-        monkeypatch.setenv("PCG_MG_TAIL", tail)
+    xs = []
+    for plan in (FUSED, SEPARATE):
+        for k, v in plan.items():
+            monkeypatch.setenv(k, v)
         with pkg.Solver(p, nrhs=3, preconditioner="multigrid-f32") as s:
             xb = torch.zeros(bs.size, dtype=torch.float64, device="cuda")
             s.solve(_dev(torch, bs), xb, tol=1e-9, maxit=500)
-            xs[tail] = (xb.cpu().numpy(), [s.pcg_rhs_stats(k).iterations for k in range(3)])
-    assert xs["4096"][1] == xs["0"][1]
-    assert np.array_equal(xs["4096"][0], xs["0"][0])
+            xs.append((xb.cpu().numpy(), [s.pcg_rhs_stats(k).iterations for k in range(3)]))
+    assert xs[0][1] == xs[1][1]
+    assert np.array_equal(xs[0][0], xs[1][0])
