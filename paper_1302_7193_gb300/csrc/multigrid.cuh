@@ -341,6 +341,34 @@ __global__ void k_mg_prolong(const T* __restrict__ zc, T* __restrict__ zf, int n
     });
 }
 
+// zf += P zc on FP32 levels whose rows split into quads (n_x % 4 == 0, n_y
+// even): a thread adds the two coarse values under a quad of fine cells, at
+// every gridDim.y-th level.  Grid (ceil(n_y n_x / 4 / 256), level groups, nrhs).
+__global__ __launch_bounds__(256) void k_mg_prolong4(const float* __restrict__ zc, float* __restrict__ zf, int nxf,
+                                                     int nyf, int nz, int nrhs, const SolveState* __restrict__ st) {
+    const int nq = nxf / 4;
+    const long long u = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (u >= (long long)nyf * nq) return;
+    const int j = (int)(u / nq), q = (int)(u - (long long)j * nq);
+    const long long planef = (long long)nxf * nyf, planec = planef / 4;
+    const int nxc = nxf / 2;
+    for (int rhs = blockIdx.z; rhs < nrhs; rhs += gridDim.z) {
+        if (st[rhs].done) continue;
+        float* f = zf + rhs * planef * nz + (long long)j * nxf + 4 * q;
+        const float* c = zc + rhs * planec * nz + (long long)(j >> 1) * nxc + 2 * q;
+#pragma unroll 4
+        for (int k = blockIdx.y; k < nz; k += gridDim.y) {
+            float4 v = *reinterpret_cast<float4*>(f + k * planef);
+            const float2 p = __ldg(reinterpret_cast<const float2*>(c + k * planec));
+            v.x += p.x;
+            v.y += p.x;
+            v.z += p.y;
+            v.w += p.y;
+            *reinterpret_cast<float4*>(f + k * planef) = v;
+        }
+    }
+}
+
 // a <-> b between the FP64 CG and an FP32 V-cycle
 template <typename TA, typename TB>
 __global__ void k_mg_convert(const TA* __restrict__ a, TB* __restrict__ b, long long vol, int nrhs,
@@ -408,8 +436,12 @@ __global__ __launch_bounds__(NT) void k_mg_dots(OpView<double> op, const double*
 // blockIdx.z = rhs * ksplit + part, part taking levels
 // [part n_z / ksplit, (part + 1) n_z / ksplit).
 // ---------------------------------------------------------------------------
-struct Quad8 {         // z and r of a row pair's two quads at one level
+// A row pair's two quads at one level: the own z rows, needed one level
+// earlier too (as the level above), and the rest.
+struct QuadOwn {
     float4 z0, z1;     // rows 2 jp, 2 jp + 1
+};
+struct QuadRest {
     float4 zs, zn;     // the row below 2 jp, the row above 2 jp + 1
     float4 r0, r1;
     float e0, w0, e1, w1;   // edge neighbours where no lane holds them
@@ -449,12 +481,15 @@ __global__ __launch_bounds__(128) void k_mg_resid4(OpView<float> op, const float
     const int k0 = (int)((long long)part * nz / ksplit), k1 = (int)((long long)(part + 1) * nz / ksplit);
     auto zq = [&](int k, long long c) -> float4 { return ld4(zb + (long long)k * pl + c); };   // a quad of z
     auto zpt = [&](int k, int j, int i) -> float { return __ldg(zb + (long long)k * pl + (long long)j * nx + i); };
-    // the level's loads; own = false: only the own rows (the level above a part)
-    auto fetch = [&](int k, Quad8& v, bool own) {
+    // a level's loads: the own rows are issued three levels ahead (the level
+    // above is read one level before the level itself), the rest two
+    auto fetch_own = [&](int k, QuadOwn& v) {
         if (!valid) return;
         v.z0 = zq(k, c0);
         v.z1 = zq(k, c1);
-        if (own) return;
+    };
+    auto fetch_rest = [&](int k, QuadRest& v) {
+        if (!valid) return;
         v.zs = zq(k, cs);
         v.zn = zq(k, cn);
         v.r0 = ld4(rb + (long long)k * pl + c0);
@@ -495,39 +530,47 @@ __global__ __launch_bounds__(128) void k_mg_resid4(OpView<float> op, const float
             ms[1][m] = mn[0][m];
         }
     }
-    Quad8 cur{}, nxt{}, nn{};
+    // own rows of levels k .. k + 3 (up to k1, the level above the part,
+    // below n_z), the rest of levels k .. k + 2 (below k1)
+    QuadOwn o0{}, o1{}, o2{}, o3{};
+    QuadRest q0{}, q1{}, q2{};
+    const int kown = min(k1, nz - 1);
+    fetch_own(k0, o0);
+    if (k0 + 1 <= kown) fetch_own(k0 + 1, o1);
+    if (k0 + 2 <= kown) fetch_own(k0 + 2, o2);
+    fetch_rest(k0, q0);
+    if (k0 + 1 < k1) fetch_rest(k0 + 1, q1);
     float fp[2][4];   // vertical flux from below, per cell
-    fetch(k0, cur, false);
-    if (k0 + 1 < nz) fetch(k0 + 1, nxt, k0 + 1 >= k1);
     if (k0 > 0) {
-        Quad8 lo{};
-        fetch(k0 - 1, lo, true);
+        QuadOwn lo{};
+        fetch_own(k0 - 1, lo);
         const float wlo = ldro(op.wv + k0 - 1);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            fp[0][m] = wlo * (q4(lo.z0, m) - q4(cur.z0, m));
-            fp[1][m] = wlo * (q4(lo.z1, m) - q4(cur.z1, m));
+            fp[0][m] = wlo * (q4(lo.z0, m) - q4(o0.z0, m));
+            fp[1][m] = wlo * (q4(lo.z1, m) - q4(o0.z1, m));
         }
     } else {
 #pragma unroll
         for (int m = 0; m < 4; ++m) fp[0][m] = fp[1][m] = 0.f;
     }
     for (int k = k0; k < k1; ++k) {
-        if (k + 2 < nz && k + 2 <= k1) fetch(k + 2, nn, k + 2 >= k1);
+        if (k + 3 <= kown) fetch_own(k + 3, o3);
+        if (k + 2 < k1) fetch_rest(k + 2, q2);
         const float wvk = ldro(op.wv + k), dkk = ldro(op.dk + k), mk = ldro(op.mass + k);
         const bool top = k + 1 >= nz;
         float t[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const float4 zr = h == 0 ? cur.z0 : cur.z1;
-            const float4 zup = h == 0 ? nxt.z0 : nxt.z1;
-            const float4 zno = h == 0 ? cur.z1 : cur.zn;   // north row
-            const float4 zso = h == 0 ? cur.zs : cur.z0;   // south row
-            const float4 rr = h == 0 ? cur.r0 : cur.r1;
+            const float4 zr = h == 0 ? o0.z0 : o0.z1;
+            const float4 zup = h == 0 ? o1.z0 : o1.z1;
+            const float4 zno = h == 0 ? o0.z1 : q0.zn;   // north row
+            const float4 zso = h == 0 ? q0.zs : o0.z0;   // south row
+            const float4 rr = h == 0 ? q0.r0 : q0.r1;
             const float esh = __shfl_down_sync(0xffffffffu, zr.x, 1);
             const float wsh = __shfl_up_sync(0xffffffffu, zr.w, 1);
-            const float E = e_shfl ? esh : (h == 0 ? cur.e0 : cur.e1);
-            const float Wv = w_shfl ? wsh : (h == 0 ? cur.w0 : cur.w1);
+            const float E = e_shfl ? esh : (h == 0 ? q0.e0 : q0.e1);
+            const float Wv = w_shfl ? wsh : (h == 0 ? q0.w0 : q0.w1);
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const float zcv = q4(zr, m);
@@ -557,8 +600,11 @@ __global__ __launch_bounds__(128) void k_mg_resid4(OpView<float> op, const float
                 *reinterpret_cast<float4*>(ob + c1) = make_float4(t[1][0], t[1][1], t[1][2], t[1][3]);
             }
         }
-        cur = nxt;
-        nxt = nn;
+        o0 = o1;
+        o1 = o2;
+        o2 = o3;
+        q0 = q1;
+        q1 = q2;
     }
 }
 

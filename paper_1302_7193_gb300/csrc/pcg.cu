@@ -881,6 +881,17 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
     }
     for (int l = std::min(L - 2, lt - 1); l >= 0; --l) {
         pcg_t hl = H(l);
+        if constexpr (sizeof(V) == 4) {
+            if (quad(hl)) {
+                const long long units = (long long)hl->ny * (hl->nx / 4);
+                const dim3 g((unsigned)((units + 255) / 256), (unsigned)std::min((hl->nz + 3) / 4, 65535),
+                             (unsigned)std::min(hl->nrhs, 65535));
+                pcg::k_mg_prolong4<<<g, 256, 0, s>>>(Z(l + 1), Z(l), hl->nx, hl->ny, hl->nz, hl->nrhs, st);
+                ++n;
+                for (int k = 0; k < h->mg_nu; ++k) smooth_more(l);
+                continue;
+            }
+        }
         const CellLaunch cl = cell_launch(hl->nx, hl->ny, hl->nz, hl->nrhs);
         pcg::k_mg_prolong<V><<<cl.g, cl.b, 0, s>>>(Z(l + 1), Z(l), hl->nx, hl->ny, hl->nz, hl->nrhs, cl.nbi, st);
         ++n;
