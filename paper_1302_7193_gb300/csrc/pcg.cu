@@ -103,10 +103,6 @@ struct pcg_ctx {
     int chunked32 = 0, chunked64 = 0, lz_a = 16, lz_b = 16, nch_b = 1;
     int spmv32 = 0, spmv64 = 0;          // SpMV sweep variant: 0 per column, 1 chunked, 2 chunked + smem tile, 3 TMA,
                                           // 4 persistent two-stage TMA
-    // minimum resident blocks asked of the compiler for the chunked FP32 sweeps;
-    // 3 for the preconditioner sweep (85-register cap, no spills) measured
-    // 9-13 % faster than the uncapped 108 registers at 256^2, 1024^2 and the shell
-    int prec_minb = 3, spmv_minb = 1;
     dim3 grid_a, block_a, grid_b, block_b;
     int nblk_a = 0, nblk_b = 0;
     dim3 grid_c, block_c;                 // one-thread-per-column sweeps: 32 x by column tiles
@@ -126,9 +122,6 @@ struct pcg_ctx {
     SolveState* mg_free = nullptr;        // all-active states for a V-cycle outside a solve
     int mg_nu = 1, mg_coarse = 8;
     long long mg_resid_threads = 524288;  // k_mg_resid splits columns until this many threads run
-    long long mg_few = 0;                 // chunked line solve below this many columns (0: by precision)
-    int mg_resid_pb = 0;                  // k_mg_resid prefetch depth, 1, 2 or 4 levels (0: by precision)
-    int mg_fuse = 1;                      // downward residual and restriction in one kernel
     long long mg_quad = 16384;            // FP32 residuals on float4 quads of row pairs on levels of at least this many columns (0: none)
     long long mg_tail_cols = 4096;        // levels of at most this many columns may run in k_mg_tail (0: none)
     long long mg_tail_smem = 200 * 1024;  // dynamic shared memory k_mg_tail may use for the levels' vectors
@@ -622,9 +615,10 @@ void launch_prec(pcg_t h, cudaStream_t s, const OpView<T>& v, T* r, T* q, T* z, 
     pcg::k_sweep_prec_chunked<T, LZ, MB><<<h->grid_a, h->block_a, 0, s>>>(v, r, q, z, st, h->partials, h->counters, \
                                                                           h->nblk_a)
     if (chunked && h->lz_a == 16) {
-        if (h->prec_minb == 3) PCG_PREC_CH(16, 3);
-        else if (h->prec_minb == 4) PCG_PREC_CH(16, 4);
-        else PCG_PREC_CH(16, 1);
+        // three resident blocks asked of the compiler (85-register cap, no
+        // spills): 9-13 % faster than the uncapped 108 registers at 256^2,
+        // 1024^2 and the shell
+        PCG_PREC_CH(16, 3);
     } else if (chunked) {
         PCG_PREC_CH(32, 1);
     } else {
@@ -669,12 +663,8 @@ void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, 
     }
     if (mode == 2) {
         PCG_SPMV_CH(16, true, 1);
-    } else if ((mode == 1 || mode >= 3) && h->lz_b == 8) {
-        if (h->spmv_minb == 8) PCG_SPMV_CH(8, false, 8);
-        else PCG_SPMV_CH(8, false, 1);
     } else if (mode == 1 || mode >= 3) {
-        if (h->spmv_minb == 6) PCG_SPMV_CH(16, false, 6);
-        else PCG_SPMV_CH(16, false, 1);
+        PCG_SPMV_CH(16, false, 1);
     } else {
         const dim3 g(h->grid_c.x, h->grid_c.y, h->grid_c.z * h->ksplit);
         if (sizeof(T) == 8 && h->spmv_pipe)
@@ -737,8 +727,7 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
     // chunked form is the faster one on every level (it keeps more loads in
     // flight and has no y round trip through memory); in FP64, bound by the
     // FP64 pipe, its extra arithmetic makes it slower on large levels.
-    const long long few_cols =
-        h->mg_few > 0 ? h->mg_few : (sizeof(V) == 4 ? std::numeric_limits<long long>::max() : 16384);
+    const long long few_cols = sizeof(V) == 4 ? std::numeric_limits<long long>::max() : 16384;
     auto few = [&](pcg_t hl) { return hl->plane * (long long)hl->nrhs < few_cols && hl->nz <= 128; };
     auto ksplit = [&](pcg_t hl) {
         int ks = 1;
@@ -760,7 +749,8 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
             pcg_t hl = H(l);
             const long long units = (long long)(hl->ny / 2) * (hl->nx / 4);
             int ks = 1;
-            while (units * hl->nrhs * ks < h->mg_resid_threads / 4 && ks < 32 && hl->nz / (2 * ks) >= 4 &&
+            // one thread per eight cells: half the scalar kernels' thread target
+            while (units * hl->nrhs * ks < h->mg_resid_threads / 2 && ks < 32 && hl->nz / (2 * ks) >= 4 &&
                    (long long)hl->nrhs * ks * 2 <= 65535)
                 ks *= 2;
             const dim3 g((unsigned)((units + 127) / 128), 1, (unsigned)(hl->nrhs * ks));
@@ -780,13 +770,11 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
         }
         const int ks = ksplit(hl);
         const dim3 g(hl->grid_c.x, hl->grid_c.y, hl->grid_c.z * ks);
-        const int pb = h->mg_resid_pb > 0 ? h->mg_resid_pb : (sizeof(V) == 4 ? 4 : 2);
-        if (pb == 4)
+        // the loads of the next 4 (FP32) or 2 (FP64) levels in flight
+        if constexpr (sizeof(V) == 4)
             pcg::k_mg_resid<V, 4><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
-        else if (pb == 2)
-            pcg::k_mg_resid<V, 2><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
         else
-            pcg::k_mg_resid<V, 1><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
+            pcg::k_mg_resid<V, 2><<<g, hl->block_c, 0, s>>>(level_view<V>(hl), R(l), Z(l), T(l), st, ks);
         ++n;
     };
     auto smooth = [&](int l, const V* rin, V om, int acc) {   // z = (acc ? z : 0) + omega M^{-1} rin
@@ -828,7 +816,7 @@ int launch_vcycle(pcg_t h, cudaStream_t s, const SolveState* st, const V* r0, V*
             resid4(l, 1, const_cast<V*>(R(l + 1)));
             continue;
         }
-        if (h->mg_fuse && hl->ny / 2 <= 65535) {
+        if (hl->ny / 2 <= 65535) {
             // the residual restricted as it is formed (t is not written)
             const int ks = ksplit(hl);
             const dim3 g((hl->nx + 31) / 32, hl->ny / 2, hl->nrhs * ks);
@@ -1330,10 +1318,6 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
         return fail(nullptr, PCG_ERR_INVALID_ARG,
                     "PCG_ALG_SINGLE_REDUCTION needs PCG_PREC_LINE and n_z <= " + std::to_string(pcg::SR_MAX_NZ));
     }
-    if (const char* e = std::getenv("PCG_MG_RESID_THREADS")) h->mg_resid_threads = std::atoll(e);   // experiments
-    if (const char* e = std::getenv("PCG_MG_FEW")) h->mg_few = std::atoll(e);                        // experiments
-    if (const char* e = std::getenv("PCG_MG_RESID_PB")) h->mg_resid_pb = std::atoi(e);                // experiments
-    if (const char* e = std::getenv("PCG_MG_FUSE")) h->mg_fuse = std::atoi(e) ? 1 : 0;                 // experiments
     if (const char* e = std::getenv("PCG_MG_TAIL")) h->mg_tail_cols = std::atoll(e);                  // 0: no k_mg_tail
     if (const char* e = std::getenv("PCG_MG_QUAD")) h->mg_quad = std::atoll(e);                       // 0: no k_mg_resid4
     h->rhs_stats.assign(h->nrhs, pcg_stats_t{});
@@ -1404,10 +1388,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     h->grid_a = dim3((h->nx + 31) / 32, h->ny, h->nrhs);
     h->nblk_a = (int)(h->grid_a.x * h->grid_a.y);
     h->lz_b = 16;
-    if (const char* e = std::getenv("PCG_SPMV_LZ")) h->lz_b = std::atoi(e) == 8 ? 8 : 16;
     if (const char* e = std::getenv("PCG_PDL")) h->pdl = std::atoi(e) ? 1 : 0;
-    if (const char* e = std::getenv("PCG_PREC_MINB")) h->prec_minb = std::atoi(e);
-    if (const char* e = std::getenv("PCG_SPMV_MINB")) h->spmv_minb = std::atoi(e);
     h->nch_b = (h->nz + h->lz_b - 1) / h->lz_b;
     h->block_b = dim3(BX, BY, 1);
     h->grid_b = dim3((h->nx + BX - 1) / BX, (h->ny + BY - 1) / BY, h->nrhs * h->nch_b);

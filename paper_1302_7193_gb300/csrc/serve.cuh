@@ -90,10 +90,6 @@ struct pcg_server {
     bool items_dirty = true;
     cudaGraphExec_t graph = nullptr;
     int blocks_prec = 152 * 3, blocks_spmv = 152 * 2;   // persistent grids (resident blocks on every SM)
-    int no_tma = 0;                     // PCG_SERVE_TMA=0: stage the SpMV tiles by the threads
-    int no_prec_tma = 0;                // PCG_SERVE_PREC_TMA=0: preconditioner items read r, q directly
-    int prec_minb = 2;                  // PCG_SERVE_PREC_MINB=3: preconditioner kernel with 3 blocks per SM
-    long long active_cap = 0;           // PCG_SERVE_ACTIVE: admit while the admitted unknowns stay below this (0: no cap)
     long long active_unknowns = 0;      // unknowns of the admitted requests
     long long epochs = 0, launches = 0, retired = 0;
     int trace = 0;                      // PCG_TRACE=1: refinement history per request on stderr
@@ -255,10 +251,10 @@ int admit(pcg_server_t s, ServeReq* q) {
                         encode_map_dims(&hm[2], q->q, nx, ny, nz, BX, pcg::SERVE_BY, pcg::SERVE_LZ) &&
                         encode_map_dims(&hm[3], q->z, nx, ny, nz, zx, pcg::SERVE_BY + 2, pcg::SERVE_LZ + 2);
         const unsigned pz = (unsigned)(q->nch * pcg::SERVE_LZ);
-        q->prec_tma = ok && !s->no_prec_tma && !q->colmode && (unsigned)q->rows * pz <= (unsigned)(8 * pcg::SERVE_LZ) &&
+        q->prec_tma = ok && !q->colmode && (unsigned)q->rows * pz <= (unsigned)(8 * pcg::SERVE_LZ) &&
                       encode_map_dims(&hm[4], q->r, nx, ny, nz, BX, (unsigned)q->rows, pz) &&
                       encode_map_dims(&hm[5], q->q, nx, ny, nz, BX, (unsigned)q->rows, pz);
-        if (ok && !s->no_tma) {
+        if (ok) {
             // pageable source: the call returns once the maps have been staged
             SRV_CK(s, cudaMemcpyAsync(q->tmaps, hm, sizeof(hm), cudaMemcpyHostToDevice, st));
         } else {
@@ -421,12 +417,8 @@ int capture_epochs(pcg_server_t s) {
     // every launch takes its items in arrival order from a counter of its own
     SRV_CK(s, cudaMemsetAsync(s->d_fetch, 0, 2 * sizeof(unsigned) * (size_t)s->epochs_per_launch, s->cap_stream));
     for (int e = 0; e < s->epochs_per_launch; ++e) {
-        if (s->prec_minb == 3)
-            pcg::k_serve_prec<3><<<s->blocks_prec, dim3(BX, 8, 1), pcg::SERVE_PREC_SMEM, s->cap_stream>>>(
-                s->d_slots, s->d_items, s->d_nitems, s->d_fetch + 2 * e);
-        else
-            pcg::k_serve_prec<2><<<s->blocks_prec, dim3(BX, 8, 1), pcg::SERVE_PREC_SMEM, s->cap_stream>>>(
-                s->d_slots, s->d_items, s->d_nitems, s->d_fetch + 2 * e);
+        pcg::k_serve_prec<2><<<s->blocks_prec, dim3(BX, 8, 1), pcg::SERVE_PREC_SMEM, s->cap_stream>>>(
+            s->d_slots, s->d_items, s->d_nitems, s->d_fetch + 2 * e);
         pcg::k_serve_scalars<0><<<s->max_slots, 256, 0, s->cap_stream>>>(s->d_slots, s->d_inner);
         pcg::k_serve_spmv<<<s->blocks_spmv, dim3(BX, pcg::SERVE_BY, 1), pcg::SERVE_SPMV_SMEM, s->cap_stream>>>(
             s->d_slots, s->d_items + s->items_cap, s->d_nitems + 1, s->d_fetch + 2 * e + 1);
@@ -527,26 +519,20 @@ int pcg_server_create(size_t budget_bytes, int max_slots, const pcg_opts_t* opts
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (const char* e2 = std::getenv("PCG_SERVE_TMA")) s->no_tma = std::atoi(e2) == 0 ? 1 : 0;
-    if (const char* e5 = std::getenv("PCG_SERVE_PREC_TMA")) s->no_prec_tma = std::atoi(e5) == 0 ? 1 : 0;   // experiments
     // persistent grids: as many blocks as are resident on every SM at once
     if ((e = cudaFuncSetAttribute(pcg::k_serve_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)pcg::SERVE_SPMV_SMEM)) != cudaSuccess) {
         s->err = cudaGetErrorString(e);
         return bail(PCG_ERR_CUDA);
     }
-    if (const char* e3 = std::getenv("PCG_SERVE_PREC_MINB")) s->prec_minb = std::atoi(e3) == 3 ? 3 : 2;
-    for (auto fn : {pcg::k_serve_prec<2>, pcg::k_serve_prec<3>})
-        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcg::SERVE_PREC_SMEM)) !=
-            cudaSuccess) {
-            s->err = cudaGetErrorString(e);
-            return bail(PCG_ERR_CUDA);
-        }
-    if (const char* e4 = std::getenv("PCG_SERVE_ACTIVE")) s->active_cap = std::atoll(e4);
+    if ((e = cudaFuncSetAttribute(pcg::k_serve_prec<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)pcg::SERVE_PREC_SMEM)) != cudaSuccess) {
+        s->err = cudaGetErrorString(e);
+        return bail(PCG_ERR_CUDA);
+    }
     int occ_a = 0, occ_b = 0;
-    cudaError_t eo = s->prec_minb == 3
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<3>, BX * 8, pcg::SERVE_PREC_SMEM)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<2>, BX * 8, pcg::SERVE_PREC_SMEM);
+    const cudaError_t eo =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, pcg::k_serve_prec<2>, BX * 8, pcg::SERVE_PREC_SMEM);
     if (eo != cudaSuccess || occ_a < 1) occ_a = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, pcg::k_serve_spmv, BX * pcg::SERVE_BY,
                                                       pcg::SERVE_SPMV_SMEM) != cudaSuccess || occ_b < 1)
@@ -631,9 +617,6 @@ int pcg_serve_step(pcg_server_t s, int max_epochs, int* n_active, int* n_pending
             for (ServeReq* r : s->slot_req) if (!r) { free_slot = true; break; }
             const int cls_mode = serve_cls_mode(q->grid, !q->alpha_e.empty() || !q->alpha_n.empty());
             if (!free_slot || s->used + request_bytes(q->grid, cls_mode) > s->budget) break;
-            // optional cap on the unknowns in flight (the first request always fits)
-            const long long qn = (long long)q->grid.n_x * q->grid.n_y * q->grid.n_z;
-            if (s->active_cap > 0 && s->active_unknowns > 0 && s->active_unknowns + qn > s->active_cap) break;
             s->pending.pop_front();
             int rc = admit(s, q);
             if (rc) return rc;
