@@ -15,7 +15,9 @@ floor, and to the FP64 solve's own true residual), the multigrid-
 preconditioned solves, and three more configurations measured in the same
 run: the 1024 x 1024 x 128 box (mixed against FP64), the served batch on a
 Poisson request stream (throughput, p50/p99, against one-at-a-time solves)
-and the 16-rhs 1440 x 640 x 64 shell band (mixed against FP64).
+and the 16-rhs 1440 x 640 x 64 shell band (mixed against FP64; the FP64
+solve there is capped at 600 iterations and its time per pass scaled to the
+full solve's iteration count, which `--workload shell-batch` measures).
 
 Multi-GPU: the solver does not shard (one problem per GPU); with N ranks each
 rank runs its own replica of the workload and `value` counts the solves of
@@ -473,7 +475,15 @@ def _timed_solve(torch, stream, s, b, x, tol, maxit=200000):
     return st, e0.elapsed_time(e1)
 
 
-def large_config_measure(dev, pkg, W, torch, which: str, hbm_peak: float, same_accuracy: bool = True):
+# FP64 iterations of the 16-rhs shell band to relative residual 1e-8 (worst
+# right-hand side), as the full run `python bench.py --workload shell-batch`
+# measures them; the default benchmark line times a capped FP64 solve and
+# scales its time per pass to this count.
+SHELL_FP64_ITERATIONS = 4603
+
+
+def large_config_measure(dev, pkg, W, torch, which: str, hbm_peak: float, same_accuracy: bool = True,
+                         fp64_maxit: int | None = None):
     """The larger configurations: FP64 and mixed solves of the same batch to
     relative residual 1e-8, device-timed (one warm-up solve each, which also
     captures the graphs), with both solutions' true residuals, the distance of
@@ -481,7 +491,11 @@ def large_config_measure(dev, pkg, W, torch, which: str, hbm_peak: float, same_a
     times against HBM, and (same_accuracy) the mixed form stopped at the FP64
     solve's own true residual.  box1024: 1024 x 1024 x 128 box, alpha = 1 +
     0.5 sin sin, b uniform seed 0.  shell-batch: 1440 x 640 x 64 lat-lon band,
-    16 right-hand sides (seeds 0..15) solved together."""
+    16 right-hand sides (seeds 0..15) solved together.
+
+    fp64_maxit caps the FP64 solve (it then stops before converging): its
+    rate is the measured time per pass scaled to SHELL_FP64_ITERATIONS + 1
+    passes, stated in the output, and the FP64 solution is not compared."""
     import numpy as np
     if which == "box1024":
         p = W.large_box()
@@ -504,7 +518,8 @@ def large_config_measure(dev, pkg, W, torch, which: str, hbm_peak: float, same_a
         with pkg.Solver(p, nrhs=nrhs, precision=prec, stream=stream.cuda_stream) as s:
             x = torch.zeros(n, dtype=torch.float64, device=dev)
             s.solve(b, x, tol=TOL, maxit=20)                  # warm-up: graph capture, lazy loading
-            st, ms = _timed_solve(torch, stream, s, b, x, TOL)
+            capped = prec == "fp64" and fp64_maxit is not None
+            st, ms = _timed_solve(torch, stream, s, b, x, TOL, fp64_maxit if capped else 200000)
             tp, tsw = s.pcg_time_sweeps(b, prec, passes=3)
             tpass = s.pcg_time_passes(b, prec, passes=5)
             by = 8 if prec == "fp64" else 4
@@ -515,10 +530,22 @@ def large_config_measure(dev, pkg, W, torch, which: str, hbm_peak: float, same_a
                          "status": st.status_name, "ms_per_iteration": tpass,
                          "ms_prec_sweep": tp, "ms_spmv_sweep": tsw,
                          "iteration_gbs_algorithmic": it_gbs, "iteration_hbm_frac": it_gbs / hbm_peak}
-            xs[prec] = x
-    d = (xs["mixed"] - xs["fp64"]).view(nrhs, -1)
-    ref = xs["fp64"].view(nrhs, -1)
-    out["mixed_vs_fp64_max_relerr"] = float((d.norm(dim=1) / ref.norm(dim=1)).max())
+            if capped:
+                # a pass per iteration plus the pass whose test fires (R6)
+                ms_full = ms / (st.iterations + 1) * (SHELL_FP64_ITERATIONS + 1)
+                out[prec].update({
+                    "timed_iterations": st.iterations, "timed_ms": ms, "ms": ms_full, "status": "capped",
+                    "solves_per_s": nrhs * 1000.0 / ms_full, "iterations": SHELL_FP64_ITERATIONS,
+                    "extrapolated": f"solve capped at {fp64_maxit} iterations ({ms:.0f} ms timed); time per pass "
+                                    f"scaled to the {SHELL_FP64_ITERATIONS} iterations the full FP64 solve takes "
+                                    f"(python bench.py --workload shell-batch); residuals are those of the capped "
+                                    f"solve"})
+            else:
+                xs[prec] = x
+    if "fp64" in xs:
+        d = (xs["mixed"] - xs["fp64"]).view(nrhs, -1)
+        ref = xs["fp64"].view(nrhs, -1)
+        out["mixed_vs_fp64_max_relerr"] = float((d.norm(dim=1) / ref.norm(dim=1)).max())
     out["value"] = out["mixed"]["solves_per_s"]
     out["mixed_speedup"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
     out["fp32_iteration_hbm_frac"] = out["mixed"]["iteration_hbm_frac"]
@@ -942,7 +969,7 @@ def main():
             smg["served_speedup_vs_" + key] = smg["value"] / smg[key]["solves_per_s"]
         extras["serve_multigrid"] = smg
         extras["shell_batch"] = large_config_measure(dev, pkg, W, torch, "shell-batch", hbm_peak,
-                                                     same_accuracy=False)
+                                                     same_accuracy=False, fp64_maxit=600)
 
     if rank == 0:
         line = {
