@@ -885,7 +885,7 @@ def main():
                                               "the sweep split below times each sweep alone between events",
                      "fp32_sweeps": {"prec_ms": mp, "prec_gbs": 4 * 4 * n / (mp * 1e-3) / 1e9,
                                      "spmv_ms": msw, "spmv_gbs": 7 * 4 * n / (msw * 1e-3) / 1e9,
-                                     "kernels": ["k_sweep_prec_tma<16,1>", "k_sweep_spmv_tma2<16,4>"]}}
+                                     "kernels": ["k_sweep_prec_tma<16,1>", "k_sweep_spmv_tma2<16,4,2>"]}}
             tol_eq = max(TOL, stats.relres_true)
             sm.solve(b, x, tol=tol_eq, maxit=100000)
             et = []

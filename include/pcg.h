@@ -224,7 +224,8 @@ int pcg_time_passes(pcg_t h, const double* b, int precision, int passes, double*
  * `stream` (a copy from pageable memory returns once the buffer has been
  * read); the factor and solve kernels follow on the same stream.  The first
  * call on each device looks up the array's device address (with that device
- * current).  Every call rewrites the whole array and the staging buffer, so
+ * current); make that first call before any stream capture begins on the
+ * device.  Every call rewrites the whole array and the staging buffer, so
  * calls whose work overlaps on the GPU (other streams) race on the array, and
  * calls from several host threads at once race on the staging buffer.
  * Errors: PCG_ERR_INVALID_ARG, PCG_ERR_CUDA (text in pcg_last_error(NULL)). */

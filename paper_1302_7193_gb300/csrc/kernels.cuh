@@ -927,20 +927,15 @@ __global__ __launch_bounds__(256, MINB) void k_sweep_prec_chunked(OpView<T> op, 
 }
 
 // SpMV sweep: block = 32 x 4 columns, one chunk of LZ levels;
-// blockIdx.z = rhs * nchunks + chunk.  TILE = true stages the z values the
-// stencil needs (levels k0-1 .. k0+LZ, the block's columns plus a one-cell
-// halo, wrapped periodically or clamped at a Neumann edge where the face
-// weight is 0) in shared memory, one 34-wide row per warp load; TILE = false
-// reads the neighbours through the read-only cache.  Either way every load
-// of a full chunk is issued before the arithmetic.
-template <typename T, int LZ, bool TILE, int MINB = 1>
+// blockIdx.z = rhs * nchunks + chunk.  The horizontal neighbours are read
+// through the read-only cache; every load of a full chunk is issued before
+// the arithmetic.
+template <typename T, int LZ, int MINB = 1>
 __global__ __launch_bounds__(NT, MINB) void k_sweep_spmv_chunked(OpView<T> op, T* __restrict__ u, T* __restrict__ p,
                                                            T* __restrict__ q, const T* __restrict__ z,
                                                            SolveState* __restrict__ states,
                                                            double* __restrict__ partials,
                                                            unsigned* __restrict__ counters, int nblocks, int nchunks) {
-    constexpr int TX = BX + 2, TY = BY + 2, TP = TX * TY, NROW = (LZ + 2) * TY;
-    __shared__ T zt[TILE ? (LZ + 2) * TP : 1];
     const int rhs = blockIdx.z / nchunks;
     const int ch = blockIdx.z - rhs * nchunks;
     SolveState* st = states + rhs;
@@ -955,32 +950,6 @@ __global__ __launch_bounds__(NT, MINB) void k_sweep_spmv_chunked(OpView<T> op, T
     const long long pl = op.plane;
     const long long base = (long long)rhs * op.vol;
     const T* __restrict__ zb = z + base;
-    if (TILE) {
-        // lane tx loads tile columns tx and (tx < 2) 32 + tx: x indices wrapped once per thread
-        int ia = (i0 - 1 + tx) % op.nx;
-        if (ia < 0) ia += op.nx;
-        int ib = (i0 + 31 + tx) % op.nx;
-        for (int row = ty; row < NROW; row += BY) {
-            const int kk = row / TY, jj = row - kk * TY;
-            const int k = k0 - 1 + kk;
-            int j = j0 - 1 + jj;
-            if (op.periodic_y) {
-                j %= op.ny;
-                if (j < 0) j += op.ny;
-            } else {
-                j = j < 0 ? 0 : (j >= op.ny ? op.ny - 1 : j);
-            }
-            T* dst = zt + kk * TP + jj * TX;
-            if (k >= 0 && k < op.nz) {
-                const T* src = zb + (long long)k * pl + (long long)j * op.nx;
-                dst[tx] = ldro(src + ia);
-                if (tx < 2) dst[32 + tx] = ldro(src + ib);
-            } else {
-                dst[tx] = T(0);
-                if (tx < 2) dst[32 + tx] = T(0);
-            }
-        }
-    }
     T ur[LZ], pr[LZ], qr[LZ], zr[LZ + 2];
     const bool act = col.valid && kn > 0;
     T* ub = u + base + col.c + (long long)k0 * pl;
@@ -992,12 +961,10 @@ __global__ __launch_bounds__(NT, MINB) void k_sweep_spmv_chunked(OpView<T> op, T
             ur[t] = ub[t * pl];
             pr[t] = pb[t * pl];
             qr[t] = qb[t * pl];
-            if (!TILE) zr[t + 1] = ldro(zb + (long long)(k0 + t) * pl + col.c);
+            zr[t + 1] = ldro(zb + (long long)(k0 + t) * pl + col.c);
         }
-        if (!TILE) {
-            zr[0] = k0 > 0 ? ldro(zb + (long long)(k0 - 1) * pl + col.c) : T(0);
-            zr[LZ + 1] = (k0 + LZ < op.nz) ? ldro(zb + (long long)(k0 + LZ) * pl + col.c) : zr[LZ];
-        }
+        zr[0] = k0 > 0 ? ldro(zb + (long long)(k0 - 1) * pl + col.c) : T(0);
+        zr[LZ + 1] = (k0 + LZ < op.nz) ? ldro(zb + (long long)(k0 + LZ) * pl + col.c) : zr[LZ];
     } else if (act) {
 #pragma unroll
         for (int t = 0; t < LZ; ++t) {
@@ -1005,37 +972,25 @@ __global__ __launch_bounds__(NT, MINB) void k_sweep_spmv_chunked(OpView<T> op, T
                 ur[t] = ub[t * pl];
                 pr[t] = pb[t * pl];
                 qr[t] = qb[t * pl];
-                if (!TILE) zr[t + 1] = ldro(zb + (long long)(k0 + t) * pl + col.c);
+                zr[t + 1] = ldro(zb + (long long)(k0 + t) * pl + col.c);
             }
         }
-        if (!TILE) zr[0] = k0 > 0 ? ldro(zb + (long long)(k0 - 1) * pl + col.c) : T(0);
+        zr[0] = k0 > 0 ? ldro(zb + (long long)(k0 - 1) * pl + col.c) : T(0);
     }
-    if (TILE) __syncthreads();
     Acc<T> sig[1];
     if (act) {
-        const int c0 = (ty + 1) * TX + (tx + 1);
-        T zc = TILE ? zt[TP + c0] : zr[1];
-        T fprev = (k0 > 0) ? ldro(op.wv + k0 - 1) * ((TILE ? zt[c0] : zr[0]) - zc) : T(0);
+        T zc = zr[1];
+        T fprev = (k0 > 0) ? ldro(op.wv + k0 - 1) * (zr[0] - zc) : T(0);
 #pragma unroll
         for (int t = 0; t < LZ; ++t) {
             if (t < kn) {
                 const int k = k0 + t;
-                const T zu = (k + 1 < op.nz) ? (TILE ? zt[(t + 2) * TP + c0] : (t + 1 < kn ? zr[t + 2] : zr[LZ + 1]))
-                                             : zc;
+                const T zu = (k + 1 < op.nz) ? (t + 1 < kn ? zr[t + 2] : zr[LZ + 1]) : zc;
                 ub[t * pl] = fma(alpha, pr[t], ur[t]);
                 const T pn = fma(beta, pr[t], zc);
                 pb[t * pl] = pn;
                 const T f = ldro(op.wv + k) * (zc - zu);
-                T hz;
-                if (TILE) {
-                    const T* zl = zt + (t + 1) * TP;
-                    hz = col.me * (zc - zl[c0 + 1]);
-                    hz = fma(col.mw, zc - zl[c0 - 1], hz);
-                    hz = fma(col.mn, zc - zl[c0 + TX], hz);
-                    hz = fma(col.ms, zc - zl[c0 - TX], hz);
-                } else {
-                    hz = horiz(col, zb + (long long)k * pl, zc);
-                }
+                const T hz = horiz(col, zb + (long long)k * pl, zc);
                 const T az = fma(ldro(op.dk + k), hz, col.area * fma(ldro(op.mass + k), zc, f - fprev));
                 const T qn = fma(beta, qr[t], az);
                 qb[t * pl] = qn;
@@ -1248,16 +1203,24 @@ struct WrapPatch {
 // zs holds levels k0-1 .. k0+LZ of the tile with halo, us/ps/qs levels k0 ..
 // k0+LZ-1 of the block's own columns; tw[t], td[t], tm[t] are wv, dk and mass
 // at level k0 + t (tw[-1] too when k0 > 0); u, p, q point at level 0 of the
-// right-hand side.  sigma = <p, q> of the chunk is summed in plain FP32 (error
-// <= LZ u sum_k |p_k q_k|) and added to the compensated accumulator once.
-template <int LZ, int BYT>
+// right-hand side.  With S > 1 the chunk's levels are split among S threads
+// of the same column: this one takes levels part LZ/S .. (part + 1) LZ/S - 1
+// and forms the flux below its first level from the tile itself (the same
+// operands and operations as the thread below it, so every cell's result is
+// the same for any S).  sigma = <p, q> of the thread's levels is summed in
+// plain FP32 (error <= (LZ/S) u sum_k |p_k q_k|) and added to the compensated
+// accumulator once.
+template <int LZ, int BYT, int S = 1>
 __device__ __forceinline__ void spmv_tile_compute_p(const OpView<float>& op, const Col<float>& col, int tx, int ty,
                                                     int k0, int kn, const float* zs, const float* us,
                                                     const float* ps, const float* qs, const float* tw,
                                                     const float* td, const float* tm, float* __restrict__ u,
                                                     float* __restrict__ p, float* __restrict__ q, float alpha,
-                                                    float beta, Acc<float>& sig) {
+                                                    float beta, Acc<float>& sig, int part = 0) {
     using TT = SpmvTmaTile<LZ, BYT>;
+    constexpr int LH = LZ / S;                  // levels of this thread: part LH .. part LH + LH - 1 of the chunk
+    const int t0 = part * LH;
+    if (t0 >= kn) return;
     const long long pl = op.plane;
     float* __restrict__ ub = u + col.c + (long long)k0 * pl;
     float* __restrict__ pb = p + col.c + (long long)k0 * pl;
@@ -1266,11 +1229,12 @@ __device__ __forceinline__ void spmv_tile_compute_p(const OpView<float>& op, con
     const int c0 = (ty + 1) * ZX + (tx + TMA_HALO_X);
     const int v0 = ty * BX + tx;
     const bool top = k0 + kn == op.nz;          // the chunk holds the top level: no flux above it
-    float zc = zs[ZP + c0];
-    float fprev = (k0 > 0) ? tw[-1] * (zs[c0] - zc) : 0.f;
+    float zc = zs[(t0 + 1) * ZP + c0];
+    float fprev = (k0 + t0 > 0) ? tw[t0 - 1] * (zs[t0 * ZP + c0] - zc) : 0.f;
     float sc = 0.f;
 #pragma unroll
-    for (int t = 0; t < LZ; ++t) {
+    for (int tt = 0; tt < LH; ++tt) {
+        const int t = t0 + tt;
         if (t < kn) {
             const float* zl = zs + (t + 1) * ZP;
             const float zu = (top && t + 1 == kn) ? zc : zl[ZP + c0];
@@ -1369,7 +1333,11 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma(
 // ... and keeps the copies of its next item in flight (second stage, second
 // mbarrier) while it computes the current one.  The level tables of all n_z
 // levels sit in shared memory after the two stages; the grid-level reduction
-// runs once per block instead of once per item.
+// runs once per block instead of once per item.  Blocks are BX x (BYT S)
+// threads: S threads per column, each taking LZ/S levels of the chunk, so a
+// block has S times the warps to hide the latency of its shared-memory reads
+// and of the dependent chain of each column (S = 2 at 256^2 x 128: 54.3 ->
+// 51.0 us per sweep; 1024^2 x 128: 650 -> 621 us).
 // ---------------------------------------------------------------------------
 template <int LZ, int BYT>
 __host__ __device__ constexpr size_t spmv_tma2_smem(int nz) {
@@ -1377,8 +1345,8 @@ __host__ __device__ constexpr size_t spmv_tma2_smem(int nz) {
            128;
 }
 
-template <int LZ, int BYT>
-__global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
+template <int LZ, int BYT, int S = 1>
+__global__ __launch_bounds__(BX * BYT * S) void k_sweep_spmv_tma2(
     OpView<float> op, const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
     const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_z, float* __restrict__ u,
     float* __restrict__ p, float* __restrict__ q, const float* __restrict__ z, SolveState* __restrict__ states,
@@ -1394,7 +1362,8 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
     uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 2 * STAGE + ((3 * nz + 4) & ~3));
     const int rhs = blockIdx.y;
     SolveState* st = states + rhs;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    // block (BX, BYT * S): row ty of the tile, level part tz of the chunk
+    const int tx = threadIdx.x, ty = threadIdx.y % BYT, tz = threadIdx.y / BYT, tid = threadIdx.y * BX + tx;
     const int nitems = gx * gy * nchunks;
     const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
     // prologue on data no sweep writes (it may overlap the previous sweep)
@@ -1402,7 +1371,7 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
         mbar_init(bar0);
         mbar_init(bar1);
     }
-    for (int k = tid; k < nz; k += BX * BYT) {
+    for (int k = tid; k < nz; k += BX * BYT * S) {
         tbw[k + 1] = ldro(op.wv + k);
         tbd[k] = ldro(op.dk + k);
         tbm[k] = ldro(op.mass + k);
@@ -1445,7 +1414,7 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
         const int i0 = (tile % gx) * BX, j0 = (tile / gx) * BYT, k0 = ch * LZ;
         const int kn = min(LZ, nz - k0);
         WrapPatch<LZ, BYT> wp;
-        wp.load(op, z + base, i0, j0, k0, kn, tx, ty);
+        wp.load(op, z + base, i0, j0, k0, tz == 0 ? kn : 0, tx, ty);   // the first level part patches the halo
         const Col<float> col = make_col(op, i0 + tx, j0 + ty);
         bool landed = mbar_wait(stage ? bar1 : bar0, stage ? par1 : par0, 1 << 22);
         landed = __syncthreads_and(landed ? 1 : 0) != 0;
@@ -1462,9 +1431,9 @@ __global__ __launch_bounds__(BX * BYT) void k_sweep_spmv_tma2(
             __syncthreads();
         }
         if (col.valid && kn > 0)
-            spmv_tile_compute_p<LZ, BYT>(op, col, tx, ty, k0, kn, zs, zs + TT::ZN, zs + TT::ZN + TT::VN,
-                                         zs + TT::ZN + 2 * TT::VN, tbw + 1 + k0, tbd + k0, tbm + k0, u + base,
-                                         p + base, q + base, alpha, beta, sig[0]);
+            spmv_tile_compute_p<LZ, BYT, S>(op, col, tx, ty, k0, kn, zs, zs + TT::ZN, zs + TT::ZN + TT::VN,
+                                            zs + TT::ZN + 2 * TT::VN, tbw + 1 + k0, tbd + k0, tbm + k0, u + base,
+                                            p + base, q + base, alpha, beta, sig[0], tz);
         // the stage has been read (and patched) by the threads: order that
         // before the bulk copies that refill it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

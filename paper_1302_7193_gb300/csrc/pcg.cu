@@ -101,7 +101,7 @@ struct pcg_ctx {
     dim3 grid, block;
     // chunked sweeps (levels split across threads): launch shapes
     int chunked32 = 0, chunked64 = 0, lz_a = 16, lz_b = 16, nch_b = 1;
-    int spmv32 = 0, spmv64 = 0;          // SpMV sweep variant: 0 per column, 1 chunked, 2 chunked + smem tile, 3 TMA,
+    int spmv32 = 0, spmv64 = 0;          // SpMV sweep variant: 0 per column, 1 chunked, 3 TMA,
                                           // 4 persistent two-stage TMA
     dim3 grid_a, block_a, grid_b, block_b;
     int nblk_a = 0, nblk_b = 0;
@@ -486,8 +486,9 @@ bool encode_map(pcg_t h, CUtensorMap* m, float* base, unsigned bx, unsigned by, 
 
 constexpr int TMA_LZ = 16, TMA_BY = 8;
 using SpmvTile = pcg::SpmvTmaTile<TMA_LZ, TMA_BY>;
-// persistent pipelined SpMV sweep: 16-level chunks of 32 x 4-column tiles
-constexpr int TMA2_LZ = 16, TMA2_BY = 4;
+// persistent pipelined SpMV sweep: 16-level chunks of 32 x 4-column tiles,
+// two threads per column (8 levels each)
+constexpr int TMA2_LZ = 16, TMA2_BY = 4, TMA2_S = 2;
 size_t spmv2_smem(int nz) { return pcg::spmv_tma2_smem<TMA2_LZ, TMA2_BY>(nz); }
 
 int ensure_ws32(pcg_t h) {
@@ -499,11 +500,11 @@ int ensure_ws32(pcg_t h) {
         const unsigned zx = BX + 2 * pcg::TMA_HALO_X;
         const size_t smem = spmv2_smem(h->nz);
         int occ = 0, dev = 0, sms = 1;
-        cudaError_t ea = cudaFuncSetAttribute(pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY>,
+        cudaError_t ea = cudaFuncSetAttribute(pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY, TMA2_S>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ea == cudaSuccess)
-            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY>,
-                                                               BX * TMA2_BY, smem);
+            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY, TMA2_S>,
+                                                               BX * TMA2_BY * TMA2_S, smem);
         if (ea == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         h->spmv2_nch = (h->nz + TMA2_LZ - 1) / TMA2_LZ;
@@ -639,13 +640,13 @@ template <typename T>
 void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, T* z, SolveState* st,
                  bool pdl = false) {
     const int mode = sizeof(T) == 4 ? h->spmv32 : h->spmv64;
-#define PCG_SPMV_CH(LZ, TILE, MB)                                                                            \
-    pcg::k_sweep_spmv_chunked<T, LZ, TILE, MB><<<h->grid_b, h->block_b, 0, s>>>(v, u, p, q, z, st, h->partials,  \
-                                                                                h->counters, h->nblk_b, h->nch_b)
+#define PCG_SPMV_CH(LZ, MB)                                                                                  \
+    pcg::k_sweep_spmv_chunked<T, LZ, MB><<<h->grid_b, h->block_b, 0, s>>>(v, u, p, q, z, st, h->partials,      \
+                                                                          h->counters, h->nblk_b, h->nch_b)
     if constexpr (sizeof(T) == 4) {
         if (mode == 4 && h->tma2_ready && u == h->u32 && p == h->p32 && q == h->q32 && z == h->z32) {
-            launch_pdl(pdl, pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY>, dim3(h->spmv2_G, h->nrhs, 1),
-                       dim3(BX, TMA2_BY, 1), spmv2_smem(h->nz), s, v, h->tm2_u, h->tm2_p, h->tm2_q, h->tm2_z, u, p, q,
+            launch_pdl(pdl, pcg::k_sweep_spmv_tma2<TMA2_LZ, TMA2_BY, TMA2_S>, dim3(h->spmv2_G, h->nrhs, 1),
+                       dim3(BX, TMA2_BY * TMA2_S, 1), spmv2_smem(h->nz), s, v, h->tm2_u, h->tm2_p, h->tm2_q, h->tm2_z, u, p, q,
                        (const T*)z, st, h->partials, h->counters, h->spmv2_gx, h->spmv2_gy, h->spmv2_nch);
             return;
         }
@@ -661,10 +662,8 @@ void launch_spmv(pcg_t h, cudaStream_t s, const OpView<T>& v, T* u, T* p, T* q, 
             return;
         }
     }
-    if (mode == 2) {
-        PCG_SPMV_CH(16, true, 1);
-    } else if (mode == 1 || mode >= 3) {
-        PCG_SPMV_CH(16, false, 1);
+    if (mode == 1 || mode >= 3) {
+        PCG_SPMV_CH(16, 1);
     } else {
         const dim3 g(h->grid_c.x, h->grid_c.y, h->grid_c.z * h->ksplit);
         if (sizeof(T) == 8 && h->spmv_pipe)
@@ -1397,8 +1396,7 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     // FP32 SpMV sweep without TMA: chunked while the grid has few columns
     // (65536 columns: 93 us vs 123 us per sweep at 128 levels); one thread per
     // column once there are enough columns to hide latency (2^20 columns:
-    // 966 us vs 1300 us).  A shared-memory z tile loaded by the threads
-    // measured slower than both and is kept only as an experiment (PCG_SPMV=tile).
+    // 966 us vs 1300 us).
     h->spmv32 = (h->chunked32 && h->plane * (long long)h->nrhs < (1LL << 19)) ? 1 : 0;
     h->spmv64 = h->chunked64 ? 1 : 0;
     // TMA-staged FP32 SpMV sweep (k_sweep_spmv_tma): tiles of 32 x 8 columns x
@@ -1435,9 +1433,8 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
             }
         }
     }
-    if (const char* sv = std::getenv("PCG_SPMV")) {            // experiments: column|chunked|tile|tma|tma2
-        const int m = !std::strcmp(sv, "tile") ? 2 : (!std::strcmp(sv, "chunked") ? 1 :
-                      (!std::strcmp(sv, "tma") ? 3 : (!std::strcmp(sv, "tma2") ? 4 : 0)));
+    if (const char* sv = std::getenv("PCG_SPMV")) {            // experiments: column|chunked|tma|tma2
+        const int m = !std::strcmp(sv, "chunked") ? 1 : (!std::strcmp(sv, "tma") ? 3 : (!std::strcmp(sv, "tma2") ? 4 : 0));
         if (h->nz <= 256 && (long long)h->nrhs * h->nch_b <= 65535) {
             h->spmv32 = (m >= 3 && !tma_ok) ? 1 : m;
             if (m < 3) h->spmv64 = m;

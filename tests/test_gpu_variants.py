@@ -39,7 +39,6 @@ FP32_VARIANTS = {
     "default": {},
     "spmv-column": {"PCG_SPMV": "column"},
     "spmv-chunked": {"PCG_SPMV": "chunked"},
-    "spmv-tile": {"PCG_SPMV": "tile"},
     "spmv-tma-single-stage": {"PCG_SPMV": "tma"},
     "spmv-tma-single-stage-8rows": {"PCG_SPMV": "tma", "PCG_TMA_BY": "8"},
     "prec-chunked": {"PCG_PREC": "chunked"},
