@@ -124,7 +124,8 @@ typedef struct {
     double inner_tol;          /* PCG_MIXED: relative tolerance of each FP32 inner solve; 0 selects 1e-5 */
     int inner_maxit;           /* PCG_MIXED: iteration cap of each inner solve; 0 selects 20000 */
     int max_outer;             /* PCG_MIXED: refinement sweeps cap; 0 selects 16   */
-    int passes_per_launch;     /* PCG passes per CUDA-graph launch between convergence polls; 0 selects 16 */
+    int passes_per_launch;     /* PCG passes per CUDA-graph launch between convergence polls; 0 selects 16
+                                  (4 with a multigrid preconditioner)                                  */
     void* stream;              /* cudaStream_t for all work; NULL = default stream */
     int preconditioner;        /* pcg_preconditioner (PCG_PREC_LINE when opts is NULL) */
     int algorithm;             /* pcg_algorithm (PCG_ALG_INTERLEAVED when opts is NULL) */

@@ -1307,6 +1307,11 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
     }
     h->mg_f32 = h->precond == PCG_PREC_MULTIGRID_F32;
     if (h->mg_f32) h->precond = PCG_PREC_MULTIGRID;
+    // A multigrid-preconditioned solve takes about 20 passes, and the two
+    // graph launches in flight at its end run their remaining passes as
+    // early exits, about 30 kernels each: 4 passes per launch instead of 16
+    // cut those to a few (a launch of 4 passes still outlasts the host's poll)
+    if (h->precond == PCG_PREC_MULTIGRID && !(opts && opts->passes_per_launch > 0)) h->ppl = 4;
     if (h->precond == PCG_PREC_MULTIGRID && h->precision != PCG_FP64) {
         delete h;
         return fail(nullptr, PCG_ERR_INVALID_ARG, "the multigrid preconditioner is available with PCG_FP64 only");

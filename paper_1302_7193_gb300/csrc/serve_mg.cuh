@@ -46,6 +46,10 @@ void mg_solve_one(ServeReq* q, cudaStream_t st) {
     pcg_opts_t o{};
     o.precision = PCG_FP64;
     o.preconditioner = PCG_PREC_MULTIGRID_F32;
+    // 16 passes per graph launch, not the 4 a lone multigrid solve takes:
+    // with up to 16 workers polling, fewer and longer launches measured
+    // faster, and other requests' work covers a solve's trailing early exits
+    o.passes_per_launch = 16;
     o.stream = (void*)st;
     pcg_t h = nullptr;
     pcg_stats_t res{};
