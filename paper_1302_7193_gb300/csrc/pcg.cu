@@ -1417,7 +1417,8 @@ int pcg_create(const pcg_grid_t* grid, const pcg_coeffs_t* coeffs, const pcg_opt
                         (long long)h->nz * h->nrhs < (1LL << 31);
     // the persistent two-stage TMA sweep wherever it applies: 54 us at
     // 256^2 x 128, 648 us at 1024^2 x 128, 4.50 ms for 16 rhs of 1440 x 640 x 64
-    // (4.3, 5.8, 5.9 TB/s), against 58 us, 832 us and 5.11 ms single-stage
+    // (4.3, 5.8, 5.9 TB/s), against 58 us, 832 us and 5.11 ms single-stage;
+    // with two threads per column 51 us and 621 us
     if (tma_ok) h->spmv32 = 4;
     // TMA-pipelined FP32 preconditioner sweep: items of prec_R rows of 32
     // columns (prec_R x chunks <= 8 warps), same eligibility plus the chunked form
