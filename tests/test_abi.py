@@ -141,3 +141,59 @@ def test_structs_match_header_layout(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
+def _noalloc_structs(p, alpha=None):
+    keep = []
+    z, zp = pkg._dbl(p.z_iface)
+    be, bp = pkg._dbl(p.beta_iface)
+    keep += [z, be]
+    ap = None
+    if alpha is not None:
+        a, ap = pkg._dbl(alpha)
+        keep.append(a)
+    g = pkg.pcg_grid_t(p.kind, p.n_x, p.n_y, p.n_z, 1, zp, p.lx, p.ly, p.lat0, p.lat1)
+    c = pkg.pcg_coeffs_t(ap, None, bp, p.lambda2)
+    return g, c, keep
+
+
+def test_noalloc_precond_rejects_bad_arguments_before_the_device(lib):
+    """pcg_precond_noalloc checks its arguments and the size of its fixed
+    scratch on the host, before any CUDA call: each bad case returns
+    PCG_ERR_INVALID_ARG with its reason.  The vector pointers are never
+    dereferenced on these paths (skipped where a GPU is present, so that no
+    kernel could ever be handed them)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("host-only argument checks; the GPU path is covered by test_zz_no_alloc.py")
+    r = z = ctypes.c_void_p(256)
+
+    def call(g, c, rr=r, zz=z):
+        rc = lib.pcg_precond_noalloc(ctypes.byref(g) if g is not None else None,
+                                     ctypes.byref(c) if c is not None else None, rr, zz, None)
+        return rc, lib.pcg_last_error(None).decode()
+
+    p = W.small_box()
+    g, c, keep = _noalloc_structs(p)
+    for args in ((None, c), (g, None)):
+        rc, msg = call(*args)
+        assert rc == pkg.PCG_ERR_INVALID_ARG and "required" in msg
+    rc, msg = call(g, c, rr=None)
+    assert rc == pkg.PCG_ERR_INVALID_ARG and "required" in msg
+    g.geometry = 7
+    rc, msg = call(g, c)
+    assert rc == pkg.PCG_ERR_INVALID_ARG and "geometry" in msg
+    g, c, keep = _noalloc_structs(p)
+    c.lambda2 = float("nan")
+    rc, msg = call(g, c)
+    assert rc == pkg.PCG_ERR_INVALID_ARG and "lambda2" in msg
+    g, c, keep = _noalloc_structs(p)
+    g.n_z = 0
+    rc, msg = call(g, c)
+    assert rc == pkg.PCG_ERR_INVALID_ARG and ">= 1" in msg
+    # per-column factors of a 256 x 256 x 128 grid need 3 * 128 * 65536 doubles
+    big = W.box_problem(256, 256, 128, 0.004)
+    g, c, keep = _noalloc_structs(big, alpha=np.ones(big.n_x * big.n_y))
+    rc, msg = call(g, c)
+    assert rc == pkg.PCG_ERR_INVALID_ARG and "scratch" in msg, msg
+    assert str(3 * 128 * 65536 + 3 * 128 + 256 + 2 * 65536) in msg
