@@ -859,8 +859,7 @@ def main():
     # mixed precision form of the same solve: to tol 1e-8 (the refinement stops
     # at the FP64 rounding floor, R12), and stopped at the true residual the
     # FP64 solve reached (one accuracy target for both)
-    mixed = mixed_eq = None
-    if not args.no_mixed:
+    def measure_mixed():
         with pkg.Solver(p, precision="mixed", stream=stream.cuda_stream) as sm:
             for _ in range(2):
                 x.zero_()
@@ -899,11 +898,19 @@ def main():
                         "speedup_vs_fp64": (1000.0 / statistics.mean(et)) / (1000.0 / ms_per_step),
                         "note": "stopped at the true relative residual the FP64 solve reached (its attainable "
                                 "accuracy at tol 1e-8 on the updated residual)"}
+        return mixed, mixed_eq
+
+    mixed = mixed_eq = None
+    if not args.no_mixed:
+        try:
+            mixed, mixed_eq = measure_mixed()
+        except Exception as e:          # recorded; the FP64 line above stands
+            mixed = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
 
     # the same FP64 solve with the multigrid V-cycle as preconditioner, in FP64
     # and in FP32 (the cycle only; the CG stays FP64)
-    multigrid = multigrid_f32 = None
-    if not args.no_mixed:
+    def measure_multigrid():
         mg = {}
         for pc in ("multigrid", "multigrid-f32"):
             with pkg.Solver(p, preconditioner=pc, stream=stream.cuda_stream) as sg:
@@ -926,7 +933,15 @@ def main():
                           "err_vs_oracle": err_vs_digest(x, digest, p.n_z),
                           "speedup_vs_line_fp64": (1000.0 / statistics.mean(gt)) / (1000.0 / ms_per_step),
                           "gpu_launches_per_solve": sg.kernel_launches}
-        multigrid, multigrid_f32 = mg["multigrid"], mg["multigrid-f32"]
+        return mg["multigrid"], mg["multigrid-f32"]
+
+    multigrid = multigrid_f32 = None
+    if not args.no_mixed:
+        try:
+            multigrid, multigrid_f32 = measure_multigrid()
+        except Exception as e:          # recorded; the FP64 line above stands
+            multigrid = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -954,22 +969,37 @@ def main():
             except Exception as e:
                 cpu["all_cores"] = {"value": None, "sample": f"failed: {e}"}
 
-    # the other configurations, measured in the same run (one GPU only)
+    # the other configurations, measured in the same run (one GPU only); a
+    # failure in one of them is recorded under its key and does not cost the
+    # benchmark line measured above
     extras = {}
+
+    def guarded(key, fn):
+        try:
+            extras[key] = fn()
+        except Exception as e:
+            extras[key] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+
     if rank == 0 and world == 1 and not args.quick:
-        extras["box1024"] = large_config_measure(dev, pkg, W, torch, "box1024", hbm_peak)
-        extras["serve"] = serve_measure(dev, pkg, W, torch, 0.5, "paper", compare=True,
-                                        arms=[("fp64", "host"), ("mixed", "host"), ("mixed", "device")])
+        guarded("box1024", lambda: large_config_measure(dev, pkg, W, torch, "box1024", hbm_peak))
+        guarded("serve", lambda: serve_measure(dev, pkg, W, torch, 0.5, "paper", compare=True,
+                                               arms=[("fp64", "host"), ("mixed", "host"), ("mixed", "device")]))
+
         # the same requests served with the multigrid preconditioner (worker pool), against one-at-a-time
         # multigrid solves; the other one-at-a-time arms are the line server's
-        smg = serve_measure(dev, pkg, W, torch, 0.5, "paper", compare=True, preconditioner="multigrid-f32",
-                            arms=[("multigrid-f32", "host")])
-        for key in ("sequential_fp64_host", "sequential_mixed_host"):
-            smg[key] = extras["serve"][key]
-            smg["served_speedup_vs_" + key] = smg["value"] / smg[key]["solves_per_s"]
-        extras["serve_multigrid"] = smg
-        extras["shell_batch"] = large_config_measure(dev, pkg, W, torch, "shell-batch", hbm_peak,
-                                                     same_accuracy=False, fp64_maxit=600)
+        def serve_mg():
+            smg = serve_measure(dev, pkg, W, torch, 0.5, "paper", compare=True, preconditioner="multigrid-f32",
+                                arms=[("multigrid-f32", "host")])
+            for key in ("sequential_fp64_host", "sequential_mixed_host"):
+                if key in extras["serve"]:
+                    smg[key] = extras["serve"][key]
+                    smg["served_speedup_vs_" + key] = smg["value"] / smg[key]["solves_per_s"]
+            return smg
+
+        guarded("serve_multigrid", serve_mg)
+        guarded("shell_batch", lambda: large_config_measure(dev, pkg, W, torch, "shell-batch", hbm_peak,
+                                                            same_accuracy=False, fp64_maxit=600))
 
     if rank == 0:
         line = {
